@@ -1,0 +1,429 @@
+// soma_oracle.cpp -- TEST INFRASTRUCTURE, not part of the product path.
+//
+// A plain, slow, FP64 CPU restatement of the single-chain-in-mean-field (SCMF)
+// Monte Carlo step that the paper's particle model (SOMA) runs (Sec. 2, the
+// SOMA paragraph: soft coarse-grained polymer model, quasi-instantaneous
+// fields for the non-bonded interactions, MC propagation of beads; Sec. 2.2:
+// the two kernels that dominate, the move kernel and the density-field
+// update).  Only tests, the package's smoke check and the benchmark's CPU
+// baseline may load this library.  It shares no code, header, table or
+// generator with the CUDA path.
+//
+// The paper names the model but prints none of its equations.  Every formula
+// below is the standard SCMF bead-spring model written out in the order the
+// step runs; each reading of an unstated detail is marked "Reading:".
+//
+// Conventions (all lengths in units of R_e = 1, energies in kT):
+//   beads of chain c are i = 0..N-1; bead i is type A if i < n_A, else B;
+//   positions are unwrapped FP64, stored pos[((c*N)+i)*3 + axis];
+//   cells are c = (ix*ny + iy)*nz + iz; counts and fields are [type][cell].
+//
+// Parity status of each exported function (what pins it in tests/):
+//   orc_philox4x32        pinned: an independent third-party Philox4x32-10
+//                         (Triton's, run by its CPU interpreter) bit for bit.
+//   orc_init              pinned: bond statistics of a Gaussian chain
+//                         (<b^2> = 1/(N-1), <R_e^2> = 1, <R_g^2> = (N+1)/6N).
+//   orc_density           pinned: count invariants and brute-force binning.
+//   orc_fields            pinned: central difference of the energy functional
+//                         and the incompressible exchange-field special case.
+//   orc_mc_step/orc_run   pinned: <R_e^2> = 1 and the acceptance quadrature at
+//                         chiN = kappaN = 0; Boltzmann occupancy of one bead in
+//                         a frozen field; exact 64-state cell-pair law of an AB
+//                         dimer on a 2^3 grid.
+//   orc_observables       pinned through the same closed forms (R_e^2, R_g^2).
+//   orc_structure_factor  pinned: ideal-chain closed form at chiN = kappaN = 0.
+//   The chiN, kappaN > 0 statistics of a dense melt have no closed form:
+//   parity unpinned there except against this oracle itself.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+extern "C" {
+
+// One system: chain architecture, box, grid, interaction strengths, seed.
+typedef struct {
+  int32_t n_poly;     // number of chains
+  int32_t N;          // beads per chain
+  int32_t n_A;        // beads 0..n_A-1 are type A, the rest type B
+  int32_t sys_index;  // system number s, the fourth Philox counter word
+  int32_t grid[3];    // cells per axis
+  int32_t pad_;
+  double box[3];      // box edge per axis, R_e units
+  double chiN, kappaN;
+  double A;           // proposal half-width; A <= 0 means 0.5/sqrt(N-1)
+  uint64_t seed;      // Philox key (lo, hi)
+} orc_desc;
+
+typedef struct {
+  double Re2;    // mean over chains of |r_{N-1} - r_0|^2
+  double Rg2;    // mean over chains of (1/N) sum_i |r_i - r_cm|^2
+  double Ebond;  // k_b * sum over bonds |b|^2
+  double Enb;    // (n_poly/n_c) sum_c [chiN phiA phiB + kappaN/2 (phiA+phiB-1)^2]
+} orc_obs;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): a 4-word counter and a
+// 2-word key; ten rounds, each multiplying counter words 0 and 2 by the two
+// published round multipliers, crossing high halves into the other pair with
+// the key, then bumping the key by the two published Weyl constants.
+// ---------------------------------------------------------------------------
+void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t prod0 = (uint64_t)M0 * (uint64_t)x0;
+    uint64_t prod1 = (uint64_t)M1 * (uint64_t)x2;
+    uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+    uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+    x0 = hi1 ^ x1 ^ k0;
+    x1 = lo1;
+    x2 = hi0 ^ x3 ^ k1;
+    x3 = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void orc_philox4x32_many(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  for (int64_t j = 0; j < n; ++j) orc_philox4x32(ctr + 4 * j, key + 2 * j, out + 4 * j);
+}
+
+// Reading: the counter of a bead move is (bead i, logical chain c, step t,
+// system s) and the key is the 64-bit seed split (lo, hi).  Step value
+// 0xFFFFFFFF is reserved for initialisation.
+static void draw(const orc_desc* d, uint32_t bead, uint32_t chain, uint32_t step, uint32_t r[4]) {
+  uint32_t ctr[4] = {bead, chain, step, (uint32_t)d->sys_index};
+  uint32_t key[2] = {(uint32_t)(d->seed & 0xFFFFFFFFu), (uint32_t)(d->seed >> 32)};
+  orc_philox4x32(ctr, key, r);
+}
+
+// Reading: a word w maps to a uniform on [0,1) as (w >> 8) * 2^-24 and to a
+// uniform on the open interval (0,1) as ((w >> 9) + 1/2) * 2^-23.
+static double unit_closed_open(uint32_t w) { return (double)(w >> 8) * 0x1p-24; }
+static double unit_open(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23; }
+static double unit_open24(uint32_t w) { return ((double)(w >> 8) + 0.5) * 0x1p-24; }
+
+// ---------------------------------------------------------------------------
+// Model constants.
+// ---------------------------------------------------------------------------
+// Harmonic bond energy (3(N-1)/2) |b|^2 in units of kT and R_e^2.
+static double bond_k(const orc_desc* d) { return 1.5 * (double)(d->N - 1); }
+
+// Proposal half-width: 0.5 R_e / sqrt(N-1) unless given; rounded through FP32
+// so that both implementations use the identical constant.
+static double proposal_A(const orc_desc* d) {
+  double a = d->A > 0.0 ? d->A : 0.5 / std::sqrt((double)(d->N - 1));
+  return (double)(float)a;
+}
+
+static int64_t n_beads(const orc_desc* d) { return (int64_t)d->n_poly * d->N; }
+static int64_t n_cells(const orc_desc* d) {
+  return (int64_t)d->grid[0] * d->grid[1] * d->grid[2];
+}
+static int type_of(const orc_desc* d, int i) { return i < d->n_A ? 0 : 1; }
+
+void orc_params(const orc_desc* d, double* k_b, double* A_eff, double* rho_bar) {
+  *k_b = bond_k(d);
+  *A_eff = proposal_A(d);
+  *rho_bar = (double)n_beads(d) / (double)n_cells(d);
+}
+
+// Cell of a position: wrap into [0, L) per axis, scale by n/L, floor, clamp.
+static int64_t cell_of(const orc_desc* d, const double r[3]) {
+  int64_t idx[3];
+  for (int a = 0; a < 3; ++a) {
+    double L = d->box[a];
+    double xw = r[a] - L * std::floor(r[a] / L);
+    int64_t i = (int64_t)std::floor(xw * ((double)d->grid[a] / L));
+    if (i > d->grid[a] - 1) i = d->grid[a] - 1;
+    if (i < 0) i = 0;
+    idx[a] = i;
+  }
+  return (idx[0] * d->grid[1] + idx[1]) * d->grid[2] + idx[2];
+}
+
+// Smallest distance from a position to a cell face (used by tests to set
+// aside moves whose cell is decided by the last bits of a coordinate).
+static double face_distance(const orc_desc* d, const double r[3]) {
+  double best = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    double L = d->box[a];
+    double h = L / (double)d->grid[a];
+    double xw = r[a] - L * std::floor(r[a] / L);
+    double f = xw / h - std::floor(xw / h);
+    double dist = std::fmin(f, 1.0 - f) * h;
+    if (dist < best) best = dist;
+  }
+  return best;
+}
+
+int64_t orc_cell_index(const orc_desc* d, const double* r) { return cell_of(d, r); }
+
+// ---------------------------------------------------------------------------
+// Initial configuration: bead 0 uniform in the box, every bond vector an
+// independent Gaussian with per-axis variance R_e^2 / (3(N-1)).
+// Reading: bead 0 uses x_a = L_a * U(word a); bond i uses Box-Muller on word
+// pairs (0,1) and (2,3), keeping three of the four normals.
+// ---------------------------------------------------------------------------
+void orc_init(const orc_desc* d, double* pos) {
+  const double sigma = d->N > 1 ? std::sqrt(1.0 / (3.0 * (double)(d->N - 1))) : 0.0;
+  const double two_pi = 2.0 * M_PI;
+  for (int c = 0; c < d->n_poly; ++c) {
+    double* p = pos + (int64_t)c * d->N * 3;
+    for (int i = 0; i < d->N; ++i) {
+      uint32_t r[4];
+      draw(d, (uint32_t)i, (uint32_t)c, 0xFFFFFFFFu, r);
+      if (i == 0) {
+        for (int a = 0; a < 3; ++a) p[a] = d->box[a] * unit_closed_open(r[a]);
+      } else {
+        double rho1 = std::sqrt(-2.0 * std::log(unit_open24(r[0])));
+        double rho2 = std::sqrt(-2.0 * std::log(unit_open24(r[2])));
+        double z0 = rho1 * std::cos(two_pi * unit_closed_open(r[1]));
+        double z1 = rho1 * std::sin(two_pi * unit_closed_open(r[1]));
+        double z2 = rho2 * std::cos(two_pi * unit_closed_open(r[3]));
+        p[3 * i + 0] = p[3 * (i - 1) + 0] + sigma * z0;
+        p[3 * i + 1] = p[3 * (i - 1) + 1] + sigma * z1;
+        p[3 * i + 2] = p[3 * (i - 1) + 2] + sigma * z2;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Density counts n_t(c): the number of beads of type t whose position lies in
+// cell c (the density-field update of Sec. 2.2), recomputed from scratch.
+// ---------------------------------------------------------------------------
+void orc_density(const orc_desc* d, const double* pos, uint32_t* counts) {
+  const int64_t nc = n_cells(d);
+  std::memset(counts, 0, sizeof(uint32_t) * 2 * nc);
+  for (int c = 0; c < d->n_poly; ++c)
+    for (int i = 0; i < d->N; ++i) {
+      const double* r = pos + ((int64_t)c * d->N + i) * 3;
+      counts[type_of(d, i) * nc + cell_of(d, r)] += 1;
+    }
+}
+
+// Quasi-instantaneous fields from the counts.  With phi_t = n_t / rho_bar the
+// non-bonded energy is the Flory-Huggins term plus Helfand compressibility,
+//   H_nb = (rho_bar/N) sum_c [chiN phiA phiB + (kappaN/2)(phiA + phiB - 1)^2],
+// and the field a bead of type t feels in cell c is dH_nb / dn_t(c):
+//   w_A = [chiN phiB + kappaN (phiA + phiB - 1)] / N,
+//   w_B = [chiN phiA + kappaN (phiA + phiB - 1)] / N.
+// Reading: the Flory-Huggins form of the chi term.
+static void cell_fields(const orc_desc* d, double phiA, double phiB, double* wA, double* wB) {
+  const double N = (double)d->N;
+  double excess = phiA + phiB - 1.0;
+  *wA = (d->chiN * phiB + d->kappaN * excess) / N;
+  *wB = (d->chiN * phiA + d->kappaN * excess) / N;
+}
+
+void orc_fields(const orc_desc* d, const uint32_t* counts, double* w) {
+  const int64_t nc = n_cells(d);
+  const double rho_bar = (double)n_beads(d) / (double)nc;
+  for (int64_t c = 0; c < nc; ++c)
+    cell_fields(d, counts[c] / rho_bar, counts[nc + c] / rho_bar, &w[c], &w[nc + c]);
+}
+
+// The non-bonded energy functional itself, H_nb from the counts.
+double orc_energy_nb(const orc_desc* d, const uint32_t* counts) {
+  const int64_t nc = n_cells(d);
+  const double rho_bar = (double)n_beads(d) / (double)nc;
+  double sum = 0.0;
+  for (int64_t c = 0; c < nc; ++c) {
+    double phiA = counts[c] / rho_bar, phiB = counts[nc + c] / rho_bar;
+    double excess = phiA + phiB - 1.0;
+    sum += d->chiN * phiA * phiB + 0.5 * d->kappaN * excess * excess;
+  }
+  return (double)d->n_poly / (double)nc * sum;
+}
+
+// Fields from given volume fractions (the coupling write of Sec. 3.2: the
+// particle run is handed concentration fields).
+void orc_fields_from_phi(const orc_desc* d, const double* phi, double* w) {
+  const int64_t nc = n_cells(d);
+  for (int64_t c = 0; c < nc; ++c) cell_fields(d, phi[c], phi[nc + c], &w[c], &w[nc + c]);
+}
+
+// ---------------------------------------------------------------------------
+// One Monte Carlo step t with frozen fields w.
+// Reading: the beads of a linear chain split into two sets, even i and odd
+// i, that share no bond; set 0 (even) moves first for every chain, then set
+// 1 (odd) sees the accepted set-0 positions.  The fields stay fixed for the
+// whole step (quasi-instantaneous field approximation, Sec. 2).
+// For every bead of the current set:
+//   d_a   = A (2 U(word a) - 1), a = 0, 1, 2;  r' = r + d
+//   dE    = k_b sum_{j = i +- 1, 0 <= j < N} (|r' - r_j|^2 - |r - r_j|^2)
+//           + w_type(cell r') - w_type(cell r)
+//   u     = open uniform from word 3
+//   accept iff dE + ln u < 0   (Metropolis, strict)
+// Optional per-bead records: accepted flag, the margin dE + ln u, and the
+// smaller distance of r and r' to a cell face.  Returns the accepted count.
+// ---------------------------------------------------------------------------
+static int64_t move_set(const orc_desc* d, double* pos, const double* w, uint32_t t, int set,
+                        uint8_t* acc_out, double* margin_out, double* face_out, int n_threads) {
+  const int64_t nc = n_cells(d);
+  const double k_b = bond_k(d);
+  const double A = proposal_A(d);
+  const int N = d->N;
+  int64_t accepted = 0;
+#pragma omp parallel for schedule(static) reduction(+ : accepted) num_threads(n_threads)
+  for (int c = 0; c < d->n_poly; ++c) {
+    double* p = pos + (int64_t)c * N * 3;
+    for (int i = set; i < N; i += 2) {
+      uint32_t r[4];
+      draw(d, (uint32_t)i, (uint32_t)c, t, r);
+      double* ri = p + 3 * i;
+      double rn[3];
+      for (int a = 0; a < 3; ++a) rn[a] = ri[a] + A * (2.0 * unit_closed_open(r[a]) - 1.0);
+      double dEb = 0.0;
+      for (int j = i - 1; j <= i + 1; j += 2) {
+        if (j < 0 || j >= N) continue;
+        const double* rj = p + 3 * j;
+        double new2 = 0.0, old2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          new2 += (rn[a] - rj[a]) * (rn[a] - rj[a]);
+          old2 += (ri[a] - rj[a]) * (ri[a] - rj[a]);
+        }
+        dEb += new2 - old2;
+      }
+      const double* wt = w + (int64_t)type_of(d, i) * nc;
+      double dE = k_b * dEb + wt[cell_of(d, rn)] - wt[cell_of(d, ri)];
+      double margin = dE + std::log(unit_open(r[3]));
+      bool ok = margin < 0.0;
+      int64_t b = (int64_t)c * N + i;
+      if (acc_out) acc_out[b] = ok ? 1 : 0;
+      if (margin_out) margin_out[b] = margin;
+      if (face_out) face_out[b] = std::fmin(face_distance(d, ri), face_distance(d, rn));
+      if (ok) {
+        for (int a = 0; a < 3; ++a) ri[a] = rn[a];
+        accepted += 1;
+      }
+    }
+  }
+  return accepted;
+}
+
+int64_t orc_mc_step(const orc_desc* d, double* pos, const double* w, uint32_t t, uint8_t* acc_out,
+                    double* margin_out, double* face_out, int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  int64_t a0 = move_set(d, pos, w, t, 0, acc_out, margin_out, face_out, n_threads);
+  int64_t a1 = move_set(d, pos, w, t, 1, acc_out, margin_out, face_out, n_threads);
+  return a0 + a1;
+}
+
+// ---------------------------------------------------------------------------
+// Observables (FP64).  Reading: the paper defines none; these are the
+// standard chain and melt measures.
+// ---------------------------------------------------------------------------
+void orc_observables(const orc_desc* d, const double* pos, orc_obs* out) {
+  const int N = d->N;
+  double re2 = 0.0, rg2 = 0.0, eb = 0.0;
+  for (int c = 0; c < d->n_poly; ++c) {
+    const double* p = pos + (int64_t)c * N * 3;
+    double e2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double v = p[3 * (N - 1) + a] - p[a];
+      e2 += v * v;
+    }
+    re2 += e2;
+    double cm[3] = {0, 0, 0};
+    for (int i = 0; i < N; ++i)
+      for (int a = 0; a < 3; ++a) cm[a] += p[3 * i + a] / N;
+    double g2 = 0.0;
+    for (int i = 0; i < N; ++i)
+      for (int a = 0; a < 3; ++a) g2 += (p[3 * i + a] - cm[a]) * (p[3 * i + a] - cm[a]);
+    rg2 += g2 / N;
+    for (int i = 1; i < N; ++i)
+      for (int a = 0; a < 3; ++a) {
+        double b = p[3 * i + a] - p[3 * (i - 1) + a];
+        eb += b * b;
+      }
+  }
+  out->Re2 = re2 / d->n_poly;
+  out->Rg2 = rg2 / d->n_poly;
+  out->Ebond = bond_k(d) * eb;
+
+  std::vector<uint32_t> counts(2 * n_cells(d));
+  orc_density(d, pos, counts.data());
+  out->Enb = orc_energy_nb(d, counts.data());
+}
+
+// Collective structure factor of the composition, S(q) = (1/n_b) |sum_j s_j
+// exp(i q.r_j)|^2 with s_j = +1 for A and -1 for B, at the lattice vectors
+// q = 2 pi m / L for the nq integer triples m.
+void orc_structure_factor(const orc_desc* d, const double* pos, int nq, const int32_t* m,
+                          double* S) {
+  const int64_t nb = n_beads(d);
+  for (int k = 0; k < nq; ++k) {
+    double q[3];
+    for (int a = 0; a < 3; ++a) q[a] = 2.0 * M_PI * (double)m[3 * k + a] / d->box[a];
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < d->n_poly; ++c)
+      for (int i = 0; i < d->N; ++i) {
+        const double* r = pos + ((int64_t)c * d->N + i) * 3;
+        double ph = q[0] * r[0] + q[1] * r[1] + q[2] * r[2];
+        double s = type_of(d, i) == 0 ? 1.0 : -1.0;
+        re += s * std::cos(ph);
+        im += s * std::sin(ph);
+      }
+    S[k] = (re * re + im * im) / (double)nb;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A run of n_steps steps starting at step t0.  Unless w_frozen is given, the
+// fields entering step t come from the counts after step t-1 (or after the
+// initial configuration).  Optional accumulators per step: occupancy counts
+// summed over steps, the joint cell histogram of two-bead chains, R_e^2 and
+// the accepted count.  Returns the total accepted count.
+// ---------------------------------------------------------------------------
+int64_t orc_run(const orc_desc* d, double* pos, uint32_t t0, int64_t n_steps,
+                const double* w_frozen, int n_threads, uint64_t* occ, uint64_t* pair_hist,
+                double* re2_trace, int64_t* acc_trace) {
+  const int64_t nc = n_cells(d);
+  std::vector<uint32_t> counts(2 * nc);
+  std::vector<double> w(2 * nc);
+  if (w_frozen) {
+    std::memcpy(w.data(), w_frozen, sizeof(double) * 2 * nc);
+  } else {
+    orc_density(d, pos, counts.data());
+    orc_fields(d, counts.data(), w.data());
+  }
+  int64_t total = 0;
+  for (int64_t s = 0; s < n_steps; ++s) {
+    int64_t a = orc_mc_step(d, pos, w.data(), (uint32_t)(t0 + s), nullptr, nullptr, nullptr,
+                            n_threads);
+    total += a;
+    if (acc_trace) acc_trace[s] = a;
+    if (!w_frozen || occ) orc_density(d, pos, counts.data());
+    if (!w_frozen) orc_fields(d, counts.data(), w.data());
+    if (occ)
+      for (int64_t c = 0; c < 2 * nc; ++c) occ[c] += counts[c];
+    if (pair_hist && d->N == 2)
+      for (int c = 0; c < d->n_poly; ++c) {
+        const double* p = pos + (int64_t)c * 6;
+        pair_hist[cell_of(d, p) * nc + cell_of(d, p + 3)] += 1;
+      }
+    if (re2_trace) {
+      double re2 = 0.0;
+      for (int c = 0; c < d->n_poly; ++c) {
+        const double* p = pos + (int64_t)c * d->N * 3;
+        for (int a = 0; a < 3; ++a) {
+          double v = p[3 * (d->N - 1) + a] - p[a];
+          re2 += v * v;
+        }
+      }
+      re2_trace[s] = re2 / d->n_poly;
+    }
+  }
+  return total;
+}
+
+}  // extern "C"

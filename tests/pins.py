@@ -1,0 +1,280 @@
+"""Pins of the oracle against facts that do not come from the oracle itself.
+
+Each ``pin_*`` function takes an oracle class (``oracle.Oracle`` or a build of
+a mutated copy of its source) and returns a list of failure strings; an empty
+list means the pin holds.  The facts used:
+
+* Philox4x32-10: an independent implementation (Triton's, on its CPU
+  interpreter) of the generator of Salmon et al. (SC'11).
+* Gaussian-chain statistics of the initial configuration and of the
+  chiN = kappaN = 0 dynamics: per-axis bond variance 1/(3(N-1)), <R_e^2> = 1,
+  <R_g^2> = (N+1)/(6N); the harmonic chain's Boltzmann law is stationary.
+* Acceptance at chiN = kappaN = 0: for a bead whose conditional position is
+  Gaussian, dE given the displacement d is normal with variance twice its mean,
+  so E[min(1, e^-dE)] = erfc(sqrt(mean)/2); averaged over the uniform cube.
+* One bead in a frozen field: cell occupancy proportional to exp(-w(c)).
+* An AB dimer on a 2^3 grid in a frozen field: the exact cell-pair law
+  P(c1, c2) ~ exp(-w_A(c1) - w_B(c2)) prod_axes K(c1_a, c2_a), with K the
+  Gaussian bond kernel integrated over a pair of periodic cells (erf sums).
+* Density counts: brute-force numpy binning and the bead-count invariants.
+* Fields: the exact central difference of the energy functional H_nb, and the
+  exchange field chiN (phiB - phiA)/N of an incompressible cell.
+* S(q) of ideal chains: (1/N) sum_ij s_i s_j exp(-q^2 |i-j| / (6(N-1))).
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import numpy as np
+from numpy.polynomial.legendre import leggauss
+from scipy.special import erf, erfc
+
+NTHREADS = max(1, min(8, os.cpu_count() or 1))
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _gl(a, b, n):
+    x, w = leggauss(n)
+    return 0.5 * (b - a) * x + 0.5 * (a + b), 0.5 * (b - a) * w
+
+
+def _check(fails, name, value, expect, tol):
+    if not (abs(value - expect) <= tol):
+        fails.append(f"{name}: got {value:.6g}, expected {expect:.6g} +- {tol:.3g}")
+
+
+# ---------------------------------------------------------------------------
+def pin_philox_triton(O, n=512, seed=12345):
+    rng = np.random.default_rng(seed)
+    ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    key[1] = 0xFFFFFFFF
+    with tempfile.TemporaryDirectory() as td:
+        pc, pk, po = (os.path.join(td, f) for f in ("c.npy", "k.npy", "o.npy"))
+        np.save(pc, ctr)
+        np.save(pk, key)
+        subprocess.check_call([sys.executable, os.path.join(HERE, "triton_philox_ref.py"), pc, pk, po])
+        ref = np.load(po)
+    got = O.philox(ctr, key)
+    bad = np.nonzero((got != ref).any(axis=1))[0]
+    return [f"philox differs from Triton's at {len(bad)} of {n} counters"] if len(bad) else []
+
+
+# ---------------------------------------------------------------------------
+def pin_init_statistics(O):
+    fails = []
+    n_poly, N = 8192, 16
+    o = O(n_poly, N, 8, (4.0, 4.0, 4.0), (16, 16, 16), 0.0, 0.0, seed=7)
+    pos = o.init().reshape(n_poly, N, 3)
+    b = np.diff(pos, axis=1)
+    nb = b.shape[0] * b.shape[1]
+    for a in range(3):
+        v = (b[:, :, a] ** 2).mean() * 3 * (N - 1)
+        _check(fails, f"bond variance axis {a} x 3(N-1)", v, 1.0, 5 * np.sqrt(2.0 / nb))
+    kurt = (b ** 4).mean() / ((b ** 2).mean() ** 2)
+    _check(fails, "bond kurtosis", kurt, 3.0, 0.05)
+    re2 = ((pos[:, -1] - pos[:, 0]) ** 2).sum(-1)
+    _check(fails, "<R_e^2>", re2.mean(), 1.0, 5 * np.sqrt(2.0 / 3.0 / n_poly))
+    cm = pos.mean(axis=1, keepdims=True)
+    rg2 = ((pos - cm) ** 2).sum(-1).mean(-1)
+    _check(fails, "<R_g^2>", rg2.mean(), (N + 1) / (6.0 * N), 5 * rg2.std() / np.sqrt(n_poly))
+    x0 = pos[:, 0]
+    if x0.min() < 0 or x0.max() >= 4.0:
+        fails.append("first bead outside the box")
+    for a in range(3):
+        _check(fails, f"first bead mean axis {a}", x0[:, a].mean(), 2.0, 5 * np.sqrt(16 / 12 / n_poly))
+    return fails
+
+
+# ---------------------------------------------------------------------------
+def _acceptance_ideal(N, A, kb, n=64):
+    x, w = _gl(0.0, A, n)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :] / A ** 3
+    D = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    a_int = float((W * erfc(D * np.sqrt(kb / 2.0))).sum())
+    a_end = float((W * erfc(D * np.sqrt(kb) / 2.0)).sum())
+    return ((N - 2) * a_int + 2 * a_end) / N
+
+
+def pin_ideal_dynamics(O, steps=120):
+    """chiN = kappaN = 0: equilibrium bond statistics persist and the
+    acceptance equals the Gaussian quadrature."""
+    fails = []
+    n_poly, N = 2048, 32
+    o = O(n_poly, N, 16, (4.0, 4.0, 4.0), (16, 16, 16), 0.0, 0.0, seed=3)
+    kb, A, _ = o.params()
+    pos = o.init()
+    res = o.run(pos, 0, steps, n_threads=NTHREADS, re2_trace=True, acc_trace=True)
+    acc = res["accepted"] / (o.n_b * steps)
+    expect = _acceptance_ideal(N, A, kb)
+    _check(fails, "acceptance vs quadrature", acc, expect, 5 * np.sqrt(expect * (1 - expect) / (o.n_b * steps)) + 2e-4)
+    p = pos.reshape(n_poly, N, 3)
+    b2 = (np.diff(p, axis=1) ** 2).sum(-1).mean() * (N - 1)
+    _check(fails, "<b^2>(N-1) after the run", b2, 1.0, 5 * np.sqrt(2.0 / 3.0 / (n_poly * (N - 1))))
+    _check(fails, "time-averaged <R_e^2>", res["re2"].mean(), 1.0, 5 * np.sqrt(2.0 / 3.0 / n_poly))
+    return fails
+
+
+# ---------------------------------------------------------------------------
+def _block_test(fails, name, samples, expect, zmax=5.5):
+    """samples: [blocks, states] normalised frequencies; compare to expect."""
+    mean = samples.mean(axis=0)
+    se = samples.std(axis=0, ddof=1) / np.sqrt(samples.shape[0])
+    se = np.maximum(se, 1e-12)
+    z = (mean - expect) / se
+    k = int(np.argmax(np.abs(z)))
+    if abs(z[k]) > zmax:
+        fails.append(f"{name}: state {k} freq {mean[k]:.5f} vs exact {expect[k]:.5f} (z={z[k]:.1f})")
+    rel = np.abs(mean - expect).max()
+    if rel > 0.01:
+        fails.append(f"{name}: max abs deviation {rel:.4f}")
+
+
+def pin_single_bead_field(O, blocks=16, per_block=15):
+    fails = []
+    rng = np.random.default_rng(11)
+    for n_A, t in ((1, 0), (0, 1)):
+        o = O(4096, 1, n_A, (1.0, 1.5, 2.0), (2, 3, 4), 0.0, 0.0, A=0.6, seed=5 + n_A)
+        w = rng.normal(0.0, 0.8, size=(2, o.n_c))
+        pos = o.init()
+        o.run(pos, 0, 10, w_frozen=w, n_threads=NTHREADS)  # burn-in from the uniform start
+        samples = []
+        for b in range(blocks):
+            r = o.run(pos, 10 + b * per_block, per_block, w_frozen=w, n_threads=NTHREADS, occ=True)
+            occ = r["occ"].reshape(2, o.n_c)[t].astype(np.float64)
+            samples.append(occ / occ.sum())
+        p = np.exp(-w[t])
+        _block_test(fails, f"single bead type {'AB'[t]} occupancy", np.array(samples), p / p.sum())
+    return fails
+
+
+# ---------------------------------------------------------------------------
+def _bond_cell_kernel(L, n, kb, nx=96, images=6):
+    """K[i, j] = int_{x in cell i} dx int db exp(-kb b^2) [x + b in cell j mod L]."""
+    h = L / n
+    K = np.zeros((n, n))
+    s = np.sqrt(kb)
+    for i in range(n):
+        x, wx = _gl(i * h, (i + 1) * h, nx)
+        for j in range(n):
+            tot = np.zeros_like(x)
+            for m in range(-images, images + 1):
+                y0, y1 = j * h + m * L, (j + 1) * h + m * L
+                tot += 0.5 * np.sqrt(np.pi / kb) * (erf(s * (y1 - x)) - erf(s * (y0 - x)))
+            K[i, j] = (wx * tot).sum()
+    return K
+
+
+def pin_dimer_cell_pairs(O, blocks=16, per_block=15):
+    fails = []
+    rng = np.random.default_rng(21)
+    box, grid = (1.0, 1.0, 1.0), (2, 2, 2)
+    o = O(4096, 2, 1, box, grid, 0.0, 0.0, seed=9)
+    kb, _, _ = o.params()
+    w = rng.normal(0.0, 0.7, size=(2, o.n_c))
+    Ks = [_bond_cell_kernel(box[a], grid[a], kb) for a in range(3)]
+    cells = [(ix, iy, iz) for ix in range(2) for iy in range(2) for iz in range(2)]
+    P = np.zeros((o.n_c, o.n_c))
+    for c1, (a1, b1, z1) in enumerate(cells):
+        for c2, (a2, b2, z2) in enumerate(cells):
+            P[c1, c2] = np.exp(-w[0, c1] - w[1, c2]) * Ks[0][a1, a2] * Ks[1][b1, b2] * Ks[2][z1, z2]
+    P /= P.sum()
+    pos = o.init()
+    o.run(pos, 0, 20, w_frozen=w, n_threads=NTHREADS)
+    samples = []
+    for b in range(blocks):
+        r = o.run(pos, 20 + b * per_block, per_block, w_frozen=w, n_threads=NTHREADS, pair_hist=True)
+        h = r["pair_hist"].astype(np.float64)
+        samples.append(h / h.sum())
+    _block_test(fails, "AB dimer cell-pair law", np.array(samples), P.reshape(-1))
+    return fails
+
+
+# ---------------------------------------------------------------------------
+def pin_density_bruteforce(O):
+    fails = []
+    rng = np.random.default_rng(31)
+    box, grid = (2.0, 3.0, 4.0), (8, 12, 16)
+    n_poly, N, n_A = 300, 10, 4
+    o = O(n_poly, N, n_A, box, grid, 0.0, 0.0, seed=1)
+    pos = rng.uniform(-7.0, 9.0, size=(o.n_b, 3))
+    pos[:5] = [[0.0, 0.0, 0.0], [2.0, 3.0, 4.0], [-2.0, -3.0, -4.0], [1.999999, 2.999999, 3.999999], [-1e-9, 0.25, 0.5]]
+    got = o.density(pos)
+    idx = []
+    for a in range(3):
+        xw = np.mod(pos[:, a], box[a])
+        i = np.floor(xw * (grid[a] / box[a])).astype(np.int64)
+        idx.append(np.clip(i, 0, grid[a] - 1))
+    cell = (idx[0] * grid[1] + idx[1]) * grid[2] + idx[2]
+    types = (np.arange(o.n_b) % N >= n_A).astype(np.int64)
+    ref = np.zeros((2, o.n_c), np.int64)
+    np.add.at(ref, (types, cell), 1)
+    if not np.array_equal(got.astype(np.int64), ref):
+        fails.append(f"density differs from brute force in {(got != ref).sum()} cells")
+    if got[0].sum() != n_poly * n_A or got[1].sum() != n_poly * (N - n_A):
+        fails.append("count sums differ from bead counts")
+    return fails
+
+
+def pin_fields_derivative(O):
+    fails = []
+    rng = np.random.default_rng(41)
+    o = O(64, 16, 5, (2.0, 2.0, 2.0), (4, 4, 4), 23.0, 47.0, seed=1)
+    counts = rng.integers(0, 40, size=(2, o.n_c)).astype(np.uint32)
+    w = o.fields(counts)
+    for t in range(2):
+        for c in rng.choice(o.n_c, 12, replace=False):
+            up, dn = counts.copy(), counts.copy()
+            up[t, c] += 1
+            dn[t, c] -= 1
+            fd = (o.energy_nb(up) - o.energy_nb(dn)) / 2.0
+            _check(fails, f"w[{t},{c}] vs dH/dn", w[t, c], fd, 1e-9 * max(1.0, abs(fd)) + 1e-9)
+    _, _, rho = o.params()
+    nA = rng.integers(0, 20, size=o.n_c)
+    phiA = nA / rho
+    inc = np.stack([phiA, 1.0 - phiA])
+    wi = o.fields_from_phi(inc)
+    _check(fails, "incompressible exchange field", float(np.abs((wi[0] - wi[1]) - 23.0 * (inc[1] - inc[0]) / 16).max()), 0.0, 1e-12)
+    return fails
+
+
+# ---------------------------------------------------------------------------
+def pin_structure_factor_ideal(O, seeds=12):
+    fails = []
+    n_poly, N, n_A, L = 2048, 16, 8, 4.0
+    ms = [(x, y, z) for x in range(-2, 3) for y in range(-2, 3) for z in range(-2, 3)
+          if 0 < x * x + y * y + z * z <= 6]
+    ms = np.array(ms, np.int32)
+    shells = (ms ** 2).sum(1)
+    s = np.where(np.arange(N) < n_A, 1.0, -1.0)
+    ij = np.abs(np.arange(N)[:, None] - np.arange(N)[None, :])
+    est = {k: [] for k in np.unique(shells)}
+    for sd in range(seeds):
+        o = O(n_poly, N, n_A, (L, L, L), (16, 16, 16), 0.0, 0.0, seed=100 + sd)
+        S = o.structure_factor(o.init(), ms)
+        for k in est:
+            est[k].append(S[shells == k].mean())
+    for k, v in est.items():
+        q2 = (2 * np.pi / L) ** 2 * k
+        exact = float((s[:, None] * s[None, :] * np.exp(-q2 * ij / (6.0 * (N - 1)))).sum() / N)
+        v = np.array(v)
+        se = v.std(ddof=1) / np.sqrt(len(v))
+        _check(fails, f"S(q) shell |m|^2={k}", v.mean(), exact, 5 * se)
+    return fails
+
+
+ALL_PINS = {
+    "philox_triton": pin_philox_triton,
+    "init_statistics": pin_init_statistics,
+    "ideal_dynamics": pin_ideal_dynamics,
+    "single_bead_field": pin_single_bead_field,
+    "dimer_cell_pairs": pin_dimer_cell_pairs,
+    "density_bruteforce": pin_density_bruteforce,
+    "fields_derivative": pin_fields_derivative,
+    "structure_factor_ideal": pin_structure_factor_ideal,
+}

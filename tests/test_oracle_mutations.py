@@ -1,0 +1,54 @@
+"""Plant plausible mistakes in a copy of the oracle source and check that the
+pins catch each one (CPU only).  The mistakes live only in a temporary copy;
+the oracle itself is never modified."""
+import os
+import subprocess
+import tempfile
+
+import pytest
+
+import pins
+from oracle import Oracle
+from oracle.oracle import _SRC
+
+# (name, text in soma_oracle.cpp, replacement, pin expected to catch it)
+MUTATIONS = [
+    ("bond constant doubled", "return 1.5 * (double)(d->N - 1);", "return 3.0 * (double)(d->N - 1);",
+     "ideal_dynamics"),
+    ("one-sided proposal", "A * (2.0 * unit_closed_open(r[a]) - 1.0)", "A * unit_closed_open(r[a])",
+     "ideal_dynamics"),
+    ("field term sign", "dE = k_b * dEb + wt[cell_of(d, rn)] - wt[cell_of(d, ri)];",
+     "dE = k_b * dEb - wt[cell_of(d, rn)] + wt[cell_of(d, ri)];", "single_bead_field"),
+    ("types swapped", "return i < d->n_A ? 0 : 1;", "return i < d->n_A ? 1 : 0;", "dimer_cell_pairs"),
+    ("right neighbour dropped", "for (int j = i - 1; j <= i + 1; j += 2)",
+     "for (int j = i - 1; j <= i - 1; j += 2)", "ideal_dynamics"),
+    ("acceptance inverted", "bool ok = margin < 0.0;", "bool ok = margin > 0.0;", "ideal_dynamics"),
+    ("cell axes transposed", "return (idx[0] * d->grid[1] + idx[1]) * d->grid[2] + idx[2];",
+     "return (idx[2] * d->grid[1] + idx[1]) * d->grid[0] + idx[0];", "density_bruteforce"),
+    ("uniform for ln u halved", "std::log(unit_open(r[3]))", "std::log(0.5 * unit_open(r[3]))",
+     "ideal_dynamics"),
+    ("chi term uses own type", "*wA = (d->chiN * phiB + d->kappaN * excess) / N;",
+     "*wA = (d->chiN * phiA + d->kappaN * excess) / N;", "fields_derivative"),
+    ("compressibility factor", "0.5 * d->kappaN * excess * excess", "d->kappaN * excess * excess",
+     "fields_derivative"),
+    ("philox key bump", "k1 += W1;", "k1 += W0;", "philox_triton"),
+    ("init bond variance", "std::sqrt(1.0 / (3.0 * (double)(d->N - 1)))",
+     "std::sqrt(1.0 / (2.0 * (double)(d->N - 1)))", "init_statistics"),
+    ("composition sign lost", "double s = type_of(d, i) == 0 ? 1.0 : -1.0;", "double s = 1.0;",
+     "structure_factor_ideal"),
+    ("bond of second bead anchored to bead 0", "p[3 * i + 0] = p[3 * (i - 1) + 0] + sigma * z0;",
+     "p[3 * i + 0] = p[0] + sigma * z0;", "init_statistics"),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_mutation(name, old, new, pin):
+    src = open(_SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique/found: {old}"
+    with tempfile.TemporaryDirectory() as td:
+        cpp = os.path.join(td, "mut.cpp")
+        so = os.path.join(td, "libmut.so")
+        open(cpp, "w").write(src.replace(old, new))
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", so, cpp])
+        fails = pins.ALL_PINS[pin](Oracle.with_library(so))
+    assert fails, f"pin {pin} did not catch the planted mistake '{name}'"
