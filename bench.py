@@ -1,0 +1,434 @@
+"""Throughput benchmark of the SCMF Monte Carlo step (bead moves per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config1]
+                    [--impl reference] [--no-batched] [--no-e2e]
+
+One JSON line on rank 0.  A step is one whole Monte Carlo step of every bead
+(move kernel with fused histogram, then field kernel, plus the periodic chain
+reorder when it falls due).  Inputs are resident in HBM; between timed steps
+a 256 MiB buffer (twice the L2) is written so every step starts from a cold
+L2; each step is bracketed by CUDA events on the library's stream and the
+move and field kernels by the library's own per-kernel events.
+
+``--impl reference`` times the plain FP64 CPU oracle on the same workload
+shape (a bounded sample of it) on the host cores instead.
+
+With N > 1 (torchrun), every rank runs its own replica of the workload on
+its own GPU (independent systems, no data-path collective): weak scaling.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "bead MC moves/s on 1xB300 and % of HBM roofline; batched vs plain speedup"
+UNIT = "moves/s"
+FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("soma_kernels.cu", "soma_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_09356_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload):
+    """DRAM bytes per launch of the move kernel from the committed ncu summary,
+    if that summary was taken from the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"k_move_bin_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != _kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_desc(name, c):
+    return (f"{name}: {c['n_poly']} AB diblocks N={c['N']} n_A={c['n_A']}, box {c['box'][0]:g}^3 R_e, "
+            f"grid {c['grid'][0]}^3, chiN={c['chiN']:g}, kappaN={c['kappaN']:g}, FP32 positions + int16 image")
+
+
+def algorithmic_bytes(n_b, n_c):
+    """Bytes the method must move per step: positions read and written
+    (24 B per bead-move) and per cell the counts written and read and the
+    fields written and read (32 B)."""
+    return 24 * n_b + 32 * n_c
+
+
+def move_kernel_bytes(n_b, n_c):
+    """Algorithmic bytes of one move-kernel launch: positions read + written
+    (24 B/bead), fields read (8 B/cell), counts written (8 B/cell)."""
+    return 24 * n_b + 16 * n_c
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(name, budget_s=12.0, steps_cap=None):
+    """The oracle as it stands, on the host cores, on a bounded sample: a
+    system of the workload's shape (same Delta, density, N, chiN, kappaN) with
+    the box shrunk until the sampled steps take about budget_s seconds."""
+    from oracle import Oracle
+    from paper_2606_09356_b300 import workloads
+    c = workloads.system_kwargs(name)
+    cores = os.cpu_count() or 1
+    # probe: rate on a small box of the same shape
+    L0, g0 = c["box"][0], c["grid"][0]
+    h = L0 / g0
+
+    def make(L):
+        g = int(round(L / h))
+        L = g * h
+        n_poly = max(1, int(round(c["n_poly"] * (L / L0) ** 3)))
+        return Oracle(n_poly, c["N"], c["n_A"], (L, L, L), (g, g, g), c["chiN"], c["kappaN"], seed=c["seed"])
+
+    probe = make(max(4.0, L0 / 4))
+    X = probe.init()
+    t = time.perf_counter()
+    probe.run(X, 0, 2, n_threads=cores)
+    rate = 2 * probe.n_b / (time.perf_counter() - t)
+    steps = 3 if steps_cap is None else steps_cap
+    target_beads = rate * budget_s / steps
+    L = min(L0, max(4.0, L0 * (target_beads / (c["n_poly"] * c["N"])) ** (1 / 3)))
+    o = make(L)
+    X = o.init()
+    t = time.perf_counter()
+    o.run(X, 0, steps, n_threads=cores)
+    dt = time.perf_counter() - t
+    sample = (f"{steps} full oracle steps (moves, re-binning, field rebuild) of a {o.n_b}-bead system of the "
+              f"{name} shape (box {o.d.box[0]:g}^3, grid {o.d.grid[0]}^3, same N, density, chiN, kappaN)")
+    return {"value": steps * o.n_b / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import Oracle
+    from paper_2606_09356_b300 import workloads
+    c = workloads.system_kwargs(args.workload)
+    cores = os.cpu_count() or 1
+    # bounded sample: shrink the box (same shape) so the K + W steps fit in ~2 minutes
+    probe = Oracle(max(1, c["n_poly"] // 64), c["N"], c["n_A"], tuple(b / 4 for b in c["box"]),
+                   tuple(g // 4 for g in c["grid"]), c["chiN"], c["kappaN"], seed=c["seed"])
+    X = probe.init()
+    t = time.perf_counter()
+    probe.run(X, 0, 1, n_threads=cores)
+    rate = probe.n_b / (time.perf_counter() - t)
+    total_steps = args.steps + args.warmup
+    frac = min(1.0, rate * 120.0 / (total_steps * c["n_poly"] * c["N"]))
+    L0, g0 = c["box"][0], c["grid"][0]
+    g = max(8, int(round(g0 * frac ** (1 / 3))))
+    L = L0 * g / g0
+    n_poly = max(1, int(round(c["n_poly"] * (g / g0) ** 3)))
+    o = Oracle(n_poly, c["N"], c["n_A"], (L, L, L), (g, g, g), c["chiN"], c["kappaN"], seed=c["seed"])
+    X = o.init()
+    o.run(X, 0, args.warmup, n_threads=cores)
+    t = time.perf_counter()
+    o.run(X, args.warmup, args.steps, n_threads=cores)
+    dt = time.perf_counter() - t
+    value = args.steps * o.n_b / dt
+    sample = (f"full oracle steps of a {o.n_b}-bead system of the {args.workload} shape (box {L:g}^3, grid {g}^3, "
+              f"same N, density, chiN, kappaN)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args.workload, c), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2606_09356_b300 import build as _build
+    from paper_2606_09356_b300 import soma, workloads
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+    if rank == 0:
+        _build.build()
+    if pg:
+        pg.barrier()
+    soma.load_library()
+
+    c = workloads.system_kwargs(args.workload)
+    system = soma.System(**{**c, "system_id": rank})
+    n_b, n_c = system.n_beads, system.n_cells
+    hbm_peak, peak_kind = _peaks()
+
+    # CPU baseline first (no GPU work in flight), rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.workload)
+
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    h = soma.Handle(system, device=local, kernel_timing=1, graph_steps=0)
+    sort_interval = h.info()["sort_interval"]
+    sptr = stream.cuda_stream
+
+    def one_step():
+        h.mc_steps(1, stream=sptr)
+
+    # warm-up
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    h.kernel_times(reset=True)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))          # evict the L2 between timed steps
+                ev[i][0].record(stream)
+            one_step()
+            with torch.cuda.stream(stream):
+                ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    kt = h.kernel_times(reset=True)
+    if pg:
+        t = torch.tensor([total_ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    moves = args.steps * n_b * ws
+    value = moves / (total_ms * 1e-3)
+    sorts = kt["reorder"][1]
+    launches = args.steps * 3 + sorts * 3  # move, field, step-counter advance; 3 own kernels per reorder
+
+    # dominant kernel: the move kernel (its average launch duration)
+    mv_ms, mv_n = kt["move"]
+    fd_ms, fd_n = kt["field"]
+    move_avg = mv_ms / max(1, mv_n)
+    achieved = move_kernel_bytes(n_b, n_c) / (move_avg * 1e-3) / 1e9
+    traffic = _profiled_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "k_move_bin", "move_ms": move_avg, "field_ms": fd_ms / max(1, fd_n),
+                "step_frac": algorithmic_bytes(n_b, n_c) * args.steps / (total_ms * 1e-3) / 1e9 / hbm_peak}
+
+    # steady state without flushes: CUDA-graph replay of many steps (L2-warm)
+    steady = None
+    if not args.no_steady:
+        hg = soma.Handle(soma.System(**{**c, "system_id": rank}), device=local)
+        hg.mc_steps(args.warmup + 16, stream=sptr)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_st = max(args.steps, 64)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+        hg.mc_steps(n_st, stream=sptr)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        steady = {"value": n_st * n_b / (ms * 1e-3), "unit": UNIT, "steps": n_st,
+                  "note": "CUDA-graph replay, no L2 flush between steps, reorder every "
+                          f"{hg.info()['sort_interval']} steps"}
+        hg.close()
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pos, img, step = h.get_state()
+        pin_pos = torch.from_numpy(pos).pin_memory()
+        pin_img = torch.from_numpy(img).pin_memory()
+        dens = torch.empty((2, n_c), dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.set_state(pin_pos.numpy(), pin_img.numpy(), step)
+        acc = 0
+        for _ in range(args.steps):
+            h.mc_steps(1, stream=sptr)
+            acc = h.accepted()                   # the step's result, 8 bytes to the host
+        h.get_density(out=dens.numpy().view(np.uint32))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h2d = (pos.nbytes + img.nbytes) / args.steps
+        d2h = 8 + dens.numel() * 4 / args.steps
+        e2e = {"value": args.steps * n_b * ws / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "note": "set_state from pinned host, per step soma_mc_steps + soma_get_accepted, "
+                       "then soma_get_density to pinned host; host wall clock"}
+        _ = acc
+
+    # batched replicas vs sequential plain runs of the same 64 systems
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = bench_batched(soma, workloads, torch, sptr, stream, steps=args.batched_steps)
+    h.close()
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, c), "n_beads": n_b, "n_cells": n_c,
+                       "l2": "flushed between timed steps (256 MiB write)", "sort_interval": sort_interval,
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "steady_state": steady, "batched": batched,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(out))
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def bench_batched(soma, workloads, torch, sptr, stream, steps=20):
+    """Aggregate moves/s of the 64-system batch in one handle (one launch per
+    kernel per step for all systems, CUDA graphs) against the same systems run
+    one after another, each in its own handle (create excluded)."""
+    specs = workloads.batch64()
+    systems = [soma.System(**{k: v for k, v in d.items() if k != "f_A"}) for d in specs]
+    moves = sum(s.n_beads for s in systems) * steps
+    hb = soma.Handle(systems)
+    hb.mc_steps(4, stream=sptr)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+    hb.mc_steps(steps, stream=sptr)
+    with torch.cuda.stream(stream):
+        b.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = a.elapsed_time(b)
+    hb.close()
+    plain_ms = 0.0
+    for s in systems:
+        h = soma.Handle(s, graph_steps=0)
+        h.mc_steps(2, stream=sptr)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            a.record(stream)
+        for _ in range(steps):
+            h.mc_steps(1, stream=sptr)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        torch.cuda.synchronize()
+        plain_ms += a.elapsed_time(b)
+        h.close()
+    return {"value": moves / (batched_ms * 1e-3), "plain_sequential": moves / (plain_ms * 1e-3),
+            "speedup": plain_ms / batched_ms, "unit": UNIT, "systems": len(systems), "steps": steps,
+            "beads": sum(s.n_beads for s in systems)}
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--workload", default="config1")
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batched-steps", type=int, default=20)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-steady", action="store_true")
+    args = p.parse_args()
+    if args.warmup < 3:
+        p.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

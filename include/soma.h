@@ -1,0 +1,209 @@
+/* soma.h -- C ABI of the B300 single-chain-in-mean-field Monte Carlo library.
+ *
+ * The library runs the SCMF Monte Carlo step of a soft coarse-grained AB
+ * polymer melt on one GPU (the particle model of Sec. 2 of the paper, the
+ * SOMA paragraph; its two dominant kernels, the bead-move kernel and the
+ * density-field update, are the ones Sec. 2.2 profiles).  One step is:
+ *
+ *   (a) every bead proposes a uniform displacement d in [-A, A]^3 and is
+ *       Metropolis-accepted against its two harmonic bonds, k_b = 3(N-1)/2,
+ *       and the frozen per-cell field w_type; even beads of every chain move
+ *       first, then odd beads (the two sets share no bond);
+ *   (b) the final positions are re-binned into integer counts n_A(c), n_B(c);
+ *   (c) the fields are rebuilt per cell from phi_t = n_t / rho_bar:
+ *       w_A = [chiN phi_B + kappaN (phi_A + phi_B - 1)] / N, w_B likewise
+ *       with phi_A in the chi term.
+ *
+ * Units: R_e = 1, kT = 1.  Random numbers: Philox4x32-10 (Salmon et al.,
+ * SC'11) with counter (bead, logical chain, step, system_id) and key = seed,
+ * so a trajectory does not depend on chain storage order or launch shape.
+ *
+ * Conventions for every call below:
+ *   - The return value is SOMA_OK (0) or a negative SOMA_E* code; nothing
+ *     else signals an error and no C++ exception crosses this boundary.  A
+ *     handle keeps the first error it met (soma_last_error); once a CUDA
+ *     error has occurred every later call on that handle returns SOMA_ESTATE.
+ *   - The library owns all device memory it allocates (through the optional
+ *     allocator in soma_options, else cudaMalloc).  Buffers passed in are
+ *     owned by the caller; `where` says whether a pointer is host memory
+ *     (SOMA_HOST) or device memory on the handle's GPU (SOMA_DEVICE).
+ *   - Work is enqueued on the caller's CUDA stream (NULL = the handle's own
+ *     stream).  Calls that return data to the host synchronise that stream.
+ *   - Layouts: positions [bead][xyz] with bead = chain * N + i in LOGICAL
+ *     chain order; counts and fields [type][cell], type 0 = A, 1 = B;
+ *     cell = (ix * ny + iy) * nz + iz.
+ *   - Positions are stored as FP32 wrapped into [0, L) plus an int16 image
+ *     count per axis (unwrapped = x + image * L).  Bond vectors are taken by
+ *     the minimum-image rule, so the box must exceed twice any bond length:
+ *     soma_create rejects boxes with L < 16 / sqrt(3 (N - 1)) (eight bond
+ *     standard deviations either way).
+ */
+#ifndef SOMA_H
+#define SOMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SOMA_OK 0
+#define SOMA_EINVAL (-1)        /* bad argument or descriptor */
+#define SOMA_ENOMEM (-2)        /* device or host allocation failed */
+#define SOMA_ECUDA (-3)         /* a CUDA runtime call failed */
+#define SOMA_ETIMEOUT (-4)      /* a bounded device-side wait ran out */
+#define SOMA_EDEVICE_CHECK (-5) /* a device-side consistency check failed */
+#define SOMA_ESTATE (-6)        /* handle already in a failed state */
+#define SOMA_ENOTSUP (-7)       /* valid request this build does not support */
+
+#define SOMA_HOST 0
+#define SOMA_DEVICE 1
+
+/* Histogram strategies of kernel (b) (soma_options.hist_mode). */
+#define SOMA_HIST_AUTO 0
+#define SOMA_HIST_FUSED 1     /* binned in the epilogue of the move kernel */
+#define SOMA_HIST_SEPARATE 2  /* separate histogram kernel after the moves */
+
+/* One system: an AB diblock melt A_{n_A} B_{N - n_A} in a periodic box. */
+typedef struct soma_system_desc {
+  int32_t n_poly;  /* chains, >= 1 */
+  int32_t N;       /* beads per chain, 1 <= N <= 4096 */
+  int32_t n_A;     /* beads 0 .. n_A-1 of a chain are type A, 0 <= n_A <= N */
+  int32_t system_id; /* fourth Philox counter word; systems that share a seed
+                        need distinct ids.  A system's trajectory depends on
+                        (seed, system_id) only, not on its place in a batch. */
+  int32_t grid[3]; /* cells per axis, >= 1 each; total cells < 2^31 */
+  int32_t reserved1;
+  double box[3];   /* box edges in R_e */
+  double chiN;     /* Flory-Huggins chi times N */
+  double kappaN;   /* Helfand compressibility kappa times N */
+  double A;        /* proposal half-width; <= 0 selects 0.5 / sqrt(N - 1) */
+  uint64_t seed;   /* Philox key */
+} soma_system_desc;
+
+typedef void* (*soma_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*soma_free_fn)(void* ptr, void* ctx);
+
+typedef struct soma_options {
+  int32_t device;        /* CUDA device ordinal; -1 = the current device */
+  int32_t sort_interval; /* steps between chain reorders; 0 = never; -1 = tuned */
+  int32_t block_threads; /* move-kernel CTA size (multiple of 32, <= 1024); 0 = tuned */
+  int32_t hist_mode;     /* SOMA_HIST_* */
+  int32_t graph_steps;   /* steps per captured CUDA graph; 0 = plain launches */
+  int32_t kernel_timing; /* 1 = record CUDA events around each kernel (plain launches) */
+  int32_t autotune;      /* 1 = time candidate shapes on the first soma_mc_steps */
+  int32_t reserved;
+  soma_alloc_fn alloc;   /* optional device allocator, with free and ctx */
+  soma_free_fn free;
+  void* alloc_ctx;
+} soma_options;
+
+typedef struct soma_obs {
+  uint64_t step;      /* MC steps done */
+  uint64_t accepted;  /* accepted moves since creation or the last set_state */
+  uint64_t attempted; /* attempted moves over the same span */
+  double acc;         /* accepted / attempted (0 if none) */
+  double Re2;         /* mean over chains of |r_{N-1} - r_0|^2, unwrapped, FP64 sum */
+  double Rg2;         /* mean over chains of (1/N) sum |r_i - r_cm|^2 */
+  double Ebond;       /* k_b sum over bonds |b|^2 */
+  double Enb;         /* (n_poly / n_c) sum_c [chiN phiA phiB + (kappaN/2)(phiA + phiB - 1)^2] */
+} soma_obs;
+
+typedef struct soma_info {
+  int64_t n_beads, n_cells;
+  double k_b;       /* 3 (N - 1) / 2 */
+  double A;         /* proposal half-width actually used (FP32 value) */
+  double rho_bar;   /* n_beads / n_cells */
+  int32_t lanes_per_chain; /* move-kernel lanes per chain (0 = generic path) */
+  int32_t block_threads;   /* move-kernel CTA size in use */
+  int32_t sort_interval;   /* reorder interval in use */
+  int32_t hist_mode;       /* histogram strategy in use */
+} soma_info;
+
+typedef struct soma_handle soma_handle;
+
+/* Fill *opt with defaults (device -1, tuned sort interval and block size,
+ * SOMA_HIST_AUTO, graphs of 16 steps, no timing, no autotune). */
+int soma_options_default(soma_options* opt);
+
+/* Create a handle for n_sys independent systems that always step together
+ * (each with its own descriptor, seed and system_id s).
+ * Validates every descriptor, allocates device memory, builds the initial
+ * configuration on the GPU (bead 0 uniform in the box, bonds Gaussian with
+ * per-axis variance 1/(3(N-1)), Philox counter (bead, chain, 0xFFFFFFFF,
+ * system_id)),
+ * bins it, builds the fields and sorts the chains.  opt may be NULL. */
+int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
+                soma_handle** out);
+void soma_destroy(soma_handle* h);
+const char* soma_strerror(int code);
+int soma_last_error(const soma_handle* h);
+
+/* Enqueue n_steps MC steps of every system on `stream` (cudaStream_t, NULL =
+ * the handle's stream).  Asynchronous.  Steps are numbered from the current
+ * step counter; the step counter must stay below 2^32 - 1. */
+int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream);
+
+/* Wait for the handle's work and check the device error word. */
+int soma_sync(soma_handle* h, void* stream);
+
+/* Density counts of the current configuration, [2][n_cells] uint32. */
+int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where);
+
+/* Fields used by the next step, [2][n_cells] FP32. */
+int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where);
+
+/* Coupling write: replace the fields of the next step by those of the given
+ * volume fractions phi [2][n_cells] (FP32); later steps rebuild from counts.
+ * (Sec. 3.2: the particle run is handed the continuum's concentrations.) */
+int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int where);
+
+/* Test mode: hold the fields at w [2][n_cells] (FP32) for every later step
+ * (w == NULL releases them and rebuilds from the current counts). */
+int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int where);
+
+/* Checkpoint: positions [n_beads][3] FP32 wrapped into [0, L), images
+ * [n_beads][3] int16, and the step counter, in logical chain order. */
+int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* step, int where);
+/* Restore: positions must lie in [0, L) per axis; resets the acceptance
+ * counters and re-bins; the step counter is shared by all systems. */
+int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img, uint64_t step,
+                   int where);
+
+/* FP64 observables of the current configuration. */
+int soma_observables(soma_handle* h, int sys, soma_obs* out);
+/* Accepted-move counter only (one small device-to-host read). */
+int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted);
+
+/* S(q) = (1/n_beads) |sum_j s_j exp(i q.r_j)|^2, s_j = +1 (A) / -1 (B), for
+ * q = 2 pi m / L at the nq integer triples m_xyz [nq][3]; S is FP64 [nq]. */
+int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz, double* S);
+
+/* Reorder the chains of every system now (storage order only; the
+ * trajectory is unchanged because random numbers follow logical ids). */
+int soma_reorder(soma_handle* h, void* stream);
+
+/* Shape and tuning facts of one system. */
+int soma_get_info(soma_handle* h, int sys, soma_info* out);
+
+/* With kernel_timing = 1: accumulated milliseconds and launch counts of the
+ * move kernel, the separate histogram kernel, the field kernel and the
+ * reorder since the last reset (ms[4], launches[4]).  Synchronises. */
+int soma_kernel_times(soma_handle* h, double* ms, int64_t* launches, int reset);
+
+/* Run the autotuner now (also run by the first soma_mc_steps when
+ * opt.autotune = 1).  The state is saved and restored, so the trajectory is
+ * unchanged.  Synchronises. */
+int soma_autotune(soma_handle* h);
+
+/* The library's device Philox4x32-10 on n counters: ctr [n][4], key [n][2],
+ * out [n][4], all uint32 host buffers (a verification aid; it runs the same
+ * device function the move kernel uses).  Synchronous. */
+int soma_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOMA_H */

@@ -87,6 +87,9 @@ class Oracle:
             L.orc_fields_from_phi.argtypes = [dp, f64p, f64p]
             L.orc_mc_step.argtypes = [dp, f64p, f64p, ctypes.c_uint32, u8p, f64p, f64p, ctypes.c_int]
             L.orc_mc_step.restype = ctypes.c_int64
+            L.orc_mc_step_chains.argtypes = [dp, f64p, u32p, ctypes.c_int64, f64p, ctypes.c_uint32, u8p, f64p,
+                                             f64p, ctypes.c_int]
+            L.orc_mc_step_chains.restype = ctypes.c_int64
             L.orc_observables.argtypes = [dp, f64p, ctypes.POINTER(OrcObs)]
             L.orc_structure_factor.argtypes = [dp, f64p, ctypes.c_int, i32p, f64p]
             L.orc_run.argtypes = [dp, f64p, ctypes.c_uint32, ctypes.c_int64, f64p, ctypes.c_int,
@@ -153,6 +156,21 @@ class Oracle:
         n = self.lib().orc_mc_step(ctypes.byref(self.d), _p(pos, ctypes.c_double), _p(w, ctypes.c_double),
                                    ctypes.c_uint32(t & 0xFFFFFFFF), _p(acc, ctypes.c_uint8),
                                    _p(margin, ctypes.c_double), _p(face, ctypes.c_double), n_threads)
+        return n, acc, margin, face
+
+    def mc_step_chains(self, pos, ids, w, t, n_threads=1):
+        """One step of the chains with logical ids ``ids`` (pos [len(ids)*N, 3], in place)."""
+        assert pos.dtype == np.float64 and pos.flags.c_contiguous
+        ids = np.ascontiguousarray(ids, np.uint32)
+        w = np.ascontiguousarray(w, np.float64)
+        nb = len(ids) * self.d.N
+        acc = np.zeros(nb, np.uint8)
+        margin = np.zeros(nb, np.float64)
+        face = np.zeros(nb, np.float64)
+        n = self.lib().orc_mc_step_chains(ctypes.byref(self.d), _p(pos, ctypes.c_double), _p(ids, ctypes.c_uint32),
+                                          len(ids), _p(w, ctypes.c_double), ctypes.c_uint32(t & 0xFFFFFFFF),
+                                          _p(acc, ctypes.c_uint8), _p(margin, ctypes.c_double),
+                                          _p(face, ctypes.c_double), n_threads)
         return n, acc, margin, face
 
     def run(self, pos, t0, n_steps, w_frozen=None, n_threads=1, occ=False, pair_hist=False,

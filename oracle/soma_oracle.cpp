@@ -267,18 +267,20 @@ void orc_fields_from_phi(const orc_desc* d, const double* phi, double* w) {
 // smaller distance of r and r' to a cell face.  Returns the accepted count.
 // ---------------------------------------------------------------------------
 static int64_t move_set(const orc_desc* d, double* pos, const double* w, uint32_t t, int set,
-                        uint8_t* acc_out, double* margin_out, double* face_out, int n_threads) {
+                        const uint32_t* ids, int64_t n_chains, uint8_t* acc_out, double* margin_out,
+                        double* face_out, int n_threads) {
   const int64_t nc = n_cells(d);
   const double k_b = bond_k(d);
   const double A = proposal_A(d);
   const int N = d->N;
   int64_t accepted = 0;
 #pragma omp parallel for schedule(static) reduction(+ : accepted) num_threads(n_threads)
-  for (int c = 0; c < d->n_poly; ++c) {
-    double* p = pos + (int64_t)c * N * 3;
+  for (int64_t c = 0; c < n_chains; ++c) {
+    double* p = pos + c * N * 3;
+    const uint32_t chain = ids ? ids[c] : (uint32_t)c;
     for (int i = set; i < N; i += 2) {
       uint32_t r[4];
-      draw(d, (uint32_t)i, (uint32_t)c, t, r);
+      draw(d, (uint32_t)i, chain, t, r);
       double* ri = p + 3 * i;
       double rn[3];
       for (int a = 0; a < 3; ++a) rn[a] = ri[a] + A * (2.0 * unit_closed_open(r[a]) - 1.0);
@@ -297,7 +299,7 @@ static int64_t move_set(const orc_desc* d, double* pos, const double* w, uint32_
       double dE = k_b * dEb + wt[cell_of(d, rn)] - wt[cell_of(d, ri)];
       double margin = dE + std::log(unit_open(r[3]));
       bool ok = margin < 0.0;
-      int64_t b = (int64_t)c * N + i;
+      int64_t b = c * N + i;
       if (acc_out) acc_out[b] = ok ? 1 : 0;
       if (margin_out) margin_out[b] = margin;
       if (face_out) face_out[b] = std::fmin(face_distance(d, ri), face_distance(d, rn));
@@ -313,8 +315,21 @@ static int64_t move_set(const orc_desc* d, double* pos, const double* w, uint32_
 int64_t orc_mc_step(const orc_desc* d, double* pos, const double* w, uint32_t t, uint8_t* acc_out,
                     double* margin_out, double* face_out, int n_threads) {
   if (n_threads < 1) n_threads = 1;
-  int64_t a0 = move_set(d, pos, w, t, 0, acc_out, margin_out, face_out, n_threads);
-  int64_t a1 = move_set(d, pos, w, t, 1, acc_out, margin_out, face_out, n_threads);
+  int64_t a0 = move_set(d, pos, w, t, 0, nullptr, d->n_poly, acc_out, margin_out, face_out, n_threads);
+  int64_t a1 = move_set(d, pos, w, t, 1, nullptr, d->n_poly, acc_out, margin_out, face_out, n_threads);
+  return a0 + a1;
+}
+
+// The same step for a sample of chains only: pos holds n_chains chains whose
+// logical ids (the Philox chain word) are ids[]; w is the full system's field.
+// Chains interact only through the frozen fields, so a sample moves exactly
+// as it would inside the whole system.
+int64_t orc_mc_step_chains(const orc_desc* d, double* pos, const uint32_t* ids, int64_t n_chains,
+                           const double* w, uint32_t t, uint8_t* acc_out, double* margin_out,
+                           double* face_out, int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  int64_t a0 = move_set(d, pos, w, t, 0, ids, n_chains, acc_out, margin_out, face_out, n_threads);
+  int64_t a1 = move_set(d, pos, w, t, 1, ids, n_chains, acc_out, margin_out, face_out, n_threads);
   return a0 + a1;
 }
 

@@ -1,0 +1,947 @@
+// soma_api.cu -- the C ABI of include/soma.h: handle life cycle, step
+// scheduling (plain launches or CUDA-graph replay), state I/O, observables,
+// reorder scheduling, per-kernel timing and the autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/soma.h"
+#include "soma_internal.cuh"
+#include "soma_launch.h"
+
+using namespace soma;
+
+namespace {
+
+constexpr int64_t kCellsPerTile = 8192;  // multiple of 4 (vectorised field kernel)
+constexpr int kDefaultThreads = 256;
+constexpr int kDefaultSortInterval = 200;
+constexpr int kDefaultGraphSteps = 16;
+enum { T_MOVE = 0, T_BIN = 1, T_FIELD = 2, T_SORT = 3 };
+
+struct TimedEvent {
+  cudaEvent_t a, b;
+  int kind;
+};
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+struct soma_handle {
+  int device = 0, sm_count = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // dedicated stream for graph capture
+  soma_options opt{};
+  int n_sys = 0;
+  std::vector<soma_system_desc> desc;
+  std::vector<SysDev> host_sys;  // pointers as allocated (device copies may be swapped by reorders)
+  SysDev* d_sys = nullptr;
+  std::vector<void*> owned;
+  // launch geometry
+  int threads = kDefaultThreads;
+  int hist_mode = SOMA_HIST_FUSED;
+  int sort_interval = kDefaultSortInterval;
+  std::vector<MoveTile> move_tiles;
+  MoveTile* d_move_tiles = nullptr;
+  int n_move_tiles = 0, move_tiles_cap = 0;
+  std::vector<CellTile> cell_tiles;
+  CellTile* d_cell_tiles = nullptr;
+  std::vector<int> generic_sys;  // systems with N > 64
+  int64_t acc_slots = 0;
+  unsigned long long* d_acc = nullptr;
+  // step counter (device base + host mirror of enqueued steps)
+  unsigned long long* d_step = nullptr;
+  uint64_t step = 0;
+  uint64_t acc_since = 0;  // step at which the acceptance counters were last cleared
+  uint64_t steps_since_sort = 0;
+  int* d_err = nullptr;
+  double* d_obs = nullptr;
+  unsigned long long* d_acc_sum = nullptr;
+  int32_t* d_m = nullptr;
+  int m_cap = 0;
+  double* d_sq = nullptr;
+  float* d_stage_pos = nullptr;
+  int16_t* d_stage_img = nullptr;
+  float* d_stage_phi = nullptr;
+  int64_t max_nb = 0, max_nc = 0;
+  SortWork sort{};
+  // graph
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  // timing
+  std::vector<TimedEvent> pending;
+  double ms[4] = {0, 0, 0, 0};
+  int64_t launches[4] = {0, 0, 0, 0};
+  bool tuned = false;
+  int sticky = SOMA_OK;
+};
+
+namespace {
+
+int fail(soma_handle* h, int code) {
+  if (h && h->sticky == SOMA_OK) h->sticky = code;
+  return code;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      if (getenv("SOMA_VERBOSE"))                                                        \
+        fprintf(stderr, "soma: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), \
+                __FILE__, __LINE__);                                                    \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? SOMA_ENOMEM : SOMA_ECUDA);       \
+    }                                                                                   \
+  } while (0)
+
+void* dev_alloc(soma_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (h->opt.alloc) {
+    p = h->opt.alloc(bytes, h->opt.alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) h->owned.push_back(p);
+  return p;
+}
+
+void dev_free_all(soma_handle* h) {
+  for (void* p : h->owned) {
+    if (h->opt.free)
+      h->opt.free(p, h->opt.alloc_ctx);
+    else
+      cudaFree(p);
+  }
+  h->owned.clear();
+}
+
+cudaStream_t pick(soma_handle* h, void* stream) { return stream ? (cudaStream_t)stream : h->stream; }
+
+int check_live(const soma_handle* h) {
+  if (!h) return SOMA_EINVAL;
+  if (h->sticky != SOMA_OK) return SOMA_ESTATE;
+  return SOMA_OK;
+}
+
+int validate_desc(const soma_system_desc& d) {
+  if (d.n_poly < 1 || d.N < 1 || d.N > 4096 || d.n_A < 0 || d.n_A > d.N) return SOMA_EINVAL;
+  if ((int64_t)d.n_poly * d.N > (int64_t)INT32_MAX) return SOMA_EINVAL;
+  int64_t nc = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (d.grid[a] < 1 || !(d.box[a] > 0.0) || !std::isfinite(d.box[a])) return SOMA_EINVAL;
+    nc *= d.grid[a];
+  }
+  if (nc >= (int64_t)INT32_MAX) return SOMA_EINVAL;
+  if (!std::isfinite(d.chiN) || !std::isfinite(d.kappaN) || !std::isfinite(d.A)) return SOMA_EINVAL;
+  if (d.N == 1 && !(d.A > 0.0)) return SOMA_EINVAL;  // no default half-width without bonds
+  if (d.N > 1) {
+    const double min_box = 16.0 / std::sqrt(3.0 * (d.N - 1));  // 2 x 8 bond standard deviations
+    for (int a = 0; a < 3; ++a)
+      if (d.box[a] < min_box) return SOMA_EINVAL;
+  }
+  const double A = d.A > 0 ? d.A : 0.5 / std::sqrt((double)(d.N - 1));
+  for (int a = 0; a < 3; ++a)
+    if (A >= d.box[a]) return SOMA_EINVAL;  // a proposal must wrap at most once
+  return SOMA_OK;
+}
+
+// Move tiles: each CTA takes (threads/32) * (32/P) consecutive chains of one
+// register-path system; generic systems get one accumulator slot each.
+int build_tiles(soma_handle* h) {
+  h->move_tiles.clear();
+  h->generic_sys.clear();
+  int acc = 0;
+  for (int s = 0; s < h->n_sys; ++s) {
+    SysDev& S = h->host_sys[s];
+    S.acc_first = acc;
+    if (S.P == 0) {
+      h->generic_sys.push_back(s);
+      S.acc_count = 1;
+      acc += 1;
+      continue;
+    }
+    const int per_cta = (h->threads / 32) * (32 / S.P);
+    int count = 0;
+    for (int first = 0; first < S.n_poly; first += per_cta) {
+      MoveTile t;
+      t.sys = s;
+      t.first_chain = first;
+      t.n_chains = std::min(per_cta, S.n_poly - first);
+      t.acc_index = acc++;
+      h->move_tiles.push_back(t);
+      ++count;
+    }
+    S.acc_count = count;
+  }
+  h->n_move_tiles = (int)h->move_tiles.size();
+  return acc;
+}
+
+int upload_tiles(soma_handle* h) {
+  if (h->n_move_tiles > h->move_tiles_cap) {
+    h->d_move_tiles = (MoveTile*)dev_alloc(h, sizeof(MoveTile) * h->n_move_tiles);
+    if (!h->d_move_tiles) return fail(h, SOMA_ENOMEM);
+    h->move_tiles_cap = h->n_move_tiles;
+  }
+  if (h->n_move_tiles)
+    CK(cudaMemcpyAsync(h->d_move_tiles, h->move_tiles.data(), sizeof(MoveTile) * h->n_move_tiles,
+                       cudaMemcpyHostToDevice, h->stream));
+  return SOMA_OK;
+}
+
+// Update only the accumulator ranges of the device-side system table (its
+// array pointers may have been swapped by reorders).
+__global__ void k_set_acc_ranges(SysDev* systems, const int2* ranges, int n) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) {
+    systems[s].acc_first = ranges[s].x;
+    systems[s].acc_count = ranges[s].y;
+  }
+}
+
+int rebuild_geometry(soma_handle* h, int threads) {
+  h->threads = threads;
+  const int acc = build_tiles(h);
+  if (acc > h->acc_slots) return fail(h, SOMA_EINVAL);
+  int rc = upload_tiles(h);
+  if (rc) return rc;
+  std::vector<int2> ranges(h->n_sys);
+  for (int s = 0; s < h->n_sys; ++s) ranges[s] = make_int2(h->host_sys[s].acc_first, h->host_sys[s].acc_count);
+  int2* d_ranges = (int2*)h->d_stage_phi;  // scratch: stage buffer is at least n_sys * 8 bytes
+  CK(cudaMemcpyAsync(d_ranges, ranges.data(), sizeof(int2) * h->n_sys, cudaMemcpyHostToDevice, h->stream));
+  k_set_acc_ranges<<<(h->n_sys + 63) / 64, 64, 0, h->stream>>>(h->d_sys, d_ranges, h->n_sys);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * h->acc_slots, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return SOMA_OK;
+}
+
+void begin_timed(soma_handle* h, cudaStream_t s, TimedEvent& te, int kind) {
+  te.kind = kind;
+  cudaEventCreate(&te.a);
+  cudaEventCreate(&te.b);
+  cudaEventRecord(te.a, s);
+}
+void end_timed(soma_handle* h, cudaStream_t s, TimedEvent& te) {
+  cudaEventRecord(te.b, s);
+  h->pending.push_back(te);
+}
+
+// Enqueue step `offset` (relative to the device step base) of every system.
+int enqueue_step(soma_handle* h, cudaStream_t s, int offset) {
+  const bool timing = h->opt.kernel_timing != 0;
+  TimedEvent te;
+  const int fused = h->hist_mode == SOMA_HIST_FUSED;
+  if (timing) begin_timed(h, s, te, T_MOVE);
+  if (h->n_move_tiles)
+    CK(launch_move_bin(h->d_sys, h->d_move_tiles, h->n_move_tiles, h->threads, h->d_step, offset, fused, s));
+  for (int g : h->generic_sys)
+    CK(launch_move_generic(h->d_sys, g, h->host_sys[g].n_poly, h->host_sys[g].N, h->d_step, offset, h->sm_count, s));
+  if (timing) {
+    end_timed(h, s, te);
+    h->launches[T_MOVE] += 1;
+  }
+  bool any_bin = false;
+  for (int g = 0; g < h->n_sys; ++g) any_bin |= (!fused || h->host_sys[g].P == 0);
+  if (any_bin) {
+    if (timing) begin_timed(h, s, te, T_BIN);
+    for (int g = 0; g < h->n_sys; ++g)
+      if (!fused || h->host_sys[g].P == 0)
+        CK(launch_bin(h->d_sys, g, h->host_sys[g].n_b, h->d_step, offset, h->sm_count, s));
+    if (timing) {
+      end_timed(h, s, te);
+      h->launches[T_BIN] += 1;
+    }
+  }
+  if (timing) begin_timed(h, s, te, T_FIELD);
+  CK(launch_field(h->d_sys, h->d_cell_tiles, (int)h->cell_tiles.size(), h->d_step, offset, s));
+  if (timing) {
+    end_timed(h, s, te);
+    h->launches[T_FIELD] += 1;
+  }
+  return SOMA_OK;
+}
+
+int enqueue_reorder(soma_handle* h, cudaStream_t s) {
+  TimedEvent te;
+  if (h->opt.kernel_timing) begin_timed(h, s, te, T_SORT);
+  CK(launch_reorder(h->d_sys, h->n_sys, h->sort, h->sm_count, s));
+  if (h->opt.kernel_timing) {
+    end_timed(h, s, te);
+    h->launches[T_SORT] += 1;
+  }
+  h->steps_since_sort = 0;
+  return SOMA_OK;
+}
+
+int capture_graph(soma_handle* h, int steps) {
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  cudaStream_t cs = h->cap_stream;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  int rc = SOMA_OK;
+  for (int i = 0; i < steps && rc == SOMA_OK; ++i) rc = enqueue_step(h, cs, i);
+  if (rc == SOMA_OK && launch_advance(h->d_step, steps, cs) != cudaSuccess) rc = SOMA_ECUDA;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (rc != SOMA_OK) {
+    if (g) cudaGraphDestroy(g);
+    return fail(h, rc);
+  }
+  CK(e);
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  h->graph_steps = steps;
+  return SOMA_OK;
+}
+
+int zero_acc_all(soma_handle* h, cudaStream_t s) {
+  CK(cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * h->acc_slots, s));
+  return SOMA_OK;
+}
+
+// Bin the current positions of system `sys` into buffer (step - 1) & 1,
+// clear buffer step & 1 and rebuild its fields (unless held).
+int rebin_all(soma_handle* h, cudaStream_t s) {
+  for (int g = 0; g < h->n_sys; ++g) {
+    SysDev& S = h->host_sys[g];
+    CK(cudaMemsetAsync(S.counts, 0, sizeof(uint32_t) * 4 * S.n_c, s));
+    CK(launch_bin(h->d_sys, g, S.n_b, h->d_step, -1, h->sm_count, s));
+  }
+  CK(launch_field(h->d_sys, h->d_cell_tiles, (int)h->cell_tiles.size(), h->d_step, -1, s));
+  return SOMA_OK;
+}
+
+int check_device_error(soma_handle* h) {
+  int err = 0;
+  CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err & kErrTimeout) return fail(h, SOMA_ETIMEOUT);
+  if (err & kErrBounds) return fail(h, SOMA_EDEVICE_CHECK);
+  return SOMA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int soma_options_default(soma_options* o) {
+  if (!o) return SOMA_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->device = -1;
+  o->sort_interval = -1;
+  o->block_threads = 0;
+  o->hist_mode = SOMA_HIST_AUTO;
+  o->graph_steps = kDefaultGraphSteps;
+  o->kernel_timing = 0;
+  o->autotune = 0;
+  return SOMA_OK;
+}
+
+const char* soma_strerror(int code) {
+  switch (code) {
+    case SOMA_OK: return "ok";
+    case SOMA_EINVAL: return "invalid argument";
+    case SOMA_ENOMEM: return "out of memory";
+    case SOMA_ECUDA: return "CUDA runtime error";
+    case SOMA_ETIMEOUT: return "device-side wait timed out";
+    case SOMA_EDEVICE_CHECK: return "device-side consistency check failed";
+    case SOMA_ESTATE: return "handle is in a failed state";
+    case SOMA_ENOTSUP: return "not supported";
+    default: return "unknown error";
+  }
+}
+
+int soma_last_error(const soma_handle* h) { return h ? h->sticky : SOMA_EINVAL; }
+
+void soma_destroy(soma_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& te : h->pending) {
+    cudaEventDestroy(te.a);
+    cudaEventDestroy(te.b);
+  }
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  dev_free_all(h);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt, soma_handle** out) {
+  if (!out) return SOMA_EINVAL;
+  *out = nullptr;
+  if (!sys || n_sys < 1 || n_sys > (1 << 20)) return SOMA_EINVAL;
+  for (int s = 0; s < n_sys; ++s)
+    if (validate_desc(sys[s]) != SOMA_OK) return SOMA_EINVAL;
+  soma_options o;
+  if (opt)
+    o = *opt;
+  else
+    soma_options_default(&o);
+  if (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads < 32 || o.block_threads > 512))
+    return SOMA_EINVAL;
+  if (o.hist_mode < SOMA_HIST_AUTO || o.hist_mode > SOMA_HIST_SEPARATE) return SOMA_EINVAL;
+  if (o.graph_steps < 0 || o.graph_steps > 4096) return SOMA_EINVAL;
+  if ((o.alloc == nullptr) != (o.free == nullptr)) return SOMA_EINVAL;
+
+  soma_handle* h = new (std::nothrow) soma_handle();
+  if (!h) return SOMA_ENOMEM;
+  h->opt = o;
+  h->n_sys = n_sys;
+  h->desc.assign(sys, sys + n_sys);
+  int rc = SOMA_OK;
+  auto bail = [&](int code) {
+    soma_destroy(h);
+    return code;
+  };
+
+  if (o.device >= 0) {
+    if (cudaSetDevice(o.device) != cudaSuccess) return bail(SOMA_ECUDA);
+    h->device = o.device;
+  } else if (cudaGetDevice(&h->device) != cudaSuccess) {
+    return bail(SOMA_ECUDA);
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return bail(SOMA_ECUDA);
+  h->sm_count = prop.multiProcessorCount;
+  if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(SOMA_ECUDA);
+  h->threads = o.block_threads ? o.block_threads : kDefaultThreads;
+  h->hist_mode = o.hist_mode == SOMA_HIST_AUTO ? SOMA_HIST_FUSED : o.hist_mode;
+  h->sort_interval = o.sort_interval < 0 ? kDefaultSortInterval : o.sort_interval;
+
+  // --- per-system constants and arrays ---------------------------------
+  h->host_sys.resize(n_sys);
+  int64_t chain_base = 0;
+  for (int s = 0; s < n_sys; ++s) {
+    const soma_system_desc& d = sys[s];
+    SysDev& S = h->host_sys[s];
+    std::memset(&S, 0, sizeof(S));
+    S.n_poly = d.n_poly;
+    S.N = d.N;
+    S.n_A = d.n_A;
+    S.P = d.N <= 64 ? next_pow2((d.N + 1) / 2) : 0;
+    S.nx = d.grid[0];
+    S.ny = d.grid[1];
+    S.nz = d.grid[2];
+    S.sys_index = d.system_id;
+    S.n_b = (int64_t)d.n_poly * d.N;
+    S.n_c = (int64_t)d.grid[0] * d.grid[1] * d.grid[2];
+    for (int a = 0; a < 3; ++a) {
+      S.L[a] = (float)d.box[a];
+      S.invL[a] = (float)(1.0 / d.box[a]);
+      S.cps[a] = (float)(d.grid[a] / d.box[a]);
+    }
+    S.A = (float)(d.A > 0 ? d.A : 0.5 / std::sqrt((double)(d.N - 1)));
+    S.kb = (float)(1.5 * (d.N - 1));
+    S.chiN_N = (float)(d.chiN / d.N);
+    S.kappaN_N = (float)(d.kappaN / d.N);
+    S.inv_rho = (float)((double)S.n_c / (double)S.n_b);
+    uint32_t k0 = (uint32_t)(d.seed & 0xFFFFFFFFu), k1 = (uint32_t)(d.seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+      S.rk[r][0] = k0;
+      S.rk[r][1] = k1;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    S.chain_base = chain_base;
+    chain_base += d.n_poly;
+    h->max_nb = std::max<int64_t>(h->max_nb, S.n_b);
+    h->max_nc = std::max<int64_t>(h->max_nc, S.n_c);
+
+    const size_t nb = (size_t)S.n_b, nc = (size_t)S.n_c;
+    S.x = (float*)dev_alloc(h, nb * 4);
+    S.y = (float*)dev_alloc(h, nb * 4);
+    S.z = (float*)dev_alloc(h, nb * 4);
+    S.img = (int16_t*)dev_alloc(h, nb * 8);
+    S.chain_id = (uint32_t*)dev_alloc(h, (size_t)d.n_poly * 4);
+    S.x_alt = (float*)dev_alloc(h, nb * 4);
+    S.y_alt = (float*)dev_alloc(h, nb * 4);
+    S.z_alt = (float*)dev_alloc(h, nb * 4);
+    S.img_alt = (int16_t*)dev_alloc(h, nb * 8);
+    S.chain_id_alt = (uint32_t*)dev_alloc(h, (size_t)d.n_poly * 4);
+    S.counts = (uint32_t*)dev_alloc(h, nc * 16);
+    S.w = (float*)dev_alloc(h, nc * 8);
+    if (!S.x || !S.y || !S.z || !S.img || !S.chain_id || !S.x_alt || !S.y_alt || !S.z_alt || !S.img_alt ||
+        !S.chain_id_alt || !S.counts || !S.w)
+      return bail(SOMA_ENOMEM);
+  }
+  // tiles for the largest accumulator need (smallest CTA) so that retuning never reallocates
+  {
+    const int t_save = h->threads;
+    h->threads = 32;
+    h->acc_slots = build_tiles(h);
+    h->threads = t_save;
+  }
+  build_tiles(h);
+  h->d_acc = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * h->acc_slots);
+  for (int s = 0; s < n_sys; ++s) h->host_sys[s].acc = h->d_acc;
+  for (int s = 0; s < n_sys; ++s) {
+    const SysDev& S = h->host_sys[s];
+    for (int64_t b = 0; b < S.n_c; b += kCellsPerTile) {
+      CellTile t;
+      t.sys = s;
+      t.pad = 0;
+      t.begin = b;
+      t.end = std::min<int64_t>(S.n_c, b + kCellsPerTile);
+      h->cell_tiles.push_back(t);
+    }
+  }
+  h->d_sys = (SysDev*)dev_alloc(h, sizeof(SysDev) * n_sys);
+  h->d_cell_tiles = (CellTile*)dev_alloc(h, sizeof(CellTile) * h->cell_tiles.size());
+  h->d_step = (unsigned long long*)dev_alloc(h, 8);
+  h->d_err = (int*)dev_alloc(h, 4);
+  h->d_obs = (double*)dev_alloc(h, 8 * sizeof(double));
+  h->d_acc_sum = (unsigned long long*)dev_alloc(h, 8);
+  h->d_stage_pos = (float*)dev_alloc(h, (size_t)h->max_nb * 12);
+  h->d_stage_img = (int16_t*)dev_alloc(h, (size_t)h->max_nb * 6);
+  h->d_stage_phi = (float*)dev_alloc(h, std::max<size_t>((size_t)h->max_nc * 8, (size_t)n_sys * 8));
+  if (!h->d_acc || !h->d_sys || !h->d_cell_tiles || !h->d_step || !h->d_err || !h->d_obs || !h->d_acc_sum ||
+      !h->d_stage_pos || !h->d_stage_img || !h->d_stage_phi)
+    return bail(SOMA_ENOMEM);
+  // sort work
+  {
+    int bits = 0;
+    while ((1 << bits) < n_sys) ++bits;
+    h->sort.n_chains = chain_base;
+    h->sort.end_bit = 40 + bits;
+    h->sort.keys_in = (unsigned long long*)dev_alloc(h, 8 * (size_t)chain_base);
+    h->sort.keys_out = (unsigned long long*)dev_alloc(h, 8 * (size_t)chain_base);
+    h->sort.vals_in = (uint32_t*)dev_alloc(h, 4 * (size_t)chain_base);
+    h->sort.vals_out = (uint32_t*)dev_alloc(h, 4 * (size_t)chain_base);
+    h->sort.chain_sys = (int32_t*)dev_alloc(h, 4 * (size_t)chain_base);
+    h->sort.temp_bytes = sort_temp_bytes(chain_base, h->sort.end_bit);
+    h->sort.temp = dev_alloc(h, h->sort.temp_bytes);
+    if (!h->sort.keys_in || !h->sort.keys_out || !h->sort.vals_in || !h->sort.vals_out || !h->sort.chain_sys ||
+        !h->sort.temp)
+      return bail(SOMA_ENOMEM);
+    std::vector<int32_t> cs((size_t)chain_base);
+    for (int s = 0; s < n_sys; ++s)
+      std::fill(cs.begin() + h->host_sys[s].chain_base, cs.begin() + h->host_sys[s].chain_base + sys[s].n_poly, s);
+    if (cudaMemcpy(h->sort.chain_sys, cs.data(), 4 * cs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(SOMA_ECUDA);
+  }
+  if (cudaMemcpy(h->d_sys, h->host_sys.data(), sizeof(SysDev) * n_sys, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(h->d_cell_tiles, h->cell_tiles.data(), sizeof(CellTile) * h->cell_tiles.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(h->d_step, 0, 8) != cudaSuccess || cudaMemset(h->d_err, 0, 4) != cudaSuccess ||
+      cudaMemset(h->d_acc, 0, sizeof(unsigned long long) * h->acc_slots) != cudaSuccess)
+    return bail(SOMA_ECUDA);
+  if ((rc = upload_tiles(h)) != SOMA_OK) return bail(rc);
+
+  // --- initial configuration, start-up checks, counts, fields, sort -----
+  for (int s = 0; s < n_sys && rc == SOMA_OK; ++s) {
+    if (launch_init(h->d_sys, s, h->host_sys[s].n_poly, h->stream) != cudaSuccess) rc = SOMA_ECUDA;
+    else if (launch_validate(h->d_sys, s, h->d_err, h->sm_count, h->stream) != cudaSuccess) rc = SOMA_ECUDA;
+  }
+  if (rc == SOMA_OK) rc = rebin_all(h, h->stream);
+  if (rc == SOMA_OK && h->sort_interval != 0) rc = enqueue_reorder(h, h->stream);
+  if (rc == SOMA_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = SOMA_ECUDA;
+  if (rc == SOMA_OK) rc = check_device_error(h);
+  if (rc != SOMA_OK) return bail(rc);
+  h->tuned = !o.autotune;
+  *out = h;
+  return SOMA_OK;
+}
+
+int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (n_steps < 0) return SOMA_EINVAL;
+  if (h->step + (uint64_t)n_steps >= (uint64_t)kInitStep) return SOMA_EINVAL;
+  if (n_steps == 0) return SOMA_OK;
+  if (!h->tuned) {
+    rc = soma_autotune(h);
+    if (rc) return rc;
+  }
+  cudaStream_t s = pick(h, stream);
+  const bool use_graph = h->opt.graph_steps > 0 && !h->opt.kernel_timing;
+  int64_t left = n_steps;
+  while (left > 0) {
+    if (h->sort_interval > 0 && h->steps_since_sort >= (uint64_t)h->sort_interval) {
+      rc = enqueue_reorder(h, s);
+      if (rc) return rc;
+    }
+    int64_t chunk = left;
+    if (h->sort_interval > 0) chunk = std::min<int64_t>(chunk, h->sort_interval - (int64_t)h->steps_since_sort);
+    if (use_graph && chunk >= h->opt.graph_steps) {
+      if (!h->graph || h->graph_steps != h->opt.graph_steps) {
+        rc = capture_graph(h, h->opt.graph_steps);
+        if (rc) return rc;
+      }
+      const int64_t reps = chunk / h->graph_steps;
+      for (int64_t r = 0; r < reps; ++r) CK(cudaGraphLaunch(h->graph, s));
+      chunk = reps * h->graph_steps;
+    } else {
+      chunk = std::min<int64_t>(chunk, 1 << 20);
+      for (int64_t i = 0; i < chunk; ++i) {
+        rc = enqueue_step(h, s, (int)i);
+        if (rc) return rc;
+      }
+      CK(launch_advance(h->d_step, chunk, s));
+    }
+    left -= chunk;
+    h->step += (uint64_t)chunk;
+    h->steps_since_sort += (uint64_t)chunk;
+  }
+  return SOMA_OK;
+}
+
+int soma_sync(soma_handle* h, void* stream) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(pick(h, stream)));
+  CK(cudaStreamSynchronize(h->stream));
+  return check_device_error(h);
+}
+
+static int sync_all(soma_handle* h) {
+  CK(cudaDeviceSynchronize());
+  return check_device_error(h);
+}
+
+int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
+  if ((rc = sync_all(h))) return rc;
+  const uint32_t* src = S.counts + (size_t)((h->step + 1) & 1) * 2 * S.n_c;
+  CK(cudaMemcpy(out, src, sizeof(uint32_t) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return SOMA_OK;
+}
+
+int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
+  if ((rc = sync_all(h))) return rc;
+  CK(cudaMemcpy(out, S.w, sizeof(float) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  return SOMA_OK;
+}
+
+static int set_frozen(soma_handle* h, int sys, int frozen) {
+  h->host_sys[sys].frozen = frozen;
+  CK(cudaMemcpy(reinterpret_cast<char*>(h->d_sys + sys) + offsetof(SysDev, frozen), &frozen, sizeof(int),
+                cudaMemcpyHostToDevice));
+  return SOMA_OK;
+}
+
+int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !phi) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
+  if ((rc = sync_all(h))) return rc;
+  CK(cudaMemcpy(h->d_stage_phi, phi, sizeof(float) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  CK(launch_field_from_phi(h->d_sys, sys, h->d_stage_phi, h->sm_count, h->stream));
+  return sync_all(h);
+}
+
+int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if ((rc = sync_all(h))) return rc;
+  if (w) {
+    if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
+    if ((rc = set_frozen(h, sys, 1))) return rc;
+    CK(cudaMemcpy(S.w, w, sizeof(float) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  } else {
+    if ((rc = set_frozen(h, sys, 0))) return rc;
+    // rebuild from the counts of the current configuration (buffer (step-1)&1); the
+    // field kernel also clears buffer step&1, which holds nothing yet
+    CK(launch_field(h->d_sys, h->d_cell_tiles, (int)h->cell_tiles.size(), h->d_step, -1, h->stream));
+  }
+  return sync_all(h);
+}
+
+int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* step, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if ((rc = sync_all(h))) return rc;
+  if (pos || img) {
+    CK(launch_gather_state(h->d_sys, sys, h->d_stage_pos, h->d_stage_img, h->sm_count, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const cudaMemcpyKind k = where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (pos) CK(cudaMemcpy(pos, h->d_stage_pos, (size_t)S.n_b * 12, k));
+    if (img) CK(cudaMemcpy(img, h->d_stage_img, (size_t)S.n_b * 6, k));
+  }
+  if (step) *step = h->step;
+  return SOMA_OK;
+}
+
+int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img, uint64_t step, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !pos || !img) return SOMA_EINVAL;
+  if (step >= (uint64_t)kInitStep) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if ((rc = sync_all(h))) return rc;
+  const cudaMemcpyKind k = where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpy(h->d_stage_pos, pos, (size_t)S.n_b * 12, k));
+  CK(cudaMemcpy(h->d_stage_img, img, (size_t)S.n_b * 6, k));
+  CK(cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+  CK(launch_validate_pos(h->d_stage_pos, S.n_b, S.L, h->d_err, h->sm_count, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int err = 0;
+  CK(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
+  if (err) {
+    CK(cudaMemset(h->d_err, 0, 4));
+    return SOMA_EINVAL;  // a position outside [0, L): rejected, the state is untouched
+  }
+  CK(launch_scatter_state(h->d_sys, sys, h->d_stage_pos, h->d_stage_img, h->sm_count, h->stream));
+  h->step = step;
+  h->acc_since = step;
+  CK(cudaMemcpyAsync(h->d_step, &step, 8, cudaMemcpyHostToDevice, h->stream));
+  if ((rc = zero_acc_all(h, h->stream))) return rc;
+  if ((rc = rebin_all(h, h->stream))) return rc;
+  return sync_all(h);
+}
+
+int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !accepted) return SOMA_EINVAL;
+  CK(launch_sum_acc(h->d_sys, sys, h->d_acc_sum, h->stream));
+  unsigned long long a = 0;
+  CK(cudaMemcpyAsync(&a, h->d_acc_sum, 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *accepted = a;
+  return SOMA_OK;
+}
+
+int soma_observables(soma_handle* h, int sys, soma_obs* out) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if ((rc = sync_all(h))) return rc;
+  CK(cudaMemsetAsync(h->d_obs, 0, 8 * sizeof(double), h->stream));
+  CK(cudaMemsetAsync(h->d_acc_sum, 0, 8, h->stream));
+  CK(launch_observables(h->d_sys, sys, h->d_step, h->d_obs, h->d_acc_sum, h->sm_count, h->stream));
+  double r[8];
+  unsigned long long acc = 0;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(r, h->d_obs, sizeof(r), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&acc, h->d_acc_sum, 8, cudaMemcpyDeviceToHost));
+  const soma_system_desc& d = h->desc[sys];
+  out->step = h->step;
+  out->accepted = acc;
+  out->attempted = (uint64_t)S.n_b * (h->step - h->acc_since);
+  out->acc = out->attempted ? (double)acc / (double)out->attempted : 0.0;
+  out->Re2 = r[0] / d.n_poly;
+  out->Rg2 = r[1] / d.n_poly;
+  out->Ebond = 1.5 * (d.N - 1) * r[2];
+  out->Enb = (double)d.n_poly / (double)S.n_c * r[3];
+  return SOMA_OK;
+}
+
+int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz, double* S_out) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || nq < 0 || (nq > 0 && (!m_xyz || !S_out))) return SOMA_EINVAL;
+  if (nq == 0) return SOMA_OK;
+  if ((rc = sync_all(h))) return rc;
+  if (nq > h->m_cap) {
+    h->d_m = (int32_t*)dev_alloc(h, sizeof(int32_t) * 3 * nq);
+    h->d_sq = (double*)dev_alloc(h, sizeof(double) * 2 * nq);
+    if (!h->d_m || !h->d_sq) return fail(h, SOMA_ENOMEM);
+    h->m_cap = nq;
+  }
+  CK(cudaMemcpy(h->d_m, m_xyz, sizeof(int32_t) * 3 * nq, cudaMemcpyHostToDevice));
+  CK(cudaMemsetAsync(h->d_sq, 0, sizeof(double) * 2 * nq, h->stream));
+  CK(launch_structure_factor(h->d_sys, sys, nq, h->d_m, h->d_sq, h->sm_count, h->stream));
+  std::vector<double> acc(2 * (size_t)nq);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(acc.data(), h->d_sq, sizeof(double) * 2 * nq, cudaMemcpyDeviceToHost));
+  const double nb = (double)h->host_sys[sys].n_b;
+  for (int q = 0; q < nq; ++q) S_out[q] = (acc[2 * q] * acc[2 * q] + acc[2 * q + 1] * acc[2 * q + 1]) / nb;
+  return SOMA_OK;
+}
+
+int soma_reorder(soma_handle* h, void* stream) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  return enqueue_reorder(h, pick(h, stream));
+}
+
+int soma_get_info(soma_handle* h, int sys, soma_info* out) {
+  if (!h || !out || sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  out->n_beads = S.n_b;
+  out->n_cells = S.n_c;
+  out->k_b = S.kb;
+  out->A = S.A;
+  out->rho_bar = (double)S.n_b / (double)S.n_c;
+  out->lanes_per_chain = S.P;
+  out->block_threads = h->threads;
+  out->sort_interval = h->sort_interval;
+  out->hist_mode = h->hist_mode;
+  return SOMA_OK;
+}
+
+int soma_kernel_times(soma_handle* h, double* ms, int64_t* launches, int reset) {
+  if (!h) return SOMA_EINVAL;
+  if (!h->pending.empty()) {
+    CK(cudaDeviceSynchronize());
+    for (auto& te : h->pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, te.a, te.b) == cudaSuccess) h->ms[te.kind] += t;
+      cudaEventDestroy(te.a);
+      cudaEventDestroy(te.b);
+    }
+    h->pending.clear();
+  }
+  for (int i = 0; i < 4; ++i) {
+    if (ms) ms[i] = h->ms[i];
+    if (launches) launches[i] = h->launches[i];
+    if (reset) {
+      h->ms[i] = 0;
+      h->launches[i] = 0;
+    }
+  }
+  return SOMA_OK;
+}
+
+// Autotuner: time a few steps per candidate (CTA size of the move kernel,
+// fused or separate histogram) from a saved copy of the state, restore the
+// state between candidates and keep the fastest.  Random numbers are
+// counter-based, so the restored trajectory is the one that would have run.
+int soma_autotune(soma_handle* h) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  h->tuned = true;
+  if (h->n_move_tiles == 0) return SOMA_OK;
+  CK(cudaDeviceSynchronize());
+  // save positions, images, chain ids of every system and the counters
+  const uint64_t step0 = h->step;
+  std::vector<SysDev> dev(h->n_sys);
+  CK(cudaMemcpy(dev.data(), h->d_sys, sizeof(SysDev) * h->n_sys, cudaMemcpyDeviceToHost));
+  std::vector<std::vector<char>> save(h->n_sys);
+  for (int s = 0; s < h->n_sys; ++s) {
+    const SysDev& S = dev[s];
+    save[s].resize((size_t)S.n_b * 20 + (size_t)S.n_poly * 4 + (size_t)S.n_c * 24);
+    char* p = save[s].data();
+    CK(cudaMemcpy(p, S.x, S.n_b * 4, cudaMemcpyDeviceToHost)); p += S.n_b * 4;
+    CK(cudaMemcpy(p, S.y, S.n_b * 4, cudaMemcpyDeviceToHost)); p += S.n_b * 4;
+    CK(cudaMemcpy(p, S.z, S.n_b * 4, cudaMemcpyDeviceToHost)); p += S.n_b * 4;
+    CK(cudaMemcpy(p, S.img, S.n_b * 8, cudaMemcpyDeviceToHost)); p += S.n_b * 8;
+    CK(cudaMemcpy(p, S.chain_id, S.n_poly * 4, cudaMemcpyDeviceToHost)); p += S.n_poly * 4;
+    CK(cudaMemcpy(p, S.counts, S.n_c * 16, cudaMemcpyDeviceToHost)); p += S.n_c * 16;
+    CK(cudaMemcpy(p, S.w, S.n_c * 8, cudaMemcpyDeviceToHost));
+  }
+  std::vector<unsigned long long> acc_total(h->n_sys);
+  for (int s = 0; s < h->n_sys; ++s) {
+    CK(launch_sum_acc(h->d_sys, s, h->d_acc_sum, h->stream));
+    CK(cudaMemcpyAsync(&acc_total[s], h->d_acc_sum, 8, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  auto restore = [&]() -> int {
+    for (int s = 0; s < h->n_sys; ++s) {
+      const SysDev& S = dev[s];
+      const char* p = save[s].data();
+      CK(cudaMemcpy(S.x, p, S.n_b * 4, cudaMemcpyHostToDevice)); p += S.n_b * 4;
+      CK(cudaMemcpy(S.y, p, S.n_b * 4, cudaMemcpyHostToDevice)); p += S.n_b * 4;
+      CK(cudaMemcpy(S.z, p, S.n_b * 4, cudaMemcpyHostToDevice)); p += S.n_b * 4;
+      CK(cudaMemcpy(S.img, p, S.n_b * 8, cudaMemcpyHostToDevice)); p += S.n_b * 8;
+      CK(cudaMemcpy(S.chain_id, p, S.n_poly * 4, cudaMemcpyHostToDevice)); p += S.n_poly * 4;
+      CK(cudaMemcpy(S.counts, p, S.n_c * 16, cudaMemcpyHostToDevice)); p += S.n_c * 16;
+      CK(cudaMemcpy(S.w, p, S.n_c * 8, cudaMemcpyHostToDevice));
+    }
+    h->step = step0;
+    CK(cudaMemcpy(h->d_step, &step0, 8, cudaMemcpyHostToDevice));
+    return SOMA_OK;
+  };
+  const int cand_threads[3] = {128, 256, 512};
+  const int cand_hist[2] = {SOMA_HIST_FUSED, SOMA_HIST_SEPARATE};
+  const int steps = 8;
+  float best = 1e30f;
+  int best_t = h->threads, best_h = h->hist_mode;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  const int timing = h->opt.kernel_timing;
+  h->opt.kernel_timing = 0;
+  for (int ti = 0; ti < 3; ++ti) {
+    if (h->opt.block_threads && cand_threads[ti] != h->opt.block_threads) continue;
+    for (int hi = 0; hi < 2; ++hi) {
+      if (h->opt.hist_mode != SOMA_HIST_AUTO && cand_hist[hi] != h->opt.hist_mode) continue;
+      h->hist_mode = cand_hist[hi];
+      if ((rc = rebuild_geometry(h, cand_threads[ti]))) return rc;
+      for (int i = 0; i < 2; ++i) enqueue_step(h, h->stream, i);  // warm-up
+      CK(launch_advance(h->d_step, 2, h->stream));
+      CK(cudaEventRecord(a, h->stream));
+      for (int i = 0; i < steps; ++i)
+        if ((rc = enqueue_step(h, h->stream, i))) return rc;
+      CK(launch_advance(h->d_step, steps, h->stream));
+      CK(cudaEventRecord(b, h->stream));
+      CK(cudaEventSynchronize(b));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best) {
+        best = ms;
+        best_t = cand_threads[ti];
+        best_h = cand_hist[hi];
+      }
+      if ((rc = restore())) return rc;
+    }
+  }
+  h->opt.kernel_timing = timing;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->hist_mode = best_h;
+  if ((rc = rebuild_geometry(h, best_t))) return rc;
+  for (int s = 0; s < h->n_sys; ++s)
+    CK(cudaMemcpy(h->d_acc + h->host_sys[s].acc_first, &acc_total[s], 8, cudaMemcpyHostToDevice));
+  return sync_all(h);
+}
+
+int soma_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n) {
+  if (n == 0) return SOMA_OK;
+  if (!ctr || !key || !out) return SOMA_EINVAL;
+  uint32_t* d = nullptr;
+  if (cudaMalloc(&d, n * 40) != cudaSuccess) {
+    cudaGetLastError();
+    return SOMA_ENOMEM;
+  }
+  int rc = SOMA_OK;
+  if (cudaMemcpy(d, ctr, n * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d + 4 * n, key, n * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      launch_philox(d, d + 4 * n, d + 6 * n, (int64_t)n, 0) != cudaSuccess ||
+      cudaMemcpy(out, d + 6 * n, n * 16, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = SOMA_ECUDA;
+  cudaFree(d);
+  return rc;
+}
+
+}  // extern "C"

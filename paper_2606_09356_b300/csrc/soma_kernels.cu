@@ -1,0 +1,731 @@
+// soma_kernels.cu -- sm_103a kernels of the SCMF Monte Carlo step.
+//
+// (a) k_move_bin: set-parallel bead moves (even set, then odd set) with the
+//     histogram (b) fused as its epilogue; the moves are the biased trial
+//     moves and energy evaluations of the move kernel profiled in Sec. 2.2.
+// (b) k_bin: stand-alone density histogram (the density-field update of
+//     Sec. 2.2), used at start-up, after a restore and with the generic path.
+// (c) k_field: per-cell field rebuild from the counts, fused with zeroing of
+//     the count buffer of the next step.
+// plus initialisation, state gather/scatter, validation, observables and S(q).
+//
+// Layout (per system, see soma_internal.cuh): positions as three FP32 arrays
+// x, y, z [n_b] wrapped into [0, L), bead = slot * N + i; images int16
+// [n_b][4]; counts uint32 [2 buffers][2 types][n_c]; fields FP32 [2][n_c].
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "soma_internal.cuh"
+#include "soma_launch.h"
+
+namespace soma {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The round keys are
+// precomputed per system on the host (seed lo/hi plus r times the published
+// Weyl increments), so a round is two wide multiplies and two 3-input XORs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, const uint32_t (*rk)[2]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[r][0], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ rk[r][1], (uint32_t)p0);
+  }
+  return c;
+}
+
+// Copy one system's constants into shared memory (all threads call).
+__device__ __forceinline__ void load_sys(SysDev* dst, const SysDev* src) {
+  const int words = sizeof(SysDev) / 4;
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldg(s + i);
+  __syncthreads();
+}
+
+__device__ __forceinline__ int cell_axis(float x, float cps, int n) {
+  const int i = (int)(x * cps);  // x >= 0, so truncation is floor
+  return min(max(i, 0), n - 1);
+}
+
+__device__ __forceinline__ int cell_of(const SysDev& S, float x, float y, float z) {
+  return (cell_axis(x, S.cps[0], S.nx) * S.ny + cell_axis(y, S.cps[1], S.ny)) * S.nz +
+         cell_axis(z, S.cps[2], S.nz);
+}
+
+// Wrap a proposed coordinate back into [0, L); delta receives the image step.
+__device__ __forceinline__ float wrap_coord(float p, float L, int& delta) {
+  delta = 0;
+  if (p >= L) {
+    p -= L;  // exact: L <= p < 2L
+    delta = 1;
+  } else if (p < 0.f) {
+    p += L;
+    delta = -1;
+    if (p >= L) {  // |p| below half an ulp of L: the wrapped value is 0 in this image
+      p = 0.f;
+      delta = 0;
+    }
+  }
+  return p;
+}
+
+__device__ __forceinline__ float min_image(float d, float L, float invL) {
+  return d - L * rintf(d * invL);
+}
+
+// One Metropolis trial of bead `bead` of logical chain `cid` at step t.
+// (x, y, z, cell) is updated in place on acceptance; wrap receives the image
+// steps packed as (dx+1) | (dy+1) << 2 | (dz+1) << 4 (21 = no wrap).
+// Neighbours a and b enter with weights wa, wb in {0, 1}.
+//   dE_bond = k_b sum_j (|r + d - r_j|^2 - |r - r_j|^2)
+//           = k_b (2 d . sum_j (r - r_j) + n_j |d|^2)
+__device__ __forceinline__ int try_move(const SysDev& S, const float* __restrict__ wt, uint32_t bead,
+                                        uint32_t cid, uint32_t t, float& x, float& y, float& z,
+                                        int& cell, int& wrap, float ax, float ay, float az, float wa,
+                                        float bx, float by, float bz, float wb) {
+  const uint4 r = philox10(make_uint4(bead, cid, t, (uint32_t)S.sys_index), S.rk);
+  // d_k = A (2 U_k - 1), U_k = (r_k >> 8) 2^-24; (r_k >> 8) 2^-23 - 1 is exact in FP32.
+  const float dx = S.A * fmaf((float)(r.x >> 8), 0x1p-23f, -1.0f);
+  const float dy = S.A * fmaf((float)(r.y >> 8), 0x1p-23f, -1.0f);
+  const float dz = S.A * fmaf((float)(r.z >> 8), 0x1p-23f, -1.0f);
+  const float sx = wa * min_image(x - ax, S.L[0], S.invL[0]) + wb * min_image(x - bx, S.L[0], S.invL[0]);
+  const float sy = wa * min_image(y - ay, S.L[1], S.invL[1]) + wb * min_image(y - by, S.L[1], S.invL[1]);
+  const float sz = wa * min_image(z - az, S.L[2], S.invL[2]) + wb * min_image(z - bz, S.L[2], S.invL[2]);
+  const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float dEb = fmaf(2.f, fmaf(dx, sx, fmaf(dy, sy, dz * sz)), (wa + wb) * d2);
+  int ex, ey, ez;
+  const float px = wrap_coord(x + dx, S.L[0], ex);
+  const float py = wrap_coord(y + dy, S.L[1], ey);
+  const float pz = wrap_coord(z + dz, S.L[2], ez);
+  const int cnew = cell_of(S, px, py, pz);
+  const float dE = fmaf(S.kb, dEb, __ldg(wt + cnew) - __ldg(wt + cell));
+  // Metropolis: accept iff dE + ln u < 0 with u = ((r_3 >> 9) + 1/2) 2^-23 in
+  // (0, 1); dE <= 0 always accepts because ln u < 0.
+  bool ok = dE <= 0.f;
+  if (!ok) {
+    const float u = fmaf((float)(r.w >> 9), 0x1p-23f, 0x1p-24f);
+    ok = dE + __logf(u) < 0.f;
+  }
+  if (ok) {
+    x = px;
+    y = py;
+    z = pz;
+    cell = cnew;
+    wrap = (ex + 1) | ((ey + 1) << 2) | ((ez + 1) << 4);
+  }
+  return ok ? 1 : 0;
+}
+
+__device__ __forceinline__ void apply_wrap(int16_t* img, int64_t bead, int wrap) {
+  if (wrap != 21) {
+    short4* p = reinterpret_cast<short4*>(img) + bead;
+    short4 v = *p;
+    v.x += (short)((wrap & 3) - 1);
+    v.y += (short)(((wrap >> 2) & 3) - 1);
+    v.z += (short)(((wrap >> 4) & 3) - 1);
+    *p = v;
+  }
+}
+
+__device__ __forceinline__ uint32_t current_step(const unsigned long long* step_base, int offset) {
+  return (uint32_t)(*step_base + (long long)offset);
+}
+
+// ---------------------------------------------------------------------------
+// (a) + fused (b): one warp holds 32/P chains, lane k of a chain holds beads
+// 2k (even set) and 2k+1 (odd set) in registers; neighbours come from the
+// adjacent lane by shuffles of width P.  Set 0 moves, then set 1 sees set
+// 0's accepted positions; the fields stay frozen for the step.  The final
+// cells are binned into count buffer t & 1 (zeroed by the previous field
+// kernel) when `bin` is set.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_move_bin(const SysDev* __restrict__ systems,
+                                                  const MoveTile* __restrict__ tiles,
+                                                  const unsigned long long* __restrict__ step_base,
+                                                  int step_offset, int bin) {
+  __shared__ SysDev S;
+  __shared__ unsigned int s_acc;
+  const MoveTile tile = tiles[blockIdx.x];
+  if (threadIdx.x == 0) s_acc = 0;
+  load_sys(&S, systems + tile.sys);
+  const uint32_t t = current_step(step_base, step_offset);
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int P = S.P, N = S.N;
+  const int k = lane & (P - 1);
+  const int chain_local = warp * (32 / P) + lane / P;
+  const bool chain_ok = chain_local < tile.n_chains;
+  const int slot = tile.first_chain + (chain_ok ? chain_local : 0);
+  const int e = 2 * k, o = 2 * k + 1;
+  const bool he = chain_ok && e < N, ho = chain_ok && o < N;
+  const int64_t base = (int64_t)slot * N;
+
+  float xe = 0.f, ye = 0.f, ze = 0.f, xo = 0.f, yo = 0.f, zo = 0.f;
+  if ((N & 1) == 0) {
+    if (he) {  // beads e, e+1 are adjacent and 8-byte aligned
+      const float2 vx = *reinterpret_cast<const float2*>(S.x + base + e);
+      const float2 vy = *reinterpret_cast<const float2*>(S.y + base + e);
+      const float2 vz = *reinterpret_cast<const float2*>(S.z + base + e);
+      xe = vx.x; xo = vx.y; ye = vy.x; yo = vy.y; ze = vz.x; zo = vz.y;
+    }
+  } else {
+    if (he) { xe = S.x[base + e]; ye = S.y[base + e]; ze = S.z[base + e]; }
+    if (ho) { xo = S.x[base + o]; yo = S.y[base + o]; zo = S.z[base + o]; }
+  }
+  const uint32_t cid = chain_ok ? __ldg(S.chain_id + slot) : 0u;
+  int ce = cell_of(S, xe, ye, ze), co = cell_of(S, xo, yo, zo);
+  int wre = 21, wro = 21;
+  int nacc = 0;
+
+  // set 0: even bead e; left neighbour 2k-1 lives in lane k-1, right is own odd
+  {
+    const float lx = __shfl_up_sync(0xffffffffu, xo, 1, P);
+    const float ly = __shfl_up_sync(0xffffffffu, yo, 1, P);
+    const float lz = __shfl_up_sync(0xffffffffu, zo, 1, P);
+    if (he) {
+      const float* wt = S.w + (e < S.n_A ? 0 : S.n_c);
+      nacc += try_move(S, wt, (uint32_t)e, cid, t, xe, ye, ze, ce, wre, lx, ly, lz, k > 0 ? 1.f : 0.f,
+                       xo, yo, zo, ho ? 1.f : 0.f);
+    }
+  }
+  // set 1: odd bead o; left is own (updated) even bead, right 2k+2 lives in lane k+1
+  {
+    const float rx = __shfl_down_sync(0xffffffffu, xe, 1, P);
+    const float ry = __shfl_down_sync(0xffffffffu, ye, 1, P);
+    const float rz = __shfl_down_sync(0xffffffffu, ze, 1, P);
+    if (ho) {
+      const float* wt = S.w + (o < S.n_A ? 0 : S.n_c);
+      nacc += try_move(S, wt, (uint32_t)o, cid, t, xo, yo, zo, co, wro, xe, ye, ze, 1.f, rx, ry, rz,
+                       (o + 1 < N) ? 1.f : 0.f);
+    }
+  }
+
+  if ((N & 1) == 0) {
+    if (he) {
+      *reinterpret_cast<float2*>(S.x + base + e) = make_float2(xe, xo);
+      *reinterpret_cast<float2*>(S.y + base + e) = make_float2(ye, yo);
+      *reinterpret_cast<float2*>(S.z + base + e) = make_float2(ze, zo);
+    }
+  } else {
+    if (he) { S.x[base + e] = xe; S.y[base + e] = ye; S.z[base + e] = ze; }
+    if (ho) { S.x[base + o] = xo; S.y[base + o] = yo; S.z[base + o] = zo; }
+  }
+  if (he) apply_wrap(S.img, base + e, wre);
+  if (ho) apply_wrap(S.img, base + o, wro);
+
+  if (bin) {
+    uint32_t* cnt = S.counts + (size_t)(t & 1u) * 2 * S.n_c;
+    if (he) atomicAdd(cnt + (e < S.n_A ? 0 : S.n_c) + ce, 1u);
+    if (ho) atomicAdd(cnt + (o < S.n_A ? 0 : S.n_c) + co, 1u);
+  }
+
+  nacc = __reduce_add_sync(0xffffffffu, nacc);
+  if (lane == 0 && nacc) atomicAdd(&s_acc, (unsigned)nacc);
+  __syncthreads();
+  if (threadIdx.x == 0) S.acc[tile.acc_index] += s_acc;
+}
+
+// ---------------------------------------------------------------------------
+// Generic move of one set for chains longer than 64 beads: one thread per
+// bead of the set, neighbours read from global memory (they belong to the
+// other set, so they do not change during this launch).  The histogram runs
+// as the separate kernel k_bin afterwards.
+// ---------------------------------------------------------------------------
+__global__ void k_move_set_generic(const SysDev* __restrict__ systems, int sys,
+                                   const unsigned long long* __restrict__ step_base, int step_offset,
+                                   int set) {
+  __shared__ SysDev S;
+  __shared__ unsigned int s_acc;
+  if (threadIdx.x == 0) s_acc = 0;
+  load_sys(&S, systems + sys);
+  const uint32_t t = current_step(step_base, step_offset);
+  const int N = S.N;
+  const int per_chain = (N - set + 1) / 2;
+  const int64_t total = (int64_t)S.n_poly * per_chain;
+  int nacc = 0;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int slot = (int)(j / per_chain);
+    const int i = set + 2 * (int)(j % per_chain);
+    const int64_t b = (int64_t)slot * N + i;
+    float x = S.x[b], y = S.y[b], z = S.z[b];
+    const bool ha = i > 0, hb = i + 1 < N;
+    const float ax = ha ? S.x[b - 1] : 0.f, ay = ha ? S.y[b - 1] : 0.f, az = ha ? S.z[b - 1] : 0.f;
+    const float bx = hb ? S.x[b + 1] : 0.f, by = hb ? S.y[b + 1] : 0.f, bz = hb ? S.z[b + 1] : 0.f;
+    int cell = cell_of(S, x, y, z), wrap = 21;
+    const float* wt = S.w + (i < S.n_A ? 0 : S.n_c);
+    const int ok = try_move(S, wt, (uint32_t)i, S.chain_id[slot], t, x, y, z, cell, wrap, ax, ay, az,
+                            ha ? 1.f : 0.f, bx, by, bz, hb ? 1.f : 0.f);
+    if (ok) {
+      S.x[b] = x; S.y[b] = y; S.z[b] = z;
+      apply_wrap(S.img, b, wrap);
+    }
+    nacc += ok;
+  }
+  nacc = __reduce_add_sync(0xffffffffu, nacc);
+  if ((threadIdx.x & 31) == 0 && nacc) atomicAdd(&s_acc, (unsigned)nacc);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_acc) atomicAdd(S.acc + S.acc_first, (unsigned long long)s_acc);
+}
+
+// ---------------------------------------------------------------------------
+// (b) Stand-alone histogram of the current positions into count buffer t & 1
+// (used at start-up, after a state restore and for chains the register move
+// kernel does not cover).  One thread per bead, one global atomic each.
+// ---------------------------------------------------------------------------
+__global__ void k_bin(const SysDev* __restrict__ systems, int sys,
+                      const unsigned long long* __restrict__ step_base, int step_offset) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  const uint32_t t = current_step(step_base, step_offset);
+  uint32_t* cnt = S.counts + (size_t)(t & 1u) * 2 * S.n_c;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(b % S.N);
+    atomicAdd(cnt + (i < S.n_A ? 0 : S.n_c) + cell_of(S, S.x[b], S.y[b], S.z[b]), 1u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (c) Field rebuild from count buffer t & 1, fused with zeroing of buffer
+// (t + 1) & 1 for the next step:  phi_t = n_t / rho_bar,
+//   w_A = chiN/N phi_B + kappaN/N (phi_A + phi_B - 1), w_B = chiN/N phi_A + ...
+// Held (frozen) fields are not overwritten.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void field_of(const SysDev& S, uint32_t nA, uint32_t nB, float& wA,
+                                         float& wB) {
+  const float pA = (float)nA * S.inv_rho, pB = (float)nB * S.inv_rho;
+  const float ex = S.kappaN_N * (pA + pB - 1.f);
+  wA = fmaf(S.chiN_N, pB, ex);
+  wB = fmaf(S.chiN_N, pA, ex);
+}
+
+__global__ void k_field(const SysDev* __restrict__ systems, const CellTile* __restrict__ tiles,
+                        const unsigned long long* __restrict__ step_base, int step_offset) {
+  __shared__ SysDev S;
+  const CellTile tile = tiles[blockIdx.x];
+  load_sys(&S, systems + tile.sys);
+  const uint32_t t = current_step(step_base, step_offset);
+  const int64_t nc = S.n_c;
+  const uint32_t* cur = S.counts + (size_t)(t & 1u) * 2 * nc;
+  uint32_t* nxt = S.counts + (size_t)((t + 1u) & 1u) * 2 * nc;
+  const bool write_w = !S.frozen;
+  if ((nc & 3) == 0 && (tile.begin & 3) == 0 && (tile.end & 3) == 0) {
+    for (int64_t c = tile.begin + 4 * (int64_t)threadIdx.x; c < tile.end; c += 4 * (int64_t)blockDim.x) {
+      const uint4 a = *reinterpret_cast<const uint4*>(cur + c);
+      const uint4 b = *reinterpret_cast<const uint4*>(cur + nc + c);
+      if (write_w) {
+        float4 wa, wb;
+        field_of(S, a.x, b.x, wa.x, wb.x);
+        field_of(S, a.y, b.y, wa.y, wb.y);
+        field_of(S, a.z, b.z, wa.z, wb.z);
+        field_of(S, a.w, b.w, wa.w, wb.w);
+        *reinterpret_cast<float4*>(S.w + c) = wa;
+        *reinterpret_cast<float4*>(S.w + nc + c) = wb;
+      }
+      *reinterpret_cast<uint4*>(nxt + c) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(nxt + nc + c) = make_uint4(0, 0, 0, 0);
+    }
+  } else {
+    for (int64_t c = tile.begin + threadIdx.x; c < tile.end; c += blockDim.x) {
+      if (write_w) {
+        float wa, wb;
+        field_of(S, cur[c], cur[nc + c], wa, wb);
+        S.w[c] = wa;
+        S.w[nc + c] = wb;
+      }
+      nxt[c] = 0u;
+      nxt[nc + c] = 0u;
+    }
+  }
+}
+
+// Fields from given volume fractions phi [2][n_c] (coupling write).
+__global__ void k_field_from_phi(const SysDev* __restrict__ systems, int sys, const float* __restrict__ phi) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  const int64_t nc = S.n_c;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+    const float pA = phi[c], pB = phi[nc + c];
+    const float ex = S.kappaN_N * (pA + pB - 1.f);
+    S.w[c] = fmaf(S.chiN_N, pB, ex);
+    S.w[nc + c] = fmaf(S.chiN_N, pA, ex);
+  }
+}
+
+__global__ void k_advance_step(unsigned long long* step_base, long long n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *step_base += (unsigned long long)n;
+}
+
+// ---------------------------------------------------------------------------
+// Initial configuration: one thread per chain; bead 0 uniform in the box,
+// bond i a Gaussian with per-axis variance 1/(3(N-1)) by Box-Muller on the
+// word pairs (0,1) and (2,3).  Accumulated in FP64, then wrapped.
+// ---------------------------------------------------------------------------
+__global__ void k_init(const SysDev* __restrict__ systems, int sys) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  const int N = S.N;
+  const double sigma = N > 1 ? sqrt(1.0 / (3.0 * (N - 1))) : 0.0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += gridDim.x * blockDim.x) {
+    double X = 0, Y = 0, Z = 0;
+    S.chain_id[c] = (uint32_t)c;
+    for (int i = 0; i < N; ++i) {
+      const uint4 r = philox10(make_uint4((uint32_t)i, (uint32_t)c, kInitStep, (uint32_t)S.sys_index), S.rk);
+      if (i == 0) {
+        X = (double)S.L[0] * ((double)(r.x >> 8) * 0x1p-24);
+        Y = (double)S.L[1] * ((double)(r.y >> 8) * 0x1p-24);
+        Z = (double)S.L[2] * ((double)(r.z >> 8) * 0x1p-24);
+      } else {
+        const double m1 = sqrt(-2.0 * log(((double)(r.x >> 8) + 0.5) * 0x1p-24));
+        const double m2 = sqrt(-2.0 * log(((double)(r.z >> 8) + 0.5) * 0x1p-24));
+        double s1, c1, s2, c2;
+        sincospi(2.0 * ((double)(r.y >> 8) * 0x1p-24), &s1, &c1);
+        sincospi(2.0 * ((double)(r.w >> 8) * 0x1p-24), &s2, &c2);
+        X += sigma * m1 * c1;
+        Y += sigma * m1 * s1;
+        Z += sigma * m2 * c2;
+      }
+      const int64_t b = (int64_t)c * N + i;
+      const double P[3] = {X, Y, Z};
+      float* dst[3] = {S.x, S.y, S.z};
+      short im[3];
+      for (int a = 0; a < 3; ++a) {
+        const double L = (double)S.L[a];
+        double n = floor(P[a] / L);
+        float xw = (float)(P[a] - n * L);
+        if (xw >= S.L[a]) { xw = 0.f; n += 1.0; }
+        if (xw < 0.f) xw = 0.f;
+        dst[a][b] = xw;
+        im[a] = (short)n;
+      }
+      reinterpret_cast<short4*>(S.img)[b] = make_short4(im[0], im[1], im[2], 0);
+    }
+  }
+}
+
+// Positions and images in logical chain order <-> storage order.
+__global__ void k_gather_state(const SysDev* __restrict__ systems, int sys, float* __restrict__ pos,
+                               int16_t* __restrict__ img) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t slot = b / S.N, i = b % S.N;
+    const int64_t lb = (int64_t)S.chain_id[slot] * S.N + i;
+    pos[3 * lb + 0] = S.x[b];
+    pos[3 * lb + 1] = S.y[b];
+    pos[3 * lb + 2] = S.z[b];
+    const short4 v = reinterpret_cast<const short4*>(S.img)[b];
+    img[3 * lb + 0] = v.x;
+    img[3 * lb + 1] = v.y;
+    img[3 * lb + 2] = v.z;
+  }
+}
+
+__global__ void k_scatter_state(const SysDev* __restrict__ systems, int sys, const float* __restrict__ pos,
+                                const int16_t* __restrict__ img) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t slot = b / S.N, i = b % S.N;
+    const int64_t lb = (int64_t)S.chain_id[slot] * S.N + i;
+    S.x[b] = pos[3 * lb + 0];
+    S.y[b] = pos[3 * lb + 1];
+    S.z[b] = pos[3 * lb + 2];
+    reinterpret_cast<short4*>(S.img)[b] = make_short4(img[3 * lb + 0], img[3 * lb + 1], img[3 * lb + 2], 0);
+  }
+}
+
+// Start-up consistency checks (Sec. 2.2 moves SOMA's validation to the GPU):
+// every coordinate finite and inside [0, L).  Sets kErrBounds on failure.
+__global__ void k_validate(const SysDev* __restrict__ systems, int sys, int* __restrict__ err) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
+    const float v[3] = {S.x[b], S.y[b], S.z[b]};
+    for (int a = 0; a < 3; ++a)
+      if (!(v[a] >= 0.f && v[a] < S.L[a])) atomicOr(err, kErrBounds);
+  }
+}
+
+// Check staged positions [n][3] before they replace the state.
+__global__ void k_validate_pos(const float* __restrict__ pos, int64_t n, float Lx, float Ly, float Lz,
+                               int* __restrict__ err) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const float x = pos[3 * b], y = pos[3 * b + 1], z = pos[3 * b + 2];
+    if (!(x >= 0.f && x < Lx && y >= 0.f && y < Ly && z >= 0.f && z < Lz)) atomicOr(err, kErrBounds);
+  }
+}
+
+// Sum of a system's accepted-move counters into *out.
+__global__ void k_sum_acc(const SysDev* __restrict__ systems, int sys, unsigned long long* __restrict__ out) {
+  const SysDev* S = systems + sys;
+  unsigned long long a = 0;
+  for (int i = threadIdx.x; i < S->acc_count; i += blockDim.x) a += S->acc[S->acc_first + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  __shared__ unsigned long long part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    *out = t;
+  }
+}
+
+__global__ void k_zero_acc(const SysDev* __restrict__ systems, int sys) {
+  const SysDev* S = systems + sys;
+  for (int i = threadIdx.x; i < S->acc_count; i += blockDim.x) S->acc[S->acc_first + i] = 0ull;
+}
+
+// ---------------------------------------------------------------------------
+// Observables in FP64: per chain R_e^2, R_g^2 and the bond energy from the
+// unwrapped positions x + image * L; per cell the non-bonded energy from the
+// counts of the current configuration.  out[0..4] = sum Re2, sum Rg2,
+// sum |b|^2, sum_c f(phi), accepted.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void k_obs_chains(const SysDev* __restrict__ systems, int sys, double* __restrict__ out) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  const int N = S.N;
+  double re2 = 0, rg2 = 0, bb = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += gridDim.x * blockDim.x) {
+    const int64_t b0 = (int64_t)c * N;
+    // unwrapped positions relative to bead 0 (keeps the sums well conditioned)
+    double first[3] = {0, 0, 0}, prev[3] = {0, 0, 0}, sum[3] = {0, 0, 0}, sq = 0;
+    for (int i = 0; i < N; ++i) {
+      const short4 im = reinterpret_cast<const short4*>(S.img)[b0 + i];
+      const double p[3] = {(double)S.x[b0 + i] + (double)im.x * S.L[0],
+                           (double)S.y[b0 + i] + (double)im.y * S.L[1],
+                           (double)S.z[b0 + i] + (double)im.z * S.L[2]};
+      for (int a = 0; a < 3; ++a) {
+        if (i == 0) first[a] = p[a];
+        const double r = p[a] - first[a];
+        if (i > 0) bb += (p[a] - prev[a]) * (p[a] - prev[a]);
+        sum[a] += r;
+        sq += r * r;
+        prev[a] = p[a];
+      }
+    }
+    for (int a = 0; a < 3; ++a) re2 += (prev[a] - first[a]) * (prev[a] - first[a]);
+    rg2 += sq / N - (sum[0] * sum[0] + sum[1] * sum[1] + sum[2] * sum[2]) / ((double)N * N);
+  }
+  re2 = warp_sum(re2);
+  rg2 = warp_sum(rg2);
+  bb = warp_sum(bb);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out + 0, re2);
+    atomicAdd(out + 1, rg2);
+    atomicAdd(out + 2, bb);
+  }
+}
+
+__global__ void k_obs_cells(const SysDev* __restrict__ systems, int sys, const unsigned long long* __restrict__ step_base,
+                            double* __restrict__ out, unsigned long long* __restrict__ acc_out) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  // counts of the current configuration sit in buffer (steps_done - 1) & 1
+  const uint32_t t = (uint32_t)(*step_base - 1ull);
+  const uint32_t* cur = S.counts + (size_t)(t & 1u) * 2 * S.n_c;
+  const double rho = (double)S.n_b / (double)S.n_c;
+  const double chiN = (double)S.chiN_N * S.N, kappaN = (double)S.kappaN_N * S.N;
+  double f = 0;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_c; c += (int64_t)gridDim.x * blockDim.x) {
+    const double pA = cur[c] / rho, pB = cur[S.n_c + c] / rho, ex = pA + pB - 1.0;
+    f += chiN * pA * pB + 0.5 * kappaN * ex * ex;
+  }
+  f = warp_sum(f);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out + 3, f);
+  if (blockIdx.x == 0) {
+    unsigned long long a = 0;
+    for (int i = threadIdx.x; i < S.acc_count; i += blockDim.x) a += S.acc[S.acc_first + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc_out, a);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S(q): per bead the phase 2 pi m.r/L from the wrapped position (q is a
+// lattice vector, so images drop out), evaluated in FP32 from the fractional
+// part, accumulated in FP64.  Each thread sums a chunk of up to kSqChunk q
+// vectors over its beads; warps reduce and add to out[2 * q + {0, 1}].
+// ---------------------------------------------------------------------------
+constexpr int kSqChunk = 8;
+
+__global__ void k_structure_factor(const SysDev* __restrict__ systems, int sys, int nq,
+                                   const int32_t* __restrict__ m, double* __restrict__ out) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  for (int q0 = 0; q0 < nq; q0 += kSqChunk) {
+    double re[kSqChunk], im[kSqChunk];
+    float mx[kSqChunk], my[kSqChunk], mz[kSqChunk];
+#pragma unroll
+    for (int j = 0; j < kSqChunk; ++j) {
+      re[j] = im[j] = 0.0;
+      const int q = q0 + j < nq ? q0 + j : nq - 1;
+      mx[j] = (float)m[3 * q + 0];
+      my[j] = (float)m[3 * q + 1];
+      mz[j] = (float)m[3 * q + 2];
+    }
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
+      const float fx = S.x[b] * S.invL[0], fy = S.y[b] * S.invL[1], fz = S.z[b] * S.invL[2];
+      const double s = ((int)(b % S.N) < S.n_A) ? 1.0 : -1.0;
+#pragma unroll
+      for (int j = 0; j < kSqChunk; ++j) {
+        float f = fmaf(mx[j], fx, fmaf(my[j], fy, mz[j] * fz));
+        f -= floorf(f);
+        float sn, cs;
+        sincospif(2.f * f, &sn, &cs);
+        re[j] += s * (double)cs;
+        im[j] += s * (double)sn;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kSqChunk; ++j) {
+      const double r = warp_sum(re[j]), i = warp_sum(im[j]);
+      if ((threadIdx.x & 31) == 0 && q0 + j < nq) {
+        atomicAdd(out + 2 * (q0 + j) + 0, r);
+        atomicAdd(out + 2 * (q0 + j) + 1, i);
+      }
+    }
+  }
+}
+
+// The device Philox on explicit counters and keys (verification entry point).
+__global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
+                         uint32_t* __restrict__ out, int64_t n) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t rk[10][2];
+    uint32_t k0 = key[2 * j], k1 = key[2 * j + 1];
+    for (int r = 0; r < 10; ++r) {
+      rk[r][0] = k0;
+      rk[r][1] = k1;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint4 v = philox10(make_uint4(ctr[4 * j], ctr[4 * j + 1], ctr[4 * j + 2], ctr[4 * j + 3]), rk);
+    out[4 * j] = v.x;
+    out[4 * j + 1] = v.y;
+    out[4 * j + 2] = v.z;
+    out[4 * j + 3] = v.w;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers.
+// ---------------------------------------------------------------------------
+cudaError_t launch_move_bin(const SysDev* systems, const MoveTile* tiles, int n_tiles, int threads,
+                            const unsigned long long* step_base, int step_offset, int bin, cudaStream_t s) {
+  k_move_bin<<<n_tiles, threads, 0, s>>>(systems, tiles, step_base, step_offset, bin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_move_generic(const SysDev* systems, int sys, int64_t n_poly, int N,
+                                const unsigned long long* step_base, int step_offset, int sm_count,
+                                cudaStream_t s) {
+  for (int set = 0; set < 2; ++set) {
+    const int64_t work = n_poly * ((N - set + 1) / 2);
+    int blocks = (int)((work + 255) / 256);
+    if (blocks > sm_count * 8) blocks = sm_count * 8;
+    if (blocks < 1) blocks = 1;
+    k_move_set_generic<<<blocks, 256, 0, s>>>(systems, sys, step_base, step_offset, set);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const SysDev* systems, int sys, int64_t n_b, const unsigned long long* step_base,
+                       int step_offset, int sm_count, cudaStream_t s) {
+  const int threads = 512;
+  int64_t blocks = (n_b + threads - 1) / threads;
+  if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
+  if (blocks < 1) blocks = 1;
+  k_bin<<<(unsigned)blocks, threads, 0, s>>>(systems, sys, step_base, step_offset);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field(const SysDev* systems, const CellTile* tiles, int n_tiles, const unsigned long long* step_base,
+                         int step_offset, cudaStream_t s) {
+  k_field<<<n_tiles, 256, 0, s>>>(systems, tiles, step_base, step_offset);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_from_phi(const SysDev* systems, int sys, const float* phi, int sm_count, cudaStream_t s) {
+  k_field_from_phi<<<sm_count * 4, 256, 0, s>>>(systems, sys, phi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(unsigned long long* step_base, long long n, cudaStream_t s) {
+  k_advance_step<<<1, 32, 0, s>>>(step_base, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const SysDev* systems, int sys, int64_t n_poly, cudaStream_t s) {
+  const int threads = 128;
+  const int64_t blocks = (n_poly + threads - 1) / threads;
+  k_init<<<(unsigned)blocks, threads, 0, s>>>(systems, sys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_state(const SysDev* systems, int sys, float* pos, int16_t* img, int sm_count, cudaStream_t s) {
+  k_gather_state<<<sm_count * 8, 256, 0, s>>>(systems, sys, pos, img);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_state(const SysDev* systems, int sys, const float* pos, const int16_t* img, int sm_count,
+                                 cudaStream_t s) {
+  k_scatter_state<<<sm_count * 8, 256, 0, s>>>(systems, sys, pos, img);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const SysDev* systems, int sys, int* err, int sm_count, cudaStream_t s) {
+  k_validate<<<sm_count * 4, 256, 0, s>>>(systems, sys, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_pos(const float* pos, int64_t n, const float* L, int* err, int sm_count,
+                                cudaStream_t s) {
+  k_validate_pos<<<sm_count * 4, 256, 0, s>>>(pos, n, L[0], L[1], L[2], err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_acc(const SysDev* systems, int sys, unsigned long long* out, cudaStream_t s) {
+  k_sum_acc<<<1, 1024, 0, s>>>(systems, sys, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_acc(const SysDev* systems, int sys, cudaStream_t s) {
+  k_zero_acc<<<1, 256, 0, s>>>(systems, sys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observables(const SysDev* systems, int sys, const unsigned long long* step_base, double* out,
+                               unsigned long long* acc_out, int sm_count, cudaStream_t s) {
+  k_obs_chains<<<sm_count * 4, 256, 0, s>>>(systems, sys, out);
+  k_obs_cells<<<sm_count * 4, 256, 0, s>>>(systems, sys, step_base, out, acc_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_structure_factor(const SysDev* systems, int sys, int nq, const int32_t* m, double* out,
+                                    int sm_count, cudaStream_t s) {
+  k_structure_factor<<<sm_count * 4, 256, 0, s>>>(systems, sys, nq, m, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t s) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  k_philox<<<(unsigned)blocks, 256, 0, s>>>(ctr, key, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace soma

@@ -1,0 +1,57 @@
+// soma_launch.h -- host-side launchers of the kernels (internal to libsoma).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "soma_internal.cuh"
+
+namespace soma {
+
+cudaError_t launch_move_bin(const SysDev* systems, const MoveTile* tiles, int n_tiles, int threads,
+                            const unsigned long long* step_base, int step_offset, int bin, cudaStream_t s);
+cudaError_t launch_move_generic(const SysDev* systems, int sys, int64_t n_poly, int N,
+                                const unsigned long long* step_base, int step_offset, int sm_count,
+                                cudaStream_t s);
+cudaError_t launch_bin(const SysDev* systems, int sys, int64_t n_b, const unsigned long long* step_base,
+                       int step_offset, int sm_count, cudaStream_t s);
+cudaError_t launch_field(const SysDev* systems, const CellTile* tiles, int n_tiles,
+                         const unsigned long long* step_base, int step_offset, cudaStream_t s);
+cudaError_t launch_field_from_phi(const SysDev* systems, int sys, const float* phi, int sm_count, cudaStream_t s);
+cudaError_t launch_advance(unsigned long long* step_base, long long n, cudaStream_t s);
+cudaError_t launch_init(const SysDev* systems, int sys, int64_t n_poly, cudaStream_t s);
+cudaError_t launch_gather_state(const SysDev* systems, int sys, float* pos, int16_t* img, int sm_count,
+                                cudaStream_t s);
+cudaError_t launch_scatter_state(const SysDev* systems, int sys, const float* pos, const int16_t* img,
+                                 int sm_count, cudaStream_t s);
+cudaError_t launch_validate(const SysDev* systems, int sys, int* err, int sm_count, cudaStream_t s);
+cudaError_t launch_validate_pos(const float* pos, int64_t n, const float* L, int* err, int sm_count,
+                                cudaStream_t s);
+cudaError_t launch_sum_acc(const SysDev* systems, int sys, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_zero_acc(const SysDev* systems, int sys, cudaStream_t s);
+cudaError_t launch_observables(const SysDev* systems, int sys, const unsigned long long* step_base, double* out,
+                               unsigned long long* acc_out, int sm_count, cudaStream_t s);
+cudaError_t launch_structure_factor(const SysDev* systems, int sys, int nq, const int32_t* m, double* out,
+                                    int sm_count, cudaStream_t s);
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t s);
+
+// Chain reorder (soma_sort.cu): sort the chains of every system by the
+// Morton key of their first bead's cell and permute positions, images and
+// chain ids into the alternate buffers, then swap the buffer pointers in the
+// device-side system table.
+struct SortWork {
+  unsigned long long* keys_in;
+  unsigned long long* keys_out;
+  uint32_t* vals_in;
+  uint32_t* vals_out;
+  void* temp;
+  size_t temp_bytes;
+  int32_t* chain_sys;  // global chain -> system
+  int64_t n_chains;
+  int end_bit;
+};
+size_t sort_temp_bytes(int64_t n_chains, int end_bit);
+cudaError_t launch_reorder(SysDev* systems, int n_sys, const SortWork& w, int sm_count, cudaStream_t s);
+
+}  // namespace soma

@@ -1,0 +1,98 @@
+// soma_sort.cu -- periodic chain reorder.
+//
+// Chains are sorted by the Morton (Z-order) key of their first bead's
+// position, quantised to 1024 steps per box edge, so that chains stored
+// next to each other sit next to each other in space: the field gathers of
+// the move kernel and the count atomics of the histogram then touch compact,
+// cache-resident cell ranges.  The random numbers follow the logical chain id
+// carried along in chain_id, so a reorder never changes the trajectory.
+// The sort itself is CUB's device radix sort (a library primitive); keys,
+// permutation and pointer swap are kernels of this file.
+#include <cub/device/device_radix_sort.cuh>
+#include <cuda_runtime.h>
+
+#include "soma_launch.h"
+
+namespace soma {
+
+__device__ __forceinline__ unsigned long long spread3(uint32_t v) {
+  unsigned long long x = v & 0x3FFu;
+  x = (x | (x << 16)) & 0x030000FFull;
+  x = (x | (x << 8)) & 0x0300F00Full;
+  x = (x | (x << 4)) & 0x030C30C3ull;
+  x = (x | (x << 2)) & 0x09249249ull;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t quant1024(float x, float invL) {
+  int q = (int)(x * invL * 1024.f);
+  return (uint32_t)(q < 0 ? 0 : (q > 1023 ? 1023 : q));
+}
+
+__global__ void k_sort_keys(const SysDev* __restrict__ systems, const int32_t* __restrict__ chain_sys,
+                            int64_t n_chains, unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n_chains; g += (int64_t)gridDim.x * blockDim.x) {
+    const int s = chain_sys[g];
+    const SysDev& S = systems[s];
+    const int64_t b = (g - S.chain_base) * S.N;
+    const uint32_t qx = quant1024(S.x[b], S.invL[0]);
+    const uint32_t qy = quant1024(S.y[b], S.invL[1]);
+    const uint32_t qz = quant1024(S.z[b], S.invL[2]);
+    keys[g] = ((unsigned long long)s << 40) | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    vals[g] = (uint32_t)g;
+  }
+}
+
+// One warp per chain in the new order: copy its beads from the old slot.
+__global__ void k_permute(const SysDev* __restrict__ systems, const int32_t* __restrict__ chain_sys,
+                          int64_t n_chains, const uint32_t* __restrict__ perm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_chains; j += warps) {
+    const int s = chain_sys[j];
+    const SysDev& S = systems[s];
+    const int64_t old_slot = (int64_t)perm[j] - S.chain_base, new_slot = j - S.chain_base;
+    const int N = S.N;
+    for (int i = lane; i < N; i += 32) {
+      const int64_t src = old_slot * N + i, dst = new_slot * N + i;
+      S.x_alt[dst] = S.x[src];
+      S.y_alt[dst] = S.y[src];
+      S.z_alt[dst] = S.z[src];
+      reinterpret_cast<short4*>(S.img_alt)[dst] = reinterpret_cast<const short4*>(S.img)[src];
+    }
+    if (lane == 0) S.chain_id_alt[new_slot] = S.chain_id[old_slot];
+  }
+}
+
+__global__ void k_swap_buffers(SysDev* systems, int n_sys) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_sys) return;
+  SysDev& S = systems[s];
+  float* t;
+  t = S.x; S.x = S.x_alt; S.x_alt = t;
+  t = S.y; S.y = S.y_alt; S.y_alt = t;
+  t = S.z; S.z = S.z_alt; S.z_alt = t;
+  int16_t* ti = S.img; S.img = S.img_alt; S.img_alt = ti;
+  uint32_t* tc = S.chain_id; S.chain_id = S.chain_id_alt; S.chain_id_alt = tc;
+}
+
+size_t sort_temp_bytes(int64_t n_chains, int end_bit) {
+  size_t bytes = 0;
+  cub::DeviceRadixSort::SortPairs(nullptr, bytes, (const unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                  (const uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)n_chains, 0, end_bit);
+  return bytes;
+}
+
+cudaError_t launch_reorder(SysDev* systems, int n_sys, const SortWork& w, int sm_count, cudaStream_t s) {
+  const int blocks = sm_count * 8;
+  k_sort_keys<<<blocks, 256, 0, s>>>(systems, w.chain_sys, w.n_chains, w.keys_in, w.vals_in);
+  size_t bytes = w.temp_bytes;
+  cudaError_t e = cub::DeviceRadixSort::SortPairs(w.temp, bytes, w.keys_in, w.keys_out, w.vals_in, w.vals_out,
+                                                  w.n_chains, 0, w.end_bit, s);
+  if (e != cudaSuccess) return e;
+  k_permute<<<blocks, 256, 0, s>>>(systems, w.chain_sys, w.n_chains, w.vals_out);
+  k_swap_buffers<<<(n_sys + 63) / 64, 64, 0, s>>>(systems, n_sys);
+  return cudaGetLastError();
+}
+
+}  // namespace soma

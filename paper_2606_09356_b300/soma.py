@@ -1,0 +1,339 @@
+"""Thin ctypes binding of libsoma (include/soma.h), same names as the C ABI.
+
+Argument marshalling only: every step of the Monte Carlo path runs in the
+CUDA kernels of libsoma.so.  There is no CPU fallback; importing this module
+without the built library raises.
+
+Module-level functions mirror the C calls one to one (``soma_create``,
+``soma_mc_steps`` ...).  ``System`` describes one melt and ``Handle`` wraps a
+handle with numpy-returning convenience methods.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBRARY = os.path.join(_HERE, "libsoma.so")
+
+SOMA_OK = 0
+SOMA_EINVAL = -1
+SOMA_ENOMEM = -2
+SOMA_ECUDA = -3
+SOMA_ETIMEOUT = -4
+SOMA_EDEVICE_CHECK = -5
+SOMA_ESTATE = -6
+SOMA_ENOTSUP = -7
+SOMA_HOST = 0
+SOMA_DEVICE = 1
+SOMA_HIST_AUTO = 0
+SOMA_HIST_FUSED = 1
+SOMA_HIST_SEPARATE = 2
+
+# every entry point declared in include/soma.h
+EXPORTS = (
+    "soma_options_default", "soma_create", "soma_destroy", "soma_strerror", "soma_last_error",
+    "soma_mc_steps", "soma_sync", "soma_get_density", "soma_get_fields", "soma_set_density",
+    "soma_freeze_fields", "soma_get_state", "soma_set_state", "soma_observables", "soma_get_accepted",
+    "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
+    "soma_philox4x32",
+)
+
+
+class SomaError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {soma_strerror(code)} ({code})")
+
+
+class soma_system_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_poly", ctypes.c_int32), ("N", ctypes.c_int32), ("n_A", ctypes.c_int32),
+        ("system_id", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("reserved1", ctypes.c_int32),
+        ("box", ctypes.c_double * 3), ("chiN", ctypes.c_double), ("kappaN", ctypes.c_double),
+        ("A", ctypes.c_double), ("seed", ctypes.c_uint64),
+    ]
+
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class soma_options(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int32), ("sort_interval", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+        ("hist_mode", ctypes.c_int32), ("graph_steps", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
+        ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class soma_obs(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_uint64), ("accepted", ctypes.c_uint64), ("attempted", ctypes.c_uint64),
+        ("acc", ctypes.c_double), ("Re2", ctypes.c_double), ("Rg2", ctypes.c_double),
+        ("Ebond", ctypes.c_double), ("Enb", ctypes.c_double),
+    ]
+
+
+class soma_info(ctypes.Structure):
+    _fields_ = [
+        ("n_beads", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("k_b", ctypes.c_double),
+        ("A", ctypes.c_double), ("rho_bar", ctypes.c_double), ("lanes_per_chain", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32), ("sort_interval", ctypes.c_int32), ("hist_mode", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load libsoma.so (built in-tree by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIBRARY
+    if not os.path.exists(path):
+        raise ImportError(f"libsoma.so not built at {path}: run paper_2606_09356_b300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, sz, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_uint64
+    L.soma_options_default.argtypes = [ctypes.POINTER(soma_options)]
+    L.soma_create.argtypes = [ctypes.POINTER(soma_system_desc), i32, ctypes.POINTER(soma_options), ctypes.POINTER(vp)]
+    L.soma_destroy.argtypes = [vp]
+    L.soma_destroy.restype = None
+    L.soma_strerror.argtypes = [i32]
+    L.soma_strerror.restype = ctypes.c_char_p
+    L.soma_last_error.argtypes = [vp]
+    L.soma_mc_steps.argtypes = [vp, i64, vp]
+    L.soma_sync.argtypes = [vp, vp]
+    L.soma_get_density.argtypes = [vp, i32, vp, sz, i32]
+    L.soma_get_fields.argtypes = [vp, i32, vp, sz, i32]
+    L.soma_set_density.argtypes = [vp, i32, vp, sz, i32]
+    L.soma_freeze_fields.argtypes = [vp, i32, vp, sz, i32]
+    L.soma_get_state.argtypes = [vp, i32, vp, vp, ctypes.POINTER(u64), i32]
+    L.soma_set_state.argtypes = [vp, i32, vp, vp, u64, i32]
+    L.soma_observables.argtypes = [vp, i32, ctypes.POINTER(soma_obs)]
+    L.soma_get_accepted.argtypes = [vp, i32, ctypes.POINTER(u64)]
+    L.soma_structure_factor.argtypes = [vp, i32, i32, vp, vp]
+    L.soma_reorder.argtypes = [vp, vp]
+    L.soma_get_info.argtypes = [vp, i32, ctypes.POINTER(soma_info)]
+    L.soma_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]
+    L.soma_autotune.argtypes = [vp]
+    L.soma_philox4x32.argtypes = [vp, vp, vp, sz]
+    for name in EXPORTS:
+        if name not in ("soma_destroy", "soma_strerror"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor on the device
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _where(a):
+    return SOMA_DEVICE if hasattr(a, "data_ptr") and a.is_cuda else SOMA_HOST
+
+
+def _check(code, what):
+    if code != SOMA_OK:
+        raise SomaError(code, what)
+
+
+# ---------------------------------------------------------------------------
+# one-to-one C calls
+# ---------------------------------------------------------------------------
+def soma_strerror(code):
+    return load_library().soma_strerror(code).decode()
+
+
+def soma_options_default():
+    o = soma_options()
+    _check(load_library().soma_options_default(ctypes.byref(o)), "soma_options_default")
+    return o
+
+
+def soma_create(descs, options=None):
+    L = load_library()
+    arr = (soma_system_desc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    rc = L.soma_create(arr, len(descs), ctypes.byref(options) if options is not None else None, ctypes.byref(h))
+    _check(rc, "soma_create")
+    return h
+
+
+def soma_destroy(h):
+    load_library().soma_destroy(h)
+
+
+def soma_mc_steps(h, n_steps, stream=None):
+    _check(load_library().soma_mc_steps(h, int(n_steps), stream), "soma_mc_steps")
+
+
+def soma_philox4x32(ctr, key):
+    """Device Philox4x32-10 of counters [n,4] under keys [n,2] (uint32)."""
+    ctr = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, np.uint32).reshape(-1, 2)
+    out = np.zeros_like(ctr)
+    _check(load_library().soma_philox4x32(_ptr(ctr), _ptr(key), _ptr(out), len(ctr)), "soma_philox4x32")
+    return out
+
+
+def soma_sync(h, stream=None):
+    _check(load_library().soma_sync(h, stream), "soma_sync")
+
+
+# ---------------------------------------------------------------------------
+class System:
+    """One AB diblock melt (the fields of soma_system_desc)."""
+
+    def __init__(self, n_poly, N, n_A, box, grid, chiN, kappaN, A=0.0, seed=1, system_id=0):
+        self.n_poly, self.N, self.n_A = int(n_poly), int(N), int(n_A)
+        self.system_id = int(system_id)
+        self.box = tuple(float(b) for b in box)
+        self.grid = tuple(int(g) for g in grid)
+        self.chiN, self.kappaN, self.A, self.seed = float(chiN), float(kappaN), float(A), int(seed)
+
+    @property
+    def n_beads(self):
+        return self.n_poly * self.N
+
+    @property
+    def n_cells(self):
+        return self.grid[0] * self.grid[1] * self.grid[2]
+
+    def desc(self):
+        d = soma_system_desc()
+        d.n_poly, d.N, d.n_A, d.system_id = self.n_poly, self.N, self.n_A, self.system_id
+        for a in range(3):
+            d.grid[a] = self.grid[a]
+            d.box[a] = self.box[a]
+        d.chiN, d.kappaN, d.A, d.seed = self.chiN, self.kappaN, self.A, self.seed
+        return d
+
+
+class Handle:
+    """Owns a soma_handle for a list of systems that step together."""
+
+    def __init__(self, systems, **options):
+        if isinstance(systems, System):
+            systems = [systems]
+        self.systems = list(systems)
+        self.lib = load_library()
+        o = soma_options_default()
+        for k, v in options.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown soma option {k}")
+            setattr(o, k, v)
+        self.h = soma_create([s.desc() for s in self.systems], o)
+
+    def close(self):
+        if self.h:
+            soma_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- stepping --------------------------------------------------------
+    def mc_steps(self, n, stream=None):
+        soma_mc_steps(self.h, n, stream)
+
+    def sync(self, stream=None):
+        soma_sync(self.h, stream)
+
+    def reorder(self, stream=None):
+        _check(self.lib.soma_reorder(self.h, stream), "soma_reorder")
+
+    def autotune(self):
+        _check(self.lib.soma_autotune(self.h), "soma_autotune")
+
+    # -- grids -----------------------------------------------------------
+    def get_density(self, sys=0, out=None):
+        nc = self.systems[sys].n_cells
+        out = np.zeros((2, nc), np.uint32) if out is None else out
+        _check(self.lib.soma_get_density(self.h, sys, _ptr(out), 2 * nc, _where(out)), "soma_get_density")
+        return out
+
+    def get_fields(self, sys=0):
+        nc = self.systems[sys].n_cells
+        out = np.zeros((2, nc), np.float32)
+        _check(self.lib.soma_get_fields(self.h, sys, _ptr(out), 2 * nc, SOMA_HOST), "soma_get_fields")
+        return out
+
+    def set_density(self, phi, sys=0):
+        phi = np.ascontiguousarray(phi, np.float32)
+        _check(self.lib.soma_set_density(self.h, sys, _ptr(phi), phi.size, SOMA_HOST), "soma_set_density")
+
+    def freeze_fields(self, w, sys=0):
+        if w is None:
+            _check(self.lib.soma_freeze_fields(self.h, sys, None, 0, SOMA_HOST), "soma_freeze_fields")
+            return
+        w = np.ascontiguousarray(w, np.float32)
+        _check(self.lib.soma_freeze_fields(self.h, sys, _ptr(w), w.size, SOMA_HOST), "soma_freeze_fields")
+
+    # -- state -----------------------------------------------------------
+    def get_state(self, sys=0, pos=None, img=None):
+        nb = self.systems[sys].n_beads
+        pos = np.zeros((nb, 3), np.float32) if pos is None else pos
+        img = np.zeros((nb, 3), np.int16) if img is None else img
+        step = ctypes.c_uint64()
+        _check(self.lib.soma_get_state(self.h, sys, _ptr(pos), _ptr(img), ctypes.byref(step), _where(pos)),
+               "soma_get_state")
+        return pos, img, step.value
+
+    def set_state(self, pos, img, step, sys=0):
+        where = _where(pos)
+        if where == SOMA_HOST:
+            pos = np.ascontiguousarray(pos, np.float32)
+            img = np.ascontiguousarray(img, np.int16)
+        _check(self.lib.soma_set_state(self.h, sys, _ptr(pos), _ptr(img), int(step), where), "soma_set_state")
+
+    def unwrapped(self, sys=0):
+        """FP64 unwrapped positions x + image * L in logical order."""
+        pos, img, _ = self.get_state(sys)
+        return pos.astype(np.float64) + img.astype(np.float64) * np.array(self.systems[sys].box)
+
+    # -- measurements ----------------------------------------------------
+    def observables(self, sys=0):
+        o = soma_obs()
+        _check(self.lib.soma_observables(self.h, sys, ctypes.byref(o)), "soma_observables")
+        nb = self.systems[sys].n_beads
+        return dict(step=o.step, accepted=o.accepted, attempted=o.attempted, acc=o.acc, Re2=o.Re2, Rg2=o.Rg2,
+                    Ebond=o.Ebond, Enb=o.Enb, n_beads=nb)
+
+    def accepted(self, sys=0):
+        a = ctypes.c_uint64()
+        _check(self.lib.soma_get_accepted(self.h, sys, ctypes.byref(a)), "soma_get_accepted")
+        return a.value
+
+    def structure_factor(self, m, sys=0):
+        m = np.ascontiguousarray(m, np.int32).reshape(-1, 3)
+        S = np.zeros(len(m), np.float64)
+        _check(self.lib.soma_structure_factor(self.h, sys, len(m), _ptr(m), _ptr(S)), "soma_structure_factor")
+        return S
+
+    def info(self, sys=0):
+        i = soma_info()
+        _check(self.lib.soma_get_info(self.h, sys, ctypes.byref(i)), "soma_get_info")
+        return {f: getattr(i, f) for f, _ in soma_info._fields_}
+
+    def kernel_times(self, reset=False):
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
+        _check(self.lib.soma_kernel_times(self.h, ms, n, int(reset)), "soma_kernel_times")
+        names = ("move", "bin", "field", "reorder")
+        return {k: (ms[i], n[i]) for i, k in enumerate(names)}

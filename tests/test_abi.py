@@ -1,0 +1,99 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/soma.h; struct layouts agree between C and the binding; argument
+validation answers without touching a GPU.  CPU only."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2606_09356_b300 import build as _build
+from paper_2606_09356_b300 import soma
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "soma.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\s*\*)\s+(soma_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return soma.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in soma.h but not exported"
+    assert set(names) == set(soma.EXPORTS), "binding export list differs from the header"
+
+
+def test_exported_symbols_are_c_linkage(lib):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", soma.LIBRARY]).decode()
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for n in declared_functions():
+        assert n in syms
+
+
+def test_struct_layouts_match_c():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "soma.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(soma_system_desc), sizeof(soma_options), sizeof(soma_obs),
+         sizeof(soma_info), offsetof(soma_system_desc, box), offsetof(soma_system_desc, seed),
+         offsetof(soma_options, alloc));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as td:
+        c = os.path.join(td, "s.c")
+        exe = os.path.join(td, "s")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", exe, c])
+        got = [int(v) for v in subprocess.check_output([exe]).split()]
+    exp = [ctypes.sizeof(soma.soma_system_desc), ctypes.sizeof(soma.soma_options), ctypes.sizeof(soma.soma_obs),
+           ctypes.sizeof(soma.soma_info), soma.soma_system_desc.box.offset, soma.soma_system_desc.seed.offset,
+           soma.soma_options.alloc.offset]
+    assert got == exp
+
+
+def test_strerror_and_defaults(lib):
+    assert soma.soma_strerror(0) == "ok"
+    assert "invalid" in soma.soma_strerror(soma.SOMA_EINVAL)
+    o = soma.soma_options_default()
+    assert o.device == -1 and o.graph_steps > 0 and o.hist_mode == soma.SOMA_HIST_AUTO
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n_poly=0), dict(N=0), dict(n_A=33), dict(n_A=-1), dict(grid=(0, 4, 4)), dict(box=(0.0, 4.0, 4.0)),
+    dict(box=(1.0, 4.0, 4.0)),          # shorter than two bond tails
+    dict(N=1, n_A=1, A=0.0),            # no default proposal without bonds
+    dict(A=5.0),                        # proposal wider than the box
+    dict(chiN=float("nan")),
+])
+def test_create_rejects_bad_descriptors_without_gpu(lib, bad):
+    kw = dict(n_poly=8, N=32, n_A=16, box=(4.0, 4.0, 4.0), grid=(4, 4, 4), chiN=1.0, kappaN=1.0)
+    kw.update(bad)
+    d = soma.System(**kw).desc()
+    arr = (soma.soma_system_desc * 1)(d)
+    h = ctypes.c_void_p()
+    assert lib.soma_create(arr, 1, None, ctypes.byref(h)) == soma.SOMA_EINVAL
+    assert not h.value
+
+
+def test_null_arguments(lib):
+    assert lib.soma_create(None, 1, None, None) == soma.SOMA_EINVAL
+    assert lib.soma_mc_steps(None, 1, None) == soma.SOMA_EINVAL
+    assert lib.soma_observables(None, 0, None) == soma.SOMA_EINVAL
+    lib.soma_destroy(None)
+    assert lib.soma_philox4x32(None, None, None, 0) == soma.SOMA_OK

@@ -1,0 +1,92 @@
+"""API behaviour on a GPU: errors, coupling writes, frozen fields, info."""
+import numpy as np
+import pytest
+
+import gpu_util as G
+from paper_2606_09356_b300 import soma, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    G.lib()
+
+
+def test_set_state_rejects_positions_outside_the_box_and_keeps_state():
+    s = soma.System(**workloads.system_kwargs("config0"))
+    with soma.Handle(s) as h:
+        pos, img, step = h.get_state()
+        bad = pos.copy()
+        bad[5, 1] = 4.0
+        with pytest.raises(soma.SomaError) as e:
+            h.set_state(bad, img, step)
+        assert e.value.code == soma.SOMA_EINVAL
+        p2, i2, _ = h.get_state()
+        assert np.array_equal(p2, pos) and np.array_equal(i2, img)
+        h.mc_steps(2)  # still usable
+        assert h.get_state()[2] == 2
+
+
+def test_argument_errors():
+    s = soma.System(**workloads.system_kwargs("config0"))
+    with soma.Handle(s) as h:
+        lib = h.lib
+        buf = np.zeros(10, np.uint32)
+        assert lib.soma_get_density(h.h, 0, soma._ptr(buf), 10, 0) == soma.SOMA_EINVAL
+        assert lib.soma_get_density(h.h, 3, soma._ptr(buf), 10, 0) == soma.SOMA_EINVAL
+        assert lib.soma_mc_steps(h.h, -1, None) == soma.SOMA_EINVAL
+        assert lib.soma_mc_steps(h.h, 0xFFFFFFFF, None) == soma.SOMA_EINVAL
+        assert lib.soma_last_error(h.h) == soma.SOMA_OK
+
+
+def test_set_density_drives_next_fields():
+    s = soma.System(**workloads.system_kwargs("config0"))
+    orc = G.oracle_for(s)
+    rng = np.random.default_rng(3)
+    phi = rng.uniform(0.0, 1.0, size=(2, s.n_cells)).astype(np.float32)
+    with soma.Handle(s) as h:
+        h.set_density(phi)
+        w = h.get_fields()
+        w64 = orc.fields_from_phi(phi.astype(np.float64))
+        assert np.allclose(w, w64, rtol=1e-6, atol=1e-5)
+        # the next step moves against these fields; the field kernel then rebuilds from counts
+        G.compare_step(h, w=w64)
+        counts = h.get_density()
+        assert np.allclose(h.get_fields(), orc.fields(counts), rtol=1e-5, atol=1e-5)
+
+
+def test_freeze_and_release_fields():
+    s = soma.System(**workloads.system_kwargs("config0"))
+    orc = G.oracle_for(s)
+    w = np.full((2, s.n_cells), 0.25, np.float32)
+    with soma.Handle(s) as h:
+        h.freeze_fields(w)
+        h.mc_steps(3)
+        assert np.array_equal(h.get_fields(), w)
+        h.freeze_fields(None)
+        assert np.allclose(h.get_fields(), orc.fields(h.get_density()), rtol=1e-5, atol=1e-5)
+
+
+def test_info_and_kernel_timing():
+    s = soma.System(**workloads.system_kwargs("config0"))
+    with soma.Handle(s, kernel_timing=1, sort_interval=4) as h:
+        h.kernel_times(reset=True)
+        info = h.info()
+        assert info["n_beads"] == 16384 and info["n_cells"] == 4096 and info["lanes_per_chain"] == 16
+        assert info["k_b"] == 46.5 and abs(info["A"] - 0.5 / np.sqrt(31)) < 1e-7
+        h.mc_steps(10)
+        t = h.kernel_times()
+        assert t["move"][1] == 10 and t["field"][1] == 10 and t["reorder"][1] == 2
+        assert t["move"][0] > 0 and t["field"][0] > 0
+
+
+def test_many_handles_and_destroy():
+    s = soma.System(**workloads.system_kwargs("config0"))
+    hs = [soma.Handle(soma.System(**{**workloads.system_kwargs("config0"), "seed": k})) for k in range(4)]
+    for h in hs:
+        h.mc_steps(3)
+    st = [h.get_state()[0] for h in hs]
+    assert not np.array_equal(st[0], st[1])
+    for h in hs:
+        h.close()

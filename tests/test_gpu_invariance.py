@@ -1,0 +1,84 @@
+"""Properties that hold bit for bit on the GPU (needs a GPU): the trajectory
+does not depend on launch shape, histogram strategy, graph capture, chain
+reorders, batching with other systems, or a checkpoint round trip."""
+import numpy as np
+import pytest
+
+import gpu_util as G
+from paper_2606_09356_b300 import soma, workloads
+
+pytestmark = pytest.mark.gpu
+
+SMALL = dict(n_poly=777, N=32, n_A=16, box=(4.0, 4.0, 5.0), grid=(16, 16, 20), chiN=20.0, kappaN=50.0, seed=3)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    G.lib()
+
+
+def _run(system, steps, **opts):
+    with soma.Handle(system, **opts) as h:
+        h.mc_steps(steps)
+        pos, img, step = h.get_state()
+        return pos, img, h.get_density(), h.accepted(), step
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        if isinstance(x, np.ndarray):
+            assert np.array_equal(x, y)
+        else:
+            assert x == y
+
+
+def test_launch_shape_histogram_graph_and_reorder_invariance():
+    s = soma.System(**SMALL)
+    ref = _run(s, 40, block_threads=256, hist_mode=soma.SOMA_HIST_FUSED, graph_steps=0, sort_interval=0)
+    for opts in (dict(block_threads=128), dict(block_threads=512), dict(hist_mode=soma.SOMA_HIST_SEPARATE),
+                 dict(graph_steps=16), dict(graph_steps=7, sort_interval=5), dict(sort_interval=1),
+                 dict(autotune=1)):
+        _same(ref, _run(s, 40, **{**dict(graph_steps=0, sort_interval=0), **opts}))
+
+
+def test_batched_equals_plain():
+    specs = workloads.batch64()[:5]
+    systems = [soma.System(**{k: v for k, v in d.items() if k != "f_A"}) for d in specs]
+    # shrink the chain counts to keep the test short
+    for s in systems:
+        s.n_poly = min(s.n_poly, 3000)
+    with soma.Handle(systems) as hb:
+        hb.mc_steps(25)
+        batched = [(hb.get_state(i)[0], hb.get_state(i)[1], hb.get_density(i), hb.accepted(i)) for i in range(5)]
+    for i, s in enumerate(systems):
+        with soma.Handle(s) as h:
+            h.mc_steps(25)
+            solo = (h.get_state()[0], h.get_state()[1], h.get_density(), h.accepted())
+        _same(batched[i], solo)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    s = soma.System(**SMALL)
+    ref = _run(s, 30)
+    with soma.Handle(s) as h:
+        h.mc_steps(13)
+        pos, img, step = h.get_state()
+        acc13 = h.accepted()
+    with soma.Handle(soma.System(**{**SMALL, "seed": 3})) as h2:
+        h2.set_state(pos, img, step)
+        h2.mc_steps(17)
+        p2, i2, st2 = h2.get_state()
+        assert st2 == 30
+        assert np.array_equal(p2, ref[0]) and np.array_equal(i2, ref[1])
+        assert np.array_equal(h2.get_density(), ref[2])
+        assert h2.accepted() + acc13 == ref[3]
+
+
+def test_reorder_keeps_logical_state():
+    s = soma.System(**SMALL)
+    with soma.Handle(s, sort_interval=0) as h:
+        h.mc_steps(10)
+        a = h.get_state()
+        h.reorder()
+        b = h.get_state()
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

@@ -1,0 +1,154 @@
+"""CUDA path against the oracle, element by element (needs a GPU).
+
+Kernel (b) is compared bit for bit (integer counts of identical positions),
+kernel (c) within a bound derived from its FP32 arithmetic, kernel (a) by
+accept decisions and positions of whole steps started from identical states."""
+import numpy as np
+import pytest
+
+import gpu_util as G
+from oracle import Oracle
+from paper_2606_09356_b300 import soma, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    G.lib()
+
+
+def test_device_philox_matches_oracle():
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 2**32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(4096, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[:2] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4]
+    key[:2] = [[0, 0], [0xFFFFFFFF] * 2]
+    assert np.array_equal(soma.soma_philox4x32(ctr, key), Oracle.philox(ctr, key))
+
+
+def _fields_bound(orc, counts):
+    # |w32 - w64| <= 8 eps32 (|chiN phi| + kappaN (phiA + phiB + 1)) / N
+    _, _, rho = orc.params()
+    phiA, phiB = counts[0] / rho, counts[1] / rho
+    d = orc.d
+    scale = (abs(d.chiN) * np.maximum(phiA, phiB) + abs(d.kappaN) * (phiA + phiB + 1.0)) / d.N
+    return 8 * np.finfo(np.float32).eps * (scale + 1e-30)
+
+
+@pytest.mark.parametrize("hist", [soma.SOMA_HIST_FUSED, soma.SOMA_HIST_SEPARATE])
+def test_density_and_fields_config0(hist):
+    sysm = soma.System(**workloads.system_kwargs("config0"))
+    orc = G.oracle_for(sysm)
+    with soma.Handle(sysm, hist_mode=hist) as h:
+        for _ in range(3):
+            X, _ = G.unwrapped(h)
+            counts = h.get_density()
+            assert np.array_equal(counts, orc.density(X))
+            assert counts[0].sum() == 512 * 16 and counts[1].sum() == 512 * 16
+            w = h.get_fields()
+            w64 = orc.fields(counts)
+            assert np.all(np.abs(w - w64) <= _fields_bound(orc, counts))
+            h.mc_steps(5)
+
+
+def test_step_parity_config0_ten_steps():
+    sysm = soma.System(**workloads.system_kwargs("config0"))
+    with soma.Handle(sysm, graph_steps=0) as h:
+        tot_sus = 0
+        for _ in range(10):
+            st = G.compare_step(h)
+            assert abs(st["acc_gpu"] - st["acc_orc"]) <= st["suspect"]
+            tot_sus += st["suspect"]
+        assert tot_sus < 0.001 * 10 * sysm.n_beads
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n_poly=37, N=7, n_A=3, box=(4.0, 4.5, 5.0), grid=(16, 18, 20), chiN=15.0, kappaN=40.0),    # odd N, ragged
+    dict(n_poly=301, N=16, n_A=8, box=(2.5, 2.5, 3.0), grid=(10, 10, 12), chiN=20.0, kappaN=50.0),
+    dict(n_poly=50, N=64, n_A=19, box=(2.0, 2.0, 2.0), grid=(16, 16, 16), chiN=25.0, kappaN=50.0),  # one warp per chain
+    dict(n_poly=40, N=80, n_A=30, box=(2.0, 2.0, 2.0), grid=(8, 8, 8), chiN=25.0, kappaN=50.0),     # generic path
+    dict(n_poly=9, N=33, n_A=33, box=(2.0, 2.0, 2.0), grid=(4, 4, 4), chiN=0.0, kappaN=30.0),       # homopolymer
+    dict(n_poly=1, N=2, n_A=1, box=(12.0, 12.0, 12.0), grid=(3, 3, 3), chiN=5.0, kappaN=5.0),       # a single dimer
+    dict(n_poly=200, N=1, n_A=1, box=(2.0, 2.0, 2.0), grid=(4, 4, 4), chiN=5.0, kappaN=10.0, A=0.3),  # monomers
+])
+@pytest.mark.parametrize("threads", [128, 512])
+def test_step_parity_shapes(kw, threads):
+    sysm = soma.System(seed=7, **kw)
+    with soma.Handle(sysm, block_threads=threads, graph_steps=0) as h:
+        for _ in range(4):
+            G.compare_step(h)
+
+
+def _sampled_parity(name, n_sample, steps=2, **opts):
+    """Full-size system in the bench's launch configuration; the oracle
+    recomputes a sample of chains one by one with the full system's fields."""
+    sysm = soma.System(**workloads.system_kwargs(name))
+    orc = G.oracle_for(sysm)
+    k_b, _, _ = orc.params()
+    band = G.band_for(sysm, k_b)
+    rng = np.random.default_rng(17)
+    ids = np.sort(rng.choice(sysm.n_poly, n_sample, replace=False)).astype(np.uint32)
+    N = sysm.N
+    sel = (ids[:, None].astype(np.int64) * N + np.arange(N)[None, :]).reshape(-1)
+    with soma.Handle(sysm, **opts) as h:
+        h.mc_steps(3)
+        for _ in range(steps):
+            X0, step = G.unwrapped(h)
+            counts = h.get_density()
+            assert counts[0].sum() == sysm.n_poly * sysm.n_A
+            assert counts[1].sum() == sysm.n_poly * (N - sysm.n_A)
+            w = orc.fields(counts)
+            Xs = np.ascontiguousarray(X0[sel])
+            _, acc, margin, face = orc.mc_step_chains(Xs, ids, w, step, n_threads=G.NTHREADS)
+            h.mc_steps(1)
+            X1, _ = G.unwrapped(h)
+            moved = np.any(X1[sel] != X0[sel], axis=1)
+            face_tol = 8.0 * float(np.spacing(np.float32(max(sysm.box))))
+            sus = ((np.abs(margin) < band) | (face < face_tol)).reshape(-1, N)
+            spread = sus.copy()
+            spread[:, 1:] |= sus[:, :-1]
+            spread[:, :-1] |= sus[:, 1:]
+            ok = ~spread.reshape(-1)
+            assert not (ok & (moved != acc.astype(bool))).any()
+            dev = np.abs(X1[sel] - Xs)[ok] / np.array(sysm.box)
+            assert dev.max() <= 1e-5
+        # the whole grid: counts of the GPU's final positions, bit for bit
+        X1, _ = G.unwrapped(h)
+        assert np.array_equal(h.get_density(), orc.density(X1))
+
+
+def test_step_parity_config1_full_size_sampled():
+    _sampled_parity("config1", 4096)
+
+
+def test_step_parity_config2_full_size_sampled():
+    _sampled_parity("config2", 2048, steps=1)
+
+
+def test_observables_match_oracle():
+    sysm = soma.System(**workloads.system_kwargs("config0"))
+    orc = G.oracle_for(sysm)
+    with soma.Handle(sysm) as h:
+        h.mc_steps(7)
+        X, _ = G.unwrapped(h)
+        o = h.observables()
+        r = orc.observables(X)
+        for k in ("Re2", "Rg2", "Ebond", "Enb"):
+            assert o[k] == pytest.approx(r[k], rel=1e-9, abs=1e-9), k
+        assert o["step"] == 7 and o["attempted"] == 7 * sysm.n_beads
+        assert 0.3 < o["acc"] < 0.9
+
+
+def test_structure_factor_matches_oracle():
+    sysm = soma.System(**workloads.system_kwargs("config0"))
+    orc = G.oracle_for(sysm)
+    m = np.array([(x, y, z) for x in range(-3, 4) for y in range(-3, 4) for z in range(0, 4)
+                  if 0 < x * x + y * y + z * z <= 12], np.int32)
+    with soma.Handle(sysm) as h:
+        h.mc_steps(5)
+        X, _ = G.unwrapped(h)
+        S = h.structure_factor(m)
+        R = orc.structure_factor(X, m)
+        # FP32 phases of wrapped positions: |dphase| <= ~2e-6 rad per bead
+        assert np.allclose(S, R, rtol=2e-4, atol=2e-4)

@@ -1,0 +1,151 @@
+"""The CUDA path against closed forms and against the oracle's statistics
+(needs a GPU)."""
+import numpy as np
+import pytest
+
+import gpu_util as G
+import pins
+from paper_2606_09356_b300 import soma, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    G.lib()
+
+
+def test_initial_configuration_is_a_gaussian_chain_melt():
+    s = soma.System(n_poly=65536, N=32, n_A=16, box=(8.0, 8.0, 8.0), grid=(32, 32, 32), chiN=0.0, kappaN=0.0)
+    with soma.Handle(s) as h:
+        X, _ = G.unwrapped(h)
+        pos, img, _ = h.get_state()
+    p = X.reshape(-1, 32, 3)
+    b = np.diff(p, axis=1)
+    n = b.shape[0] * b.shape[1]
+    for a in range(3):
+        assert abs((b[:, :, a] ** 2).mean() * 93 - 1.0) < 5 * np.sqrt(2.0 / n)
+    re2 = ((p[:, -1] - p[:, 0]) ** 2).sum(-1)
+    assert abs(re2.mean() - 1.0) < 5 * np.sqrt(2 / 3 / len(re2))
+    assert pos.min() >= 0.0 and pos.max() < 8.0
+
+
+def test_ideal_chains_acceptance_and_re2():
+    s = soma.System(n_poly=16384, N=32, n_A=16, box=(8.0, 8.0, 8.0), grid=(32, 32, 32), chiN=0.0, kappaN=0.0)
+    steps = 200
+    with soma.Handle(s) as h:
+        kb = h.info()["k_b"]
+        A = h.info()["A"]
+        h.mc_steps(steps)
+        o = h.observables()
+    expect = pins._acceptance_ideal(32, A, kb)
+    assert abs(o["acc"] - expect) < 5 * np.sqrt(expect * (1 - expect) / (s.n_beads * steps)) + 2e-4
+    assert abs(o["Re2"] - 1.0) < 5 * np.sqrt(2 / 3 / s.n_poly)
+
+
+def test_single_bead_boltzmann_occupancy_in_frozen_field():
+    rng = np.random.default_rng(11)
+    s = soma.System(n_poly=65536, N=1, n_A=1, box=(1.0, 1.5, 2.0), grid=(2, 3, 4), chiN=0.0, kappaN=0.0, A=0.6)
+    w = rng.normal(0.0, 0.8, size=(2, s.n_cells)).astype(np.float32)
+    with soma.Handle(s) as h:
+        h.freeze_fields(w)
+        h.mc_steps(20)
+        samples = []
+        for _ in range(16):
+            occ = np.zeros(s.n_cells)
+            for _ in range(5):
+                h.mc_steps(3)
+                occ += h.get_density()[0]
+            samples.append(occ / occ.sum())
+        assert np.array_equal(h.get_fields(), w)
+    p = np.exp(-w[0].astype(np.float64))
+    fails = []
+    pins._block_test(fails, "gpu single bead", np.array(samples), p / p.sum())
+    assert not fails, fails
+
+
+def test_dimer_cell_pair_law_in_frozen_field():
+    """AB dimers on a 2^3 grid in a frozen field: the cell-pair law is exact.
+    The box must hold two bond tails (L >= 16/sqrt(3)), so cells are 5 R_e
+    wide and a long run is needed to mix between them."""
+    rng = np.random.default_rng(21)
+    box, grid = (10.0, 10.0, 10.0), (2, 2, 2)
+    s = soma.System(n_poly=65536, N=2, n_A=1, box=box, grid=grid, chiN=0.0, kappaN=0.0, A=1.0)
+    w = rng.normal(0.0, 0.7, size=(2, 8)).astype(np.float32)
+    Ks = [pins._bond_cell_kernel(box[a], grid[a], 1.5) for a in range(3)]
+    cells = [(ix, iy, iz) for ix in range(2) for iy in range(2) for iz in range(2)]
+    P = np.zeros((8, 8))
+    for c1, (a1, b1, z1) in enumerate(cells):
+        for c2, (a2, b2, z2) in enumerate(cells):
+            P[c1, c2] = np.exp(-float(w[0, c1]) - float(w[1, c2])) * Ks[0][a1, a2] * Ks[1][b1, b2] * Ks[2][z1, z2]
+    P /= P.sum()
+
+    def cells_of(pos):  # brute-force binning of wrapped positions
+        i = np.minimum((pos * (np.array(grid) / np.array(box))).astype(np.int64), np.array(grid) - 1)
+        return (i[:, 0] * grid[1] + i[:, 1]) * grid[2] + i[:, 2]
+
+    with soma.Handle(s) as h:
+        h.freeze_fields(w)
+        h.mc_steps(1500)
+        samples = []
+        for _ in range(16):
+            hist = np.zeros(64)
+            for _ in range(10):
+                h.mc_steps(25)
+                c = cells_of(h.get_state()[0])
+                np.add.at(hist, c[0::2] * 8 + c[1::2], 1)
+            samples.append(hist / hist.sum())
+    fails = []
+    pins._block_test(fails, "gpu dimer", np.array(samples), P.reshape(-1), zmax=6.0)
+    assert not fails, fails
+
+
+def test_long_run_statistics_agree_with_oracle():
+    """chiN = 20, kappaN = 50 (config 0 shape): <R_e^2>, acceptance and the
+    peak of S(q) from the GPU and the oracle agree within 3 sigma over seeds."""
+    kw = workloads.system_kwargs("config0")
+    m = np.array([(x, y, z) for x in range(-4, 5) for y in range(-4, 5) for z in range(-4, 5)
+                  if 0 < x * x + y * y + z * z <= 16], np.int32)
+    shells = (m ** 2).sum(1)
+    burn, steps, every = 300, 1200, 100
+
+    def stats_gpu(seed):
+        with soma.Handle(soma.System(**{**kw, "seed": seed})) as h:
+            h.mc_steps(burn)
+            a0 = h.accepted()
+            re2, sq = [], []
+            for _ in range(steps // every):
+                h.mc_steps(every)
+                re2.append(h.observables()["Re2"])
+                sq.append(h.structure_factor(m))
+            acc = (h.accepted() - a0) / (steps * h.systems[0].n_beads)
+        return np.mean(re2), acc, np.mean(sq, axis=0)
+
+    def stats_orc(seed):
+        o = G.oracle_for(soma.System(**{**kw, "seed": seed}))
+        X = o.init()
+        o.run(X, 0, burn, n_threads=G.NTHREADS)
+        re2, sq, acc = [], [], 0
+        for k in range(steps // every):
+            r = o.run(X, burn + k * every, every, n_threads=G.NTHREADS)
+            acc += r["accepted"]
+            re2.append(o.observables(X)["Re2"])
+            sq.append(o.structure_factor(X, m))
+        return np.mean(re2), acc / (steps * o.n_b), np.mean(sq, axis=0)
+
+    seeds = range(1, 9)
+    g = [stats_gpu(s) for s in seeds]
+    r = [stats_orc(s) for s in seeds]
+    for k, name in ((0, "Re2"), (1, "acc")):
+        a = np.array([x[k] for x in g])
+        b = np.array([x[k] for x in r])
+        se = np.sqrt(a.var(ddof=1) / len(a) + b.var(ddof=1) / len(b))
+        assert abs(a.mean() - b.mean()) <= 3 * se + 1e-12, (name, a.mean(), b.mean(), se)
+    # S(q*): shell-averaged, q* = the shell maximising the oracle's mean
+    def shell_avg(S):
+        return np.array([S[shells == k].mean() for k in np.unique(shells)])
+    ga = np.array([shell_avg(x[2]) for x in g])
+    ra = np.array([shell_avg(x[2]) for x in r])
+    kstar = int(np.argmax(ra.mean(0)))
+    se = np.sqrt(ga[:, kstar].var(ddof=1) / 8 + ra[:, kstar].var(ddof=1) / 8)
+    assert abs(ga[:, kstar].mean() - ra[:, kstar].mean()) <= 3 * se
