@@ -52,7 +52,7 @@ def _peaks():
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("soma_kernels.cu", "soma_internal.cuh"):
+    for f in ("soma_move.cu", "soma_device.cuh", "soma_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2606_09356_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -61,7 +61,7 @@ def _kernel_source_hash():
 def _profiled_traffic(workload):
     """DRAM bytes per launch of the move kernel from the committed ncu summary,
     if that summary was taken from the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"k_move_bin_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"k_move_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -299,7 +299,7 @@ def run_gpu(args):
     traffic = _profiled_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_move_bin", "move_ms": move_avg, "field_ms": fd_ms / max(1, fd_n),
+                "kernel": "k_move", "move_ms": move_avg, "field_ms": fd_ms / max(1, fd_n),
                 "step_frac": algorithmic_bytes(n_b, n_c) * args.steps / (total_ms * 1e-3) / 1e9 / hbm_peak}
 
     # steady state without flushes: CUDA-graph replay of many steps (L2-warm)

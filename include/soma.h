@@ -88,7 +88,7 @@ typedef void (*soma_free_fn)(void* ptr, void* ctx);
 typedef struct soma_options {
   int32_t device;        /* CUDA device ordinal; -1 = the current device */
   int32_t sort_interval; /* steps between chain reorders; 0 = never; -1 = tuned */
-  int32_t block_threads; /* move-kernel CTA size (multiple of 32, <= 1024); 0 = tuned */
+  int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent move kernel; 0 = as many as fit */
   int32_t hist_mode;     /* SOMA_HIST_* */
   int32_t graph_steps;   /* steps per captured CUDA graph; 0 = plain launches */
   int32_t kernel_timing; /* 1 = record CUDA events around each kernel (plain launches) */
@@ -116,14 +116,14 @@ typedef struct soma_info {
   double A;         /* proposal half-width actually used (FP32 value) */
   double rho_bar;   /* n_beads / n_cells */
   int32_t lanes_per_chain; /* move-kernel lanes per chain (0 = generic path) */
-  int32_t block_threads;   /* move-kernel CTA size in use */
+  int32_t ctas_per_sm;     /* move-kernel CTAs per SM in use */
   int32_t sort_interval;   /* reorder interval in use */
   int32_t hist_mode;       /* histogram strategy in use */
 } soma_info;
 
 typedef struct soma_handle soma_handle;
 
-/* Fill *opt with defaults (device -1, tuned sort interval and block size,
+/* Fill *opt with defaults (device -1, default sort interval, full occupancy,
  * SOMA_HIST_AUTO, graphs of 16 steps, no timing, no autotune). */
 int soma_options_default(soma_options* opt);
 

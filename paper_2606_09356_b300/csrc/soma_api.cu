@@ -1,6 +1,7 @@
 // soma_api.cu -- the C ABI of include/soma.h: handle life cycle, step
-// scheduling (plain launches or CUDA-graph replay), state I/O, observables,
-// reorder scheduling, per-kernel timing and the autotuner.
+// scheduling (plain launches or CUDA-graph replay; independent systems run as
+// parallel graph branches), state I/O, observables, reorder scheduling,
+// per-kernel timing and the autotuner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,10 +21,9 @@ using namespace soma;
 
 namespace {
 
-constexpr int64_t kCellsPerTile = 8192;  // multiple of 4 (vectorised field kernel)
-constexpr int kDefaultThreads = 256;
 constexpr int kDefaultSortInterval = 200;
 constexpr int kDefaultGraphSteps = 16;
+constexpr int kMaxBranchStreams = 32;
 enum { T_MOVE = 0, T_BIN = 1, T_FIELD = 2, T_SORT = 3 };
 
 struct TimedEvent {
@@ -43,23 +43,24 @@ struct soma_handle {
   int device = 0, sm_count = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // dedicated stream for graph capture
+  std::vector<cudaStream_t> branch;   // streams of the per-system graph branches
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
   soma_options opt{};
   int n_sys = 0;
   std::vector<soma_system_desc> desc;
-  std::vector<SysDev> host_sys;  // pointers as allocated (device copies may be swapped by reorders)
+  std::vector<SysDev> host_sys;  // device pointers and constants (fixed for the handle's life)
   SysDev* d_sys = nullptr;
+  std::vector<MoveArgs> margs;
+  std::vector<FieldArgs> fargs;
+  std::vector<int> n_tiles;
   std::vector<void*> owned;
   // launch geometry
-  int threads = kDefaultThreads;
+  int max_ctas_per_sm = 1;
+  int ctas_per_sm = 1;
   int hist_mode = SOMA_HIST_FUSED;
   int sort_interval = kDefaultSortInterval;
-  std::vector<MoveTile> move_tiles;
-  MoveTile* d_move_tiles = nullptr;
-  int n_move_tiles = 0, move_tiles_cap = 0;
-  std::vector<CellTile> cell_tiles;
-  CellTile* d_cell_tiles = nullptr;
-  std::vector<int> generic_sys;  // systems with N > 64
-  int64_t acc_slots = 0;
+  int acc_per_sys = 1;
   unsigned long long* d_acc = nullptr;
   // step counter (device base + host mirror of enqueued steps)
   unsigned long long* d_step = nullptr;
@@ -99,7 +100,7 @@ int fail(soma_handle* h, int code) {
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \
     if (e_ != cudaSuccess) {                                                            \
-      if (getenv("SOMA_VERBOSE"))                                                        \
+      if (getenv("SOMA_VERBOSE"))                                                       \
         fprintf(stderr, "soma: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), \
                 __FILE__, __LINE__);                                                    \
       return fail(h, e_ == cudaErrorMemoryAllocation ? SOMA_ENOMEM : SOMA_ECUDA);       \
@@ -107,7 +108,8 @@ int fail(soma_handle* h, int code) {
   } while (0)
 
 void* dev_alloc(soma_handle* h, size_t bytes) {
-  if (bytes == 0) bytes = 16;
+  bytes = ((bytes + 255) / 256) * 256;
+  if (bytes == 0) bytes = 256;
   void* p = nullptr;
   if (h->opt.alloc) {
     p = h->opt.alloc(bytes, h->opt.alloc_ctx);
@@ -139,13 +141,13 @@ int check_live(const soma_handle* h) {
 
 int validate_desc(const soma_system_desc& d) {
   if (d.n_poly < 1 || d.N < 1 || d.N > 4096 || d.n_A < 0 || d.n_A > d.N) return SOMA_EINVAL;
-  if ((int64_t)d.n_poly * d.N > (int64_t)INT32_MAX) return SOMA_EINVAL;
+  if ((int64_t)d.n_poly * d.N > (int64_t)INT32_MAX - 64) return SOMA_EINVAL;
   int64_t nc = 1;
   for (int a = 0; a < 3; ++a) {
     if (d.grid[a] < 1 || !(d.box[a] > 0.0) || !std::isfinite(d.box[a])) return SOMA_EINVAL;
     nc *= d.grid[a];
   }
-  if (nc >= (int64_t)INT32_MAX) return SOMA_EINVAL;
+  if (nc >= (int64_t)INT32_MAX / 4) return SOMA_EINVAL;
   if (!std::isfinite(d.chiN) || !std::isfinite(d.kappaN) || !std::isfinite(d.A)) return SOMA_EINVAL;
   if (d.N == 1 && !(d.A > 0.0)) return SOMA_EINVAL;  // no default half-width without bonds
   if (d.N > 1) {
@@ -159,79 +161,69 @@ int validate_desc(const soma_system_desc& d) {
   return SOMA_OK;
 }
 
-// Move tiles: each CTA takes (threads/32) * (32/P) consecutive chains of one
-// register-path system; generic systems get one accumulator slot each.
-int build_tiles(soma_handle* h) {
-  h->move_tiles.clear();
-  h->generic_sys.clear();
-  int acc = 0;
+int move_grid(const soma_handle* h, int s) {
+  const int g = std::min(h->n_tiles[s], h->sm_count * h->ctas_per_sm);
+  return std::max(g, 1);
+}
+
+void build_args(soma_handle* h) {
+  h->margs.resize(h->n_sys);
+  h->fargs.resize(h->n_sys);
+  h->n_tiles.resize(h->n_sys);
   for (int s = 0; s < h->n_sys; ++s) {
-    SysDev& S = h->host_sys[s];
-    S.acc_first = acc;
-    if (S.P == 0) {
-      h->generic_sys.push_back(s);
-      S.acc_count = 1;
-      acc += 1;
-      continue;
+    const SysDev& S = h->host_sys[s];
+    MoveArgs& a = h->margs[s];
+    std::memset(&a, 0, sizeof(a));
+    for (int i = 0; i < 3; ++i) {
+      a.L[i] = S.L[i];
+      a.invL[i] = S.invL[i];
+      a.cps[i] = S.cps[i];
     }
-    const int per_cta = (h->threads / 32) * (32 / S.P);
-    int count = 0;
-    for (int first = 0; first < S.n_poly; first += per_cta) {
-      MoveTile t;
-      t.sys = s;
-      t.first_chain = first;
-      t.n_chains = std::min(per_cta, S.n_poly - first);
-      t.acc_index = acc++;
-      h->move_tiles.push_back(t);
-      ++count;
-    }
-    S.acc_count = count;
+    a.n[0] = S.nx;
+    a.n[1] = S.ny;
+    a.n[2] = S.nz;
+    a.A = S.A;
+    a.kb = S.kb;
+    std::memcpy(a.rk, S.rk, sizeof(a.rk));
+    a.N = S.N;
+    a.n_A = S.n_A;
+    a.P = S.P;
+    a.sys_index = S.sys_index;
+    a.n_poly = S.n_poly;
+    a.chains_per_tile = S.P ? move_kernel_chains_per_tile(S.P) : 0;
+    a.n_tiles = S.P ? (S.n_poly + a.chains_per_tile - 1) / a.chains_per_tile : 0;
+    a.bin = h->hist_mode == SOMA_HIST_FUSED ? 1 : 0;
+    a.n_c = S.n_c;
+    a.x = S.x;
+    a.y = S.y;
+    a.z = S.z;
+    a.img = S.img;
+    a.chain_id = S.chain_id;
+    a.counts = S.counts;
+    a.w = S.w;
+    a.acc = h->d_acc + S.acc_first;
+    a.step_base = h->d_step;
+    a.err = h->d_err;
+    h->n_tiles[s] = a.n_tiles;
+
+    FieldArgs& f = h->fargs[s];
+    std::memset(&f, 0, sizeof(f));
+    f.counts = S.counts;
+    f.w = S.w;
+    f.n_c = S.n_c;
+    f.inv_rho = S.inv_rho;
+    f.chiN_N = S.chiN_N;
+    f.kappaN_N = S.kappaN_N;
+    f.frozen = S.frozen;
+    f.step_base = h->d_step;
   }
-  h->n_move_tiles = (int)h->move_tiles.size();
-  return acc;
 }
 
-int upload_tiles(soma_handle* h) {
-  if (h->n_move_tiles > h->move_tiles_cap) {
-    h->d_move_tiles = (MoveTile*)dev_alloc(h, sizeof(MoveTile) * h->n_move_tiles);
-    if (!h->d_move_tiles) return fail(h, SOMA_ENOMEM);
-    h->move_tiles_cap = h->n_move_tiles;
-  }
-  if (h->n_move_tiles)
-    CK(cudaMemcpyAsync(h->d_move_tiles, h->move_tiles.data(), sizeof(MoveTile) * h->n_move_tiles,
-                       cudaMemcpyHostToDevice, h->stream));
-  return SOMA_OK;
-}
-
-// Update only the accumulator ranges of the device-side system table (its
-// array pointers may have been swapped by reorders).
-__global__ void k_set_acc_ranges(SysDev* systems, const int2* ranges, int n) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) {
-    systems[s].acc_first = ranges[s].x;
-    systems[s].acc_count = ranges[s].y;
-  }
-}
-
-int rebuild_geometry(soma_handle* h, int threads) {
-  h->threads = threads;
-  const int acc = build_tiles(h);
-  if (acc > h->acc_slots) return fail(h, SOMA_EINVAL);
-  int rc = upload_tiles(h);
-  if (rc) return rc;
-  std::vector<int2> ranges(h->n_sys);
-  for (int s = 0; s < h->n_sys; ++s) ranges[s] = make_int2(h->host_sys[s].acc_first, h->host_sys[s].acc_count);
-  int2* d_ranges = (int2*)h->d_stage_phi;  // scratch: stage buffer is at least n_sys * 8 bytes
-  CK(cudaMemcpyAsync(d_ranges, ranges.data(), sizeof(int2) * h->n_sys, cudaMemcpyHostToDevice, h->stream));
-  k_set_acc_ranges<<<(h->n_sys + 63) / 64, 64, 0, h->stream>>>(h->d_sys, d_ranges, h->n_sys);
-  CK(cudaGetLastError());
-  CK(cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * h->acc_slots, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+void drop_graph(soma_handle* h) {
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
   }
-  return SOMA_OK;
 }
 
 void begin_timed(soma_handle* h, cudaStream_t s, TimedEvent& te, int kind) {
@@ -243,39 +235,54 @@ void begin_timed(soma_handle* h, cudaStream_t s, TimedEvent& te, int kind) {
 void end_timed(soma_handle* h, cudaStream_t s, TimedEvent& te) {
   cudaEventRecord(te.b, s);
   h->pending.push_back(te);
+  h->launches[te.kind] += 1;
 }
 
-// Enqueue step `offset` (relative to the device step base) of every system.
-int enqueue_step(soma_handle* h, cudaStream_t s, int offset) {
+// Steps offset0 .. offset0+n-1 (relative to the device step base) of system
+// `sys` on stream `s`: move (+ fused histogram), [separate histogram], field.
+int enqueue_system(soma_handle* h, cudaStream_t s, int sys, int offset0, int n) {
   const bool timing = h->opt.kernel_timing != 0;
+  const SysDev& S = h->host_sys[sys];
+  const bool separate_bin = S.P == 0 || h->hist_mode == SOMA_HIST_SEPARATE;
   TimedEvent te;
-  const int fused = h->hist_mode == SOMA_HIST_FUSED;
-  if (timing) begin_timed(h, s, te, T_MOVE);
-  if (h->n_move_tiles)
-    CK(launch_move_bin(h->d_sys, h->d_move_tiles, h->n_move_tiles, h->threads, h->d_step, offset, fused, s));
-  for (int g : h->generic_sys)
-    CK(launch_move_generic(h->d_sys, g, h->host_sys[g].n_poly, h->host_sys[g].N, h->d_step, offset, h->sm_count, s));
-  if (timing) {
-    end_timed(h, s, te);
-    h->launches[T_MOVE] += 1;
-  }
-  bool any_bin = false;
-  for (int g = 0; g < h->n_sys; ++g) any_bin |= (!fused || h->host_sys[g].P == 0);
-  if (any_bin) {
-    if (timing) begin_timed(h, s, te, T_BIN);
-    for (int g = 0; g < h->n_sys; ++g)
-      if (!fused || h->host_sys[g].P == 0)
-        CK(launch_bin(h->d_sys, g, h->host_sys[g].n_b, h->d_step, offset, h->sm_count, s));
-    if (timing) {
-      end_timed(h, s, te);
-      h->launches[T_BIN] += 1;
+  for (int i = 0; i < n; ++i) {
+    const int off = offset0 + i;
+    if (timing) begin_timed(h, s, te, T_MOVE);
+    if (S.P)
+      CK(launch_move(h->margs[sys], move_grid(h, sys), off, s));
+    else
+      CK(launch_move_generic(h->d_sys, sys, S.n_poly, S.N, h->d_step, off, h->sm_count, s));
+    if (timing) end_timed(h, s, te);
+    if (separate_bin) {
+      if (timing) begin_timed(h, s, te, T_BIN);
+      CK(launch_bin(h->d_sys, sys, S.n_b, h->d_step, off, h->sm_count, s));
+      if (timing) end_timed(h, s, te);
     }
+    if (timing) begin_timed(h, s, te, T_FIELD);
+    CK(launch_field(h->fargs[sys], off, s));
+    if (timing) end_timed(h, s, te);
   }
-  if (timing) begin_timed(h, s, te, T_FIELD);
-  CK(launch_field(h->d_sys, h->d_cell_tiles, (int)h->cell_tiles.size(), h->d_step, offset, s));
-  if (timing) {
-    end_timed(h, s, te);
-    h->launches[T_FIELD] += 1;
+  return SOMA_OK;
+}
+
+// n steps of every system.  A single system runs on `s`; several systems run
+// as independent branches (fork on `s`, one branch stream per system, join
+// back on `s`), so no system waits for another inside the n steps.
+int enqueue_steps(soma_handle* h, cudaStream_t s, int offset0, int n) {
+  int rc;
+  if (h->n_sys == 1 || h->opt.kernel_timing) {
+    for (int sys = 0; sys < h->n_sys; ++sys)
+      if ((rc = enqueue_system(h, s, sys, offset0, n))) return rc;
+    return SOMA_OK;
+  }
+  CK(cudaEventRecord(h->fork, s));
+  const int nb = (int)h->branch.size();
+  for (int b = 0; b < nb; ++b) CK(cudaStreamWaitEvent(h->branch[b], h->fork, 0));
+  for (int sys = 0; sys < h->n_sys; ++sys)
+    if ((rc = enqueue_system(h, h->branch[sys % nb], sys, offset0, n))) return rc;
+  for (int b = 0; b < nb; ++b) {
+    CK(cudaEventRecord(h->join[b], h->branch[b]));
+    CK(cudaStreamWaitEvent(s, h->join[b], 0));
   }
   return SOMA_OK;
 }
@@ -284,23 +291,16 @@ int enqueue_reorder(soma_handle* h, cudaStream_t s) {
   TimedEvent te;
   if (h->opt.kernel_timing) begin_timed(h, s, te, T_SORT);
   CK(launch_reorder(h->d_sys, h->n_sys, h->sort, h->sm_count, s));
-  if (h->opt.kernel_timing) {
-    end_timed(h, s, te);
-    h->launches[T_SORT] += 1;
-  }
+  if (h->opt.kernel_timing) end_timed(h, s, te);
   h->steps_since_sort = 0;
   return SOMA_OK;
 }
 
 int capture_graph(soma_handle* h, int steps) {
-  if (h->graph) {
-    cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-  }
+  drop_graph(h);
   cudaStream_t cs = h->cap_stream;
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  int rc = SOMA_OK;
-  for (int i = 0; i < steps && rc == SOMA_OK; ++i) rc = enqueue_step(h, cs, i);
+  int rc = enqueue_steps(h, cs, 0, steps);
   if (rc == SOMA_OK && launch_advance(h->d_step, steps, cs) != cudaSuccess) rc = SOMA_ECUDA;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &g);
@@ -316,20 +316,15 @@ int capture_graph(soma_handle* h, int steps) {
   return SOMA_OK;
 }
 
-int zero_acc_all(soma_handle* h, cudaStream_t s) {
-  CK(cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * h->acc_slots, s));
-  return SOMA_OK;
-}
-
-// Bin the current positions of system `sys` into buffer (step - 1) & 1,
-// clear buffer step & 1 and rebuild its fields (unless held).
+// Bin the current positions into buffer (step - 1) & 1, clear buffer step & 1
+// and rebuild the fields (unless held).
 int rebin_all(soma_handle* h, cudaStream_t s) {
   for (int g = 0; g < h->n_sys; ++g) {
     SysDev& S = h->host_sys[g];
     CK(cudaMemsetAsync(S.counts, 0, sizeof(uint32_t) * 4 * S.n_c, s));
     CK(launch_bin(h->d_sys, g, S.n_b, h->d_step, -1, h->sm_count, s));
+    CK(launch_field(h->fargs[g], -1, s));
   }
-  CK(launch_field(h->d_sys, h->d_cell_tiles, (int)h->cell_tiles.size(), h->d_step, -1, s));
   return SOMA_OK;
 }
 
@@ -341,6 +336,27 @@ int check_device_error(soma_handle* h) {
   return SOMA_OK;
 }
 
+int sync_all(soma_handle* h) {
+  CK(cudaDeviceSynchronize());
+  return check_device_error(h);
+}
+
+int set_frozen(soma_handle* h, int sys, int frozen) {
+  h->host_sys[sys].frozen = frozen;
+  h->fargs[sys].frozen = frozen;
+  drop_graph(h);
+  CK(cudaMemcpy(reinterpret_cast<char*>(h->d_sys + sys) + offsetof(SysDev, frozen), &frozen, sizeof(int),
+                cudaMemcpyHostToDevice));
+  return SOMA_OK;
+}
+
+void apply_geometry(soma_handle* h, int ctas_per_sm, int hist_mode) {
+  h->ctas_per_sm = std::max(1, std::min(ctas_per_sm, h->max_ctas_per_sm));
+  h->hist_mode = hist_mode;
+  build_args(h);
+  drop_graph(h);
+}
+
 }  // namespace
 
 extern "C" {
@@ -350,7 +366,7 @@ int soma_options_default(soma_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->device = -1;
   o->sort_interval = -1;
-  o->block_threads = 0;
+  o->ctas_per_sm = 0;
   o->hist_mode = SOMA_HIST_AUTO;
   o->graph_steps = kDefaultGraphSteps;
   o->kernel_timing = 0;
@@ -381,8 +397,13 @@ void soma_destroy(soma_handle* h) {
     cudaEventDestroy(te.a);
     cudaEventDestroy(te.b);
   }
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  drop_graph(h);
   dev_free_all(h);
+  for (auto st : h->branch)
+    if (st) cudaStreamDestroy(st);
+  for (auto ev : h->join)
+    if (ev) cudaEventDestroy(ev);
+  if (h->fork) cudaEventDestroy(h->fork);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -391,7 +412,7 @@ void soma_destroy(soma_handle* h) {
 int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt, soma_handle** out) {
   if (!out) return SOMA_EINVAL;
   *out = nullptr;
-  if (!sys || n_sys < 1 || n_sys > (1 << 20)) return SOMA_EINVAL;
+  if (!sys || n_sys < 1 || n_sys > (1 << 16)) return SOMA_EINVAL;
   for (int s = 0; s < n_sys; ++s)
     if (validate_desc(sys[s]) != SOMA_OK) return SOMA_EINVAL;
   soma_options o;
@@ -399,8 +420,7 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
     o = *opt;
   else
     soma_options_default(&o);
-  if (o.block_threads != 0 && (o.block_threads % 32 != 0 || o.block_threads < 32 || o.block_threads > 512))
-    return SOMA_EINVAL;
+  if (o.ctas_per_sm < 0 || o.ctas_per_sm > 64) return SOMA_EINVAL;
   if (o.hist_mode < SOMA_HIST_AUTO || o.hist_mode > SOMA_HIST_SEPARATE) return SOMA_EINVAL;
   if (o.graph_steps < 0 || o.graph_steps > 4096) return SOMA_EINVAL;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SOMA_EINVAL;
@@ -426,11 +446,23 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return bail(SOMA_ECUDA);
   h->sm_count = prop.multiProcessorCount;
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess)
     return bail(SOMA_ECUDA);
-  h->threads = o.block_threads ? o.block_threads : kDefaultThreads;
+  if (n_sys > 1) {
+    const int nb = std::min(n_sys, kMaxBranchStreams);
+    h->branch.resize(nb, nullptr);
+    h->join.resize(nb, nullptr);
+    for (int b = 0; b < nb; ++b)
+      if (cudaStreamCreateWithFlags(&h->branch[b], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->join[b], cudaEventDisableTiming) != cudaSuccess)
+        return bail(SOMA_ECUDA);
+  }
+  h->max_ctas_per_sm = move_kernel_max_ctas_per_sm();
+  h->ctas_per_sm = o.ctas_per_sm ? std::min<int>(o.ctas_per_sm, h->max_ctas_per_sm) : h->max_ctas_per_sm;
   h->hist_mode = o.hist_mode == SOMA_HIST_AUTO ? SOMA_HIST_FUSED : o.hist_mode;
   h->sort_interval = o.sort_interval < 0 ? kDefaultSortInterval : o.sort_interval;
+  h->acc_per_sys = h->sm_count * h->max_ctas_per_sm;
 
   // --- per-system constants and arrays ---------------------------------
   h->host_sys.resize(n_sys);
@@ -468,58 +500,44 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
     }
     S.chain_base = chain_base;
     chain_base += d.n_poly;
+    S.acc_first = s * h->acc_per_sys;
+    S.acc_count = h->acc_per_sys;
     h->max_nb = std::max<int64_t>(h->max_nb, S.n_b);
     h->max_nc = std::max<int64_t>(h->max_nc, S.n_c);
 
-    const size_t nb = (size_t)S.n_b, nc = (size_t)S.n_c;
+    // bulk copies read whole 16-byte granules: pad position and id arrays
+    const size_t nb = (size_t)S.n_b + 8, nc = (size_t)S.n_c, np = (size_t)d.n_poly + 8;
     S.x = (float*)dev_alloc(h, nb * 4);
     S.y = (float*)dev_alloc(h, nb * 4);
     S.z = (float*)dev_alloc(h, nb * 4);
     S.img = (int16_t*)dev_alloc(h, nb * 8);
-    S.chain_id = (uint32_t*)dev_alloc(h, (size_t)d.n_poly * 4);
+    S.chain_id = (uint32_t*)dev_alloc(h, np * 4);
     S.x_alt = (float*)dev_alloc(h, nb * 4);
     S.y_alt = (float*)dev_alloc(h, nb * 4);
     S.z_alt = (float*)dev_alloc(h, nb * 4);
     S.img_alt = (int16_t*)dev_alloc(h, nb * 8);
-    S.chain_id_alt = (uint32_t*)dev_alloc(h, (size_t)d.n_poly * 4);
+    S.chain_id_alt = (uint32_t*)dev_alloc(h, np * 4);
     S.counts = (uint32_t*)dev_alloc(h, nc * 16);
     S.w = (float*)dev_alloc(h, nc * 8);
     if (!S.x || !S.y || !S.z || !S.img || !S.chain_id || !S.x_alt || !S.y_alt || !S.z_alt || !S.img_alt ||
         !S.chain_id_alt || !S.counts || !S.w)
       return bail(SOMA_ENOMEM);
+    if (cudaMemset(S.x, 0, nb * 4) != cudaSuccess || cudaMemset(S.y, 0, nb * 4) != cudaSuccess ||
+        cudaMemset(S.z, 0, nb * 4) != cudaSuccess || cudaMemset(S.chain_id, 0, np * 4) != cudaSuccess)
+      return bail(SOMA_ECUDA);
   }
-  // tiles for the largest accumulator need (smallest CTA) so that retuning never reallocates
-  {
-    const int t_save = h->threads;
-    h->threads = 32;
-    h->acc_slots = build_tiles(h);
-    h->threads = t_save;
-  }
-  build_tiles(h);
-  h->d_acc = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * h->acc_slots);
+  h->d_acc = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * (size_t)h->acc_per_sys * n_sys);
   for (int s = 0; s < n_sys; ++s) h->host_sys[s].acc = h->d_acc;
-  for (int s = 0; s < n_sys; ++s) {
-    const SysDev& S = h->host_sys[s];
-    for (int64_t b = 0; b < S.n_c; b += kCellsPerTile) {
-      CellTile t;
-      t.sys = s;
-      t.pad = 0;
-      t.begin = b;
-      t.end = std::min<int64_t>(S.n_c, b + kCellsPerTile);
-      h->cell_tiles.push_back(t);
-    }
-  }
   h->d_sys = (SysDev*)dev_alloc(h, sizeof(SysDev) * n_sys);
-  h->d_cell_tiles = (CellTile*)dev_alloc(h, sizeof(CellTile) * h->cell_tiles.size());
   h->d_step = (unsigned long long*)dev_alloc(h, 8);
   h->d_err = (int*)dev_alloc(h, 4);
   h->d_obs = (double*)dev_alloc(h, 8 * sizeof(double));
   h->d_acc_sum = (unsigned long long*)dev_alloc(h, 8);
   h->d_stage_pos = (float*)dev_alloc(h, (size_t)h->max_nb * 12);
   h->d_stage_img = (int16_t*)dev_alloc(h, (size_t)h->max_nb * 6);
-  h->d_stage_phi = (float*)dev_alloc(h, std::max<size_t>((size_t)h->max_nc * 8, (size_t)n_sys * 8));
-  if (!h->d_acc || !h->d_sys || !h->d_cell_tiles || !h->d_step || !h->d_err || !h->d_obs || !h->d_acc_sum ||
-      !h->d_stage_pos || !h->d_stage_img || !h->d_stage_phi)
+  h->d_stage_phi = (float*)dev_alloc(h, (size_t)h->max_nc * 8);
+  if (!h->d_acc || !h->d_sys || !h->d_step || !h->d_err || !h->d_obs || !h->d_acc_sum || !h->d_stage_pos ||
+      !h->d_stage_img || !h->d_stage_phi)
     return bail(SOMA_ENOMEM);
   // sort work
   {
@@ -544,12 +562,10 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
       return bail(SOMA_ECUDA);
   }
   if (cudaMemcpy(h->d_sys, h->host_sys.data(), sizeof(SysDev) * n_sys, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(h->d_cell_tiles, h->cell_tiles.data(), sizeof(CellTile) * h->cell_tiles.size(),
-                 cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(h->d_step, 0, 8) != cudaSuccess || cudaMemset(h->d_err, 0, 4) != cudaSuccess ||
-      cudaMemset(h->d_acc, 0, sizeof(unsigned long long) * h->acc_slots) != cudaSuccess)
+      cudaMemset(h->d_acc, 0, sizeof(unsigned long long) * (size_t)h->acc_per_sys * n_sys) != cudaSuccess)
     return bail(SOMA_ECUDA);
-  if ((rc = upload_tiles(h)) != SOMA_OK) return bail(rc);
+  build_args(h);
 
   // --- initial configuration, start-up checks, counts, fields, sort -----
   for (int s = 0; s < n_sys && rc == SOMA_OK; ++s) {
@@ -595,11 +611,8 @@ int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
       for (int64_t r = 0; r < reps; ++r) CK(cudaGraphLaunch(h->graph, s));
       chunk = reps * h->graph_steps;
     } else {
-      chunk = std::min<int64_t>(chunk, 1 << 20);
-      for (int64_t i = 0; i < chunk; ++i) {
-        rc = enqueue_step(h, s, (int)i);
-        if (rc) return rc;
-      }
+      chunk = std::min<int64_t>(chunk, 1 << 16);
+      if ((rc = enqueue_steps(h, s, 0, (int)chunk))) return rc;
       CK(launch_advance(h->d_step, chunk, s));
     }
     left -= chunk;
@@ -614,11 +627,6 @@ int soma_sync(soma_handle* h, void* stream) {
   if (rc) return rc;
   CK(cudaStreamSynchronize(pick(h, stream)));
   CK(cudaStreamSynchronize(h->stream));
-  return check_device_error(h);
-}
-
-static int sync_all(soma_handle* h) {
-  CK(cudaDeviceSynchronize());
   return check_device_error(h);
 }
 
@@ -642,13 +650,6 @@ int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where) {
   if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
   if ((rc = sync_all(h))) return rc;
   CK(cudaMemcpy(out, S.w, sizeof(float) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
-  return SOMA_OK;
-}
-
-static int set_frozen(soma_handle* h, int sys, int frozen) {
-  h->host_sys[sys].frozen = frozen;
-  CK(cudaMemcpy(reinterpret_cast<char*>(h->d_sys + sys) + offsetof(SysDev, frozen), &frozen, sizeof(int),
-                cudaMemcpyHostToDevice));
   return SOMA_OK;
 }
 
@@ -676,9 +677,9 @@ int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int wh
     CK(cudaMemcpy(S.w, w, sizeof(float) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
   } else {
     if ((rc = set_frozen(h, sys, 0))) return rc;
-    // rebuild from the counts of the current configuration (buffer (step-1)&1); the
-    // field kernel also clears buffer step&1, which holds nothing yet
-    CK(launch_field(h->d_sys, h->d_cell_tiles, (int)h->cell_tiles.size(), h->d_step, -1, h->stream));
+    // rebuild from the counts of the current configuration (buffer (step-1)&1);
+    // this also clears buffer step&1, which holds nothing yet
+    CK(launch_field(h->fargs[sys], -1, h->stream));
   }
   return sync_all(h);
 }
@@ -723,7 +724,7 @@ int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img
   h->step = step;
   h->acc_since = step;
   CK(cudaMemcpyAsync(h->d_step, &step, 8, cudaMemcpyHostToDevice, h->stream));
-  if ((rc = zero_acc_all(h, h->stream))) return rc;
+  CK(cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * (size_t)h->acc_per_sys * h->n_sys, h->stream));
   if ((rc = rebin_all(h, h->stream))) return rc;
   return sync_all(h);
 }
@@ -804,7 +805,7 @@ int soma_get_info(soma_handle* h, int sys, soma_info* out) {
   out->A = S.A;
   out->rho_bar = (double)S.n_b / (double)S.n_c;
   out->lanes_per_chain = S.P;
-  out->block_threads = h->threads;
+  out->ctas_per_sm = h->ctas_per_sm;
   out->sort_interval = h->sort_interval;
   out->hist_mode = h->hist_mode;
   return SOMA_OK;
@@ -833,23 +834,20 @@ int soma_kernel_times(soma_handle* h, double* ms, int64_t* launches, int reset) 
   return SOMA_OK;
 }
 
-// Autotuner: time a few steps per candidate (CTA size of the move kernel,
-// fused or separate histogram) from a saved copy of the state, restore the
-// state between candidates and keep the fastest.  Random numbers are
-// counter-based, so the restored trajectory is the one that would have run.
+// Autotuner: time a few steps per candidate (resident CTAs per SM of the
+// move kernel, fused or separate histogram) from a saved copy of the state,
+// restore the state between candidates and keep the fastest.  Random numbers
+// are counter-based, so the restored trajectory is the one that would have
+// run; the acceptance counters are restored as well.
 int soma_autotune(soma_handle* h) {
   int rc = check_live(h);
   if (rc) return rc;
   h->tuned = true;
-  if (h->n_move_tiles == 0) return SOMA_OK;
-  CK(cudaDeviceSynchronize());
-  // save positions, images, chain ids of every system and the counters
+  if ((rc = sync_all(h))) return rc;
   const uint64_t step0 = h->step;
-  std::vector<SysDev> dev(h->n_sys);
-  CK(cudaMemcpy(dev.data(), h->d_sys, sizeof(SysDev) * h->n_sys, cudaMemcpyDeviceToHost));
   std::vector<std::vector<char>> save(h->n_sys);
   for (int s = 0; s < h->n_sys; ++s) {
-    const SysDev& S = dev[s];
+    const SysDev& S = h->host_sys[s];
     save[s].resize((size_t)S.n_b * 20 + (size_t)S.n_poly * 4 + (size_t)S.n_c * 24);
     char* p = save[s].data();
     CK(cudaMemcpy(p, S.x, S.n_b * 4, cudaMemcpyDeviceToHost)); p += S.n_b * 4;
@@ -860,15 +858,12 @@ int soma_autotune(soma_handle* h) {
     CK(cudaMemcpy(p, S.counts, S.n_c * 16, cudaMemcpyDeviceToHost)); p += S.n_c * 16;
     CK(cudaMemcpy(p, S.w, S.n_c * 8, cudaMemcpyDeviceToHost));
   }
-  std::vector<unsigned long long> acc_total(h->n_sys);
-  for (int s = 0; s < h->n_sys; ++s) {
-    CK(launch_sum_acc(h->d_sys, s, h->d_acc_sum, h->stream));
-    CK(cudaMemcpyAsync(&acc_total[s], h->d_acc_sum, 8, cudaMemcpyDeviceToHost, h->stream));
-  }
-  CK(cudaStreamSynchronize(h->stream));
+  const size_t acc_n = (size_t)h->acc_per_sys * h->n_sys;
+  std::vector<unsigned long long> acc_save(acc_n);
+  CK(cudaMemcpy(acc_save.data(), h->d_acc, 8 * acc_n, cudaMemcpyDeviceToHost));
   auto restore = [&]() -> int {
     for (int s = 0; s < h->n_sys; ++s) {
-      const SysDev& S = dev[s];
+      const SysDev& S = h->host_sys[s];
       const char* p = save[s].data();
       CK(cudaMemcpy(S.x, p, S.n_b * 4, cudaMemcpyHostToDevice)); p += S.n_b * 4;
       CK(cudaMemcpy(S.y, p, S.n_b * 4, cudaMemcpyHostToDevice)); p += S.n_b * 4;
@@ -878,31 +873,28 @@ int soma_autotune(soma_handle* h) {
       CK(cudaMemcpy(S.counts, p, S.n_c * 16, cudaMemcpyHostToDevice)); p += S.n_c * 16;
       CK(cudaMemcpy(S.w, p, S.n_c * 8, cudaMemcpyHostToDevice));
     }
+    CK(cudaMemcpy(h->d_acc, acc_save.data(), 8 * acc_n, cudaMemcpyHostToDevice));
     h->step = step0;
     CK(cudaMemcpy(h->d_step, &step0, 8, cudaMemcpyHostToDevice));
     return SOMA_OK;
   };
-  const int cand_threads[3] = {128, 256, 512};
-  const int cand_hist[2] = {SOMA_HIST_FUSED, SOMA_HIST_SEPARATE};
-  const int steps = 8;
+  const int steps = 6;
   float best = 1e30f;
-  int best_t = h->threads, best_h = h->hist_mode;
+  int best_c = h->ctas_per_sm, best_h = h->hist_mode;
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
   const int timing = h->opt.kernel_timing;
   h->opt.kernel_timing = 0;
-  for (int ti = 0; ti < 3; ++ti) {
-    if (h->opt.block_threads && cand_threads[ti] != h->opt.block_threads) continue;
-    for (int hi = 0; hi < 2; ++hi) {
-      if (h->opt.hist_mode != SOMA_HIST_AUTO && cand_hist[hi] != h->opt.hist_mode) continue;
-      h->hist_mode = cand_hist[hi];
-      if ((rc = rebuild_geometry(h, cand_threads[ti]))) return rc;
-      for (int i = 0; i < 2; ++i) enqueue_step(h, h->stream, i);  // warm-up
+  for (int c = 1; c <= h->max_ctas_per_sm; ++c) {
+    if (h->opt.ctas_per_sm && c != h->opt.ctas_per_sm) continue;
+    for (int hm = SOMA_HIST_FUSED; hm <= SOMA_HIST_SEPARATE; ++hm) {
+      if (h->opt.hist_mode != SOMA_HIST_AUTO && hm != h->opt.hist_mode) continue;
+      apply_geometry(h, c, hm);
+      if ((rc = enqueue_steps(h, h->stream, 0, 2))) return rc;  // warm-up
       CK(launch_advance(h->d_step, 2, h->stream));
       CK(cudaEventRecord(a, h->stream));
-      for (int i = 0; i < steps; ++i)
-        if ((rc = enqueue_step(h, h->stream, i))) return rc;
+      if ((rc = enqueue_steps(h, h->stream, 0, steps))) return rc;
       CK(launch_advance(h->d_step, steps, h->stream));
       CK(cudaEventRecord(b, h->stream));
       CK(cudaEventSynchronize(b));
@@ -910,8 +902,8 @@ int soma_autotune(soma_handle* h) {
       CK(cudaEventElapsedTime(&ms, a, b));
       if (ms < best) {
         best = ms;
-        best_t = cand_threads[ti];
-        best_h = cand_hist[hi];
+        best_c = c;
+        best_h = hm;
       }
       if ((rc = restore())) return rc;
     }
@@ -919,10 +911,7 @@ int soma_autotune(soma_handle* h) {
   h->opt.kernel_timing = timing;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  h->hist_mode = best_h;
-  if ((rc = rebuild_geometry(h, best_t))) return rc;
-  for (int s = 0; s < h->n_sys; ++s)
-    CK(cudaMemcpy(h->d_acc + h->host_sys[s].acc_first, &acc_total[s], 8, cudaMemcpyHostToDevice));
+  apply_geometry(h, best_c, best_h);
   return sync_all(h);
 }
 

@@ -1,0 +1,126 @@
+// soma_device.cuh -- device helpers shared by the kernels of libsoma:
+// Philox4x32-10, cell indexing, periodic wrap and minimum image, the
+// Metropolis trial of one bead, image bookkeeping.
+#pragma once
+
+#include <cstdint>
+
+#include "soma_internal.cuh"
+
+namespace soma {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The round keys are
+// precomputed per system on the host (seed lo/hi plus r times the published
+// Weyl increments), so a round is two wide multiplies and two 3-input XORs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, const uint32_t (*rk)[2]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[r][0], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ rk[r][1], (uint32_t)p0);
+  }
+  return c;
+}
+
+// Copy one system's constants into shared memory (all threads call).
+__device__ __forceinline__ void load_sys(SysDev* dst, const SysDev* src) {
+  const int words = sizeof(SysDev) / 4;
+  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldg(s + i);
+  __syncthreads();
+}
+
+__device__ __forceinline__ int cell_axis(float x, float cps, int n) {
+  const int i = (int)(x * cps);  // x >= 0, so truncation is floor
+  return min(max(i, 0), n - 1);
+}
+
+__device__ __forceinline__ int cell_of(const SysDev& S, float x, float y, float z) {
+  return (cell_axis(x, S.cps[0], S.nx) * S.ny + cell_axis(y, S.cps[1], S.ny)) * S.nz +
+         cell_axis(z, S.cps[2], S.nz);
+}
+
+// Wrap a proposed coordinate back into [0, L); delta receives the image step.
+__device__ __forceinline__ float wrap_coord(float p, float L, int& delta) {
+  delta = 0;
+  if (p >= L) {
+    p -= L;  // exact: L <= p < 2L
+    delta = 1;
+  } else if (p < 0.f) {
+    p += L;
+    delta = -1;
+    if (p >= L) {  // |p| below half an ulp of L: the wrapped value is 0 in this image
+      p = 0.f;
+      delta = 0;
+    }
+  }
+  return p;
+}
+
+__device__ __forceinline__ float min_image(float d, float L, float invL) {
+  return d - L * rintf(d * invL);
+}
+
+// One Metropolis trial of bead `bead` of logical chain `cid` at step t.
+// (x, y, z, cell) is updated in place on acceptance; wrap receives the image
+// steps packed as (dx+1) | (dy+1) << 2 | (dz+1) << 4 (21 = no wrap).
+// Neighbours a and b enter with weights wa, wb in {0, 1}.
+//   dE_bond = k_b sum_j (|r + d - r_j|^2 - |r - r_j|^2)
+//           = k_b (2 d . sum_j (r - r_j) + n_j |d|^2)
+__device__ __forceinline__ int try_move(const SysDev& S, const float* __restrict__ wt, uint32_t bead,
+                                        uint32_t cid, uint32_t t, float& x, float& y, float& z,
+                                        int& cell, int& wrap, float ax, float ay, float az, float wa,
+                                        float bx, float by, float bz, float wb) {
+  const uint4 r = philox10(make_uint4(bead, cid, t, (uint32_t)S.sys_index), S.rk);
+  // d_k = A (2 U_k - 1), U_k = (r_k >> 8) 2^-24; (r_k >> 8) 2^-23 - 1 is exact in FP32.
+  const float dx = S.A * fmaf((float)(r.x >> 8), 0x1p-23f, -1.0f);
+  const float dy = S.A * fmaf((float)(r.y >> 8), 0x1p-23f, -1.0f);
+  const float dz = S.A * fmaf((float)(r.z >> 8), 0x1p-23f, -1.0f);
+  const float sx = wa * min_image(x - ax, S.L[0], S.invL[0]) + wb * min_image(x - bx, S.L[0], S.invL[0]);
+  const float sy = wa * min_image(y - ay, S.L[1], S.invL[1]) + wb * min_image(y - by, S.L[1], S.invL[1]);
+  const float sz = wa * min_image(z - az, S.L[2], S.invL[2]) + wb * min_image(z - bz, S.L[2], S.invL[2]);
+  const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float dEb = fmaf(2.f, fmaf(dx, sx, fmaf(dy, sy, dz * sz)), (wa + wb) * d2);
+  int ex, ey, ez;
+  const float px = wrap_coord(x + dx, S.L[0], ex);
+  const float py = wrap_coord(y + dy, S.L[1], ey);
+  const float pz = wrap_coord(z + dz, S.L[2], ez);
+  const int cnew = cell_of(S, px, py, pz);
+  const float dE = fmaf(S.kb, dEb, __ldg(wt + cnew) - __ldg(wt + cell));
+  // Metropolis: accept iff dE + ln u < 0 with u = ((r_3 >> 9) + 1/2) 2^-23 in
+  // (0, 1); dE <= 0 always accepts because ln u < 0.
+  bool ok = dE <= 0.f;
+  if (!ok) {
+    const float u = fmaf((float)(r.w >> 9), 0x1p-23f, 0x1p-24f);
+    ok = dE + __logf(u) < 0.f;
+  }
+  if (ok) {
+    x = px;
+    y = py;
+    z = pz;
+    cell = cnew;
+    wrap = (ex + 1) | ((ey + 1) << 2) | ((ez + 1) << 4);
+  }
+  return ok ? 1 : 0;
+}
+
+__device__ __forceinline__ void apply_wrap(int16_t* img, int64_t bead, int wrap) {
+  if (wrap != 21) {
+    short4* p = reinterpret_cast<short4*>(img) + bead;
+    short4 v = *p;
+    v.x += (short)((wrap & 3) - 1);
+    v.y += (short)(((wrap >> 2) & 3) - 1);
+    v.z += (short)(((wrap >> 4) & 3) - 1);
+    *p = v;
+  }
+}
+
+__device__ __forceinline__ uint32_t current_step(const unsigned long long* step_base, int offset) {
+  return (uint32_t)(*step_base + (long long)offset);
+}
+
+}  // namespace soma

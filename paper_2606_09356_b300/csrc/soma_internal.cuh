@@ -37,19 +37,36 @@ struct alignas(16) SysDev {
   int64_t chain_base;           // first chain of this system in the global chain order
 };
 
-// A CTA's share of the move kernel: consecutive storage slots of one system.
-struct MoveTile {
-  int32_t sys;
-  int32_t first_chain;
-  int32_t n_chains;
-  int32_t acc_index;
+// Everything the move kernel needs for one system, passed by value as a
+// __grid_constant__ kernel parameter (constant bank: no loads in the loop).
+struct MoveArgs {
+  float L[3], invL[3], cps[3];
+  int32_t n[3];
+  float A, kb;
+  uint32_t rk[10][2];        // Philox round keys
+  int32_t N, n_A, P, sys_index;
+  int32_t n_poly, chains_per_tile, n_tiles, bin;
+  int64_t n_c;
+  float* x;
+  float* y;
+  float* z;
+  int16_t* img;
+  const uint32_t* chain_id;
+  uint32_t* counts;          // [2 buffers][2 types][n_c]
+  const float* w;            // [2 types][n_c]
+  unsigned long long* acc;   // one accepted-move slot per CTA of this system
+  const unsigned long long* step_base;
+  int* err;
 };
 
-// A CTA's share of a per-cell kernel: cells [begin, end) of one system.
-struct CellTile {
-  int32_t sys;
-  int32_t pad;
-  int64_t begin, end;
+// The field kernel's view of one system (also by value).
+struct FieldArgs {
+  uint32_t* counts;          // [2 buffers][2 types][n_c]
+  float* w;                  // [2 types][n_c]
+  int64_t n_c;
+  float inv_rho, chiN_N, kappaN_N;
+  int32_t frozen;
+  const unsigned long long* step_base;
 };
 
 // Device error word bits.

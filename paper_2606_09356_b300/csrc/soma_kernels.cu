@@ -1,8 +1,7 @@
 // soma_kernels.cu -- sm_103a kernels of the SCMF Monte Carlo step.
 //
-// (a) k_move_bin: set-parallel bead moves (even set, then odd set) with the
-//     histogram (b) fused as its epilogue; the moves are the biased trial
-//     moves and energy evaluations of the move kernel profiled in Sec. 2.2.
+// (a) the register/TMA move kernel lives in soma_move.cu; this file holds
+//     the generic move path for chains longer than 64 beads.
 // (b) k_bin: stand-alone density histogram (the density-field update of
 //     Sec. 2.2), used at start-up, after a restore and with the generic path.
 // (c) k_field: per-cell field rebuild from the counts, fused with zeroing of
@@ -15,218 +14,11 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "soma_device.cuh"
 #include "soma_internal.cuh"
 #include "soma_launch.h"
 
 namespace soma {
-
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  The round keys are
-// precomputed per system on the host (seed lo/hi plus r times the published
-// Weyl increments), so a round is two wide multiplies and two 3-input XORs.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox10(uint4 c, const uint32_t (*rk)[2]) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
-    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[r][0], (uint32_t)p1,
-                   (uint32_t)(p0 >> 32) ^ c.w ^ rk[r][1], (uint32_t)p0);
-  }
-  return c;
-}
-
-// Copy one system's constants into shared memory (all threads call).
-__device__ __forceinline__ void load_sys(SysDev* dst, const SysDev* src) {
-  const int words = sizeof(SysDev) / 4;
-  const uint32_t* s = reinterpret_cast<const uint32_t*>(src);
-  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
-  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldg(s + i);
-  __syncthreads();
-}
-
-__device__ __forceinline__ int cell_axis(float x, float cps, int n) {
-  const int i = (int)(x * cps);  // x >= 0, so truncation is floor
-  return min(max(i, 0), n - 1);
-}
-
-__device__ __forceinline__ int cell_of(const SysDev& S, float x, float y, float z) {
-  return (cell_axis(x, S.cps[0], S.nx) * S.ny + cell_axis(y, S.cps[1], S.ny)) * S.nz +
-         cell_axis(z, S.cps[2], S.nz);
-}
-
-// Wrap a proposed coordinate back into [0, L); delta receives the image step.
-__device__ __forceinline__ float wrap_coord(float p, float L, int& delta) {
-  delta = 0;
-  if (p >= L) {
-    p -= L;  // exact: L <= p < 2L
-    delta = 1;
-  } else if (p < 0.f) {
-    p += L;
-    delta = -1;
-    if (p >= L) {  // |p| below half an ulp of L: the wrapped value is 0 in this image
-      p = 0.f;
-      delta = 0;
-    }
-  }
-  return p;
-}
-
-__device__ __forceinline__ float min_image(float d, float L, float invL) {
-  return d - L * rintf(d * invL);
-}
-
-// One Metropolis trial of bead `bead` of logical chain `cid` at step t.
-// (x, y, z, cell) is updated in place on acceptance; wrap receives the image
-// steps packed as (dx+1) | (dy+1) << 2 | (dz+1) << 4 (21 = no wrap).
-// Neighbours a and b enter with weights wa, wb in {0, 1}.
-//   dE_bond = k_b sum_j (|r + d - r_j|^2 - |r - r_j|^2)
-//           = k_b (2 d . sum_j (r - r_j) + n_j |d|^2)
-__device__ __forceinline__ int try_move(const SysDev& S, const float* __restrict__ wt, uint32_t bead,
-                                        uint32_t cid, uint32_t t, float& x, float& y, float& z,
-                                        int& cell, int& wrap, float ax, float ay, float az, float wa,
-                                        float bx, float by, float bz, float wb) {
-  const uint4 r = philox10(make_uint4(bead, cid, t, (uint32_t)S.sys_index), S.rk);
-  // d_k = A (2 U_k - 1), U_k = (r_k >> 8) 2^-24; (r_k >> 8) 2^-23 - 1 is exact in FP32.
-  const float dx = S.A * fmaf((float)(r.x >> 8), 0x1p-23f, -1.0f);
-  const float dy = S.A * fmaf((float)(r.y >> 8), 0x1p-23f, -1.0f);
-  const float dz = S.A * fmaf((float)(r.z >> 8), 0x1p-23f, -1.0f);
-  const float sx = wa * min_image(x - ax, S.L[0], S.invL[0]) + wb * min_image(x - bx, S.L[0], S.invL[0]);
-  const float sy = wa * min_image(y - ay, S.L[1], S.invL[1]) + wb * min_image(y - by, S.L[1], S.invL[1]);
-  const float sz = wa * min_image(z - az, S.L[2], S.invL[2]) + wb * min_image(z - bz, S.L[2], S.invL[2]);
-  const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  const float dEb = fmaf(2.f, fmaf(dx, sx, fmaf(dy, sy, dz * sz)), (wa + wb) * d2);
-  int ex, ey, ez;
-  const float px = wrap_coord(x + dx, S.L[0], ex);
-  const float py = wrap_coord(y + dy, S.L[1], ey);
-  const float pz = wrap_coord(z + dz, S.L[2], ez);
-  const int cnew = cell_of(S, px, py, pz);
-  const float dE = fmaf(S.kb, dEb, __ldg(wt + cnew) - __ldg(wt + cell));
-  // Metropolis: accept iff dE + ln u < 0 with u = ((r_3 >> 9) + 1/2) 2^-23 in
-  // (0, 1); dE <= 0 always accepts because ln u < 0.
-  bool ok = dE <= 0.f;
-  if (!ok) {
-    const float u = fmaf((float)(r.w >> 9), 0x1p-23f, 0x1p-24f);
-    ok = dE + __logf(u) < 0.f;
-  }
-  if (ok) {
-    x = px;
-    y = py;
-    z = pz;
-    cell = cnew;
-    wrap = (ex + 1) | ((ey + 1) << 2) | ((ez + 1) << 4);
-  }
-  return ok ? 1 : 0;
-}
-
-__device__ __forceinline__ void apply_wrap(int16_t* img, int64_t bead, int wrap) {
-  if (wrap != 21) {
-    short4* p = reinterpret_cast<short4*>(img) + bead;
-    short4 v = *p;
-    v.x += (short)((wrap & 3) - 1);
-    v.y += (short)(((wrap >> 2) & 3) - 1);
-    v.z += (short)(((wrap >> 4) & 3) - 1);
-    *p = v;
-  }
-}
-
-__device__ __forceinline__ uint32_t current_step(const unsigned long long* step_base, int offset) {
-  return (uint32_t)(*step_base + (long long)offset);
-}
-
-// ---------------------------------------------------------------------------
-// (a) + fused (b): one warp holds 32/P chains, lane k of a chain holds beads
-// 2k (even set) and 2k+1 (odd set) in registers; neighbours come from the
-// adjacent lane by shuffles of width P.  Set 0 moves, then set 1 sees set
-// 0's accepted positions; the fields stay frozen for the step.  The final
-// cells are binned into count buffer t & 1 (zeroed by the previous field
-// kernel) when `bin` is set.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_move_bin(const SysDev* __restrict__ systems,
-                                                  const MoveTile* __restrict__ tiles,
-                                                  const unsigned long long* __restrict__ step_base,
-                                                  int step_offset, int bin) {
-  __shared__ SysDev S;
-  __shared__ unsigned int s_acc;
-  const MoveTile tile = tiles[blockIdx.x];
-  if (threadIdx.x == 0) s_acc = 0;
-  load_sys(&S, systems + tile.sys);
-  const uint32_t t = current_step(step_base, step_offset);
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int P = S.P, N = S.N;
-  const int k = lane & (P - 1);
-  const int chain_local = warp * (32 / P) + lane / P;
-  const bool chain_ok = chain_local < tile.n_chains;
-  const int slot = tile.first_chain + (chain_ok ? chain_local : 0);
-  const int e = 2 * k, o = 2 * k + 1;
-  const bool he = chain_ok && e < N, ho = chain_ok && o < N;
-  const int64_t base = (int64_t)slot * N;
-
-  float xe = 0.f, ye = 0.f, ze = 0.f, xo = 0.f, yo = 0.f, zo = 0.f;
-  if ((N & 1) == 0) {
-    if (he) {  // beads e, e+1 are adjacent and 8-byte aligned
-      const float2 vx = *reinterpret_cast<const float2*>(S.x + base + e);
-      const float2 vy = *reinterpret_cast<const float2*>(S.y + base + e);
-      const float2 vz = *reinterpret_cast<const float2*>(S.z + base + e);
-      xe = vx.x; xo = vx.y; ye = vy.x; yo = vy.y; ze = vz.x; zo = vz.y;
-    }
-  } else {
-    if (he) { xe = S.x[base + e]; ye = S.y[base + e]; ze = S.z[base + e]; }
-    if (ho) { xo = S.x[base + o]; yo = S.y[base + o]; zo = S.z[base + o]; }
-  }
-  const uint32_t cid = chain_ok ? __ldg(S.chain_id + slot) : 0u;
-  int ce = cell_of(S, xe, ye, ze), co = cell_of(S, xo, yo, zo);
-  int wre = 21, wro = 21;
-  int nacc = 0;
-
-  // set 0: even bead e; left neighbour 2k-1 lives in lane k-1, right is own odd
-  {
-    const float lx = __shfl_up_sync(0xffffffffu, xo, 1, P);
-    const float ly = __shfl_up_sync(0xffffffffu, yo, 1, P);
-    const float lz = __shfl_up_sync(0xffffffffu, zo, 1, P);
-    if (he) {
-      const float* wt = S.w + (e < S.n_A ? 0 : S.n_c);
-      nacc += try_move(S, wt, (uint32_t)e, cid, t, xe, ye, ze, ce, wre, lx, ly, lz, k > 0 ? 1.f : 0.f,
-                       xo, yo, zo, ho ? 1.f : 0.f);
-    }
-  }
-  // set 1: odd bead o; left is own (updated) even bead, right 2k+2 lives in lane k+1
-  {
-    const float rx = __shfl_down_sync(0xffffffffu, xe, 1, P);
-    const float ry = __shfl_down_sync(0xffffffffu, ye, 1, P);
-    const float rz = __shfl_down_sync(0xffffffffu, ze, 1, P);
-    if (ho) {
-      const float* wt = S.w + (o < S.n_A ? 0 : S.n_c);
-      nacc += try_move(S, wt, (uint32_t)o, cid, t, xo, yo, zo, co, wro, xe, ye, ze, 1.f, rx, ry, rz,
-                       (o + 1 < N) ? 1.f : 0.f);
-    }
-  }
-
-  if ((N & 1) == 0) {
-    if (he) {
-      *reinterpret_cast<float2*>(S.x + base + e) = make_float2(xe, xo);
-      *reinterpret_cast<float2*>(S.y + base + e) = make_float2(ye, yo);
-      *reinterpret_cast<float2*>(S.z + base + e) = make_float2(ze, zo);
-    }
-  } else {
-    if (he) { S.x[base + e] = xe; S.y[base + e] = ye; S.z[base + e] = ze; }
-    if (ho) { S.x[base + o] = xo; S.y[base + o] = yo; S.z[base + o] = zo; }
-  }
-  if (he) apply_wrap(S.img, base + e, wre);
-  if (ho) apply_wrap(S.img, base + o, wro);
-
-  if (bin) {
-    uint32_t* cnt = S.counts + (size_t)(t & 1u) * 2 * S.n_c;
-    if (he) atomicAdd(cnt + (e < S.n_A ? 0 : S.n_c) + ce, 1u);
-    if (ho) atomicAdd(cnt + (o < S.n_A ? 0 : S.n_c) + co, 1u);
-  }
-
-  nacc = __reduce_add_sync(0xffffffffu, nacc);
-  if (lane == 0 && nacc) atomicAdd(&s_acc, (unsigned)nacc);
-  __syncthreads();
-  if (threadIdx.x == 0) S.acc[tile.acc_index] += s_acc;
-}
 
 // ---------------------------------------------------------------------------
 // Generic move of one set for chains longer than 64 beads: one thread per
@@ -292,49 +84,50 @@ __global__ void k_bin(const SysDev* __restrict__ systems, int sys,
 // (c) Field rebuild from count buffer t & 1, fused with zeroing of buffer
 // (t + 1) & 1 for the next step:  phi_t = n_t / rho_bar,
 //   w_A = chiN/N phi_B + kappaN/N (phi_A + phi_B - 1), w_B = chiN/N phi_A + ...
-// Held (frozen) fields are not overwritten.
+// Held (frozen) fields are not overwritten.  One system per launch, one
+// group of four cells per thread (16-byte loads and stores).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void field_of(const SysDev& S, uint32_t nA, uint32_t nB, float& wA,
-                                         float& wB) {
-  const float pA = (float)nA * S.inv_rho, pB = (float)nB * S.inv_rho;
-  const float ex = S.kappaN_N * (pA + pB - 1.f);
-  wA = fmaf(S.chiN_N, pB, ex);
-  wB = fmaf(S.chiN_N, pA, ex);
+__device__ __forceinline__ void field_pair(const FieldArgs& f, uint32_t nA, uint32_t nB, float& wA, float& wB) {
+  const float pA = (float)nA * f.inv_rho, pB = (float)nB * f.inv_rho;
+  const float ex = f.kappaN_N * (pA + pB - 1.f);
+  wA = fmaf(f.chiN_N, pB, ex);
+  wB = fmaf(f.chiN_N, pA, ex);
 }
 
-__global__ void k_field(const SysDev* __restrict__ systems, const CellTile* __restrict__ tiles,
-                        const unsigned long long* __restrict__ step_base, int step_offset) {
-  __shared__ SysDev S;
-  const CellTile tile = tiles[blockIdx.x];
-  load_sys(&S, systems + tile.sys);
-  const uint32_t t = current_step(step_base, step_offset);
-  const int64_t nc = S.n_c;
-  const uint32_t* cur = S.counts + (size_t)(t & 1u) * 2 * nc;
-  uint32_t* nxt = S.counts + (size_t)((t + 1u) & 1u) * 2 * nc;
-  const bool write_w = !S.frozen;
-  if ((nc & 3) == 0 && (tile.begin & 3) == 0 && (tile.end & 3) == 0) {
-    for (int64_t c = tile.begin + 4 * (int64_t)threadIdx.x; c < tile.end; c += 4 * (int64_t)blockDim.x) {
-      const uint4 a = *reinterpret_cast<const uint4*>(cur + c);
-      const uint4 b = *reinterpret_cast<const uint4*>(cur + nc + c);
-      if (write_w) {
+__global__ void __launch_bounds__(256) k_field(const __grid_constant__ FieldArgs f, int step_offset) {
+  const uint32_t t = (uint32_t)(*f.step_base + (long long)step_offset);
+  const int64_t nc = f.n_c;
+  const uint32_t* __restrict__ cur = f.counts + (size_t)(t & 1u) * 2 * nc;
+  uint32_t* __restrict__ nxt = f.counts + (size_t)((t + 1u) & 1u) * 2 * nc;
+  float* __restrict__ w = f.w;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if ((nc & 3) == 0) {
+    const int64_t n4 = nc >> 2;
+    const uint4* cur4 = reinterpret_cast<const uint4*>(cur);
+    uint4* nxt4 = reinterpret_cast<uint4*>(nxt);
+    float4* w4 = reinterpret_cast<float4*>(w);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+      const uint4 a = __ldg(cur4 + i);
+      const uint4 b = __ldg(cur4 + n4 + i);
+      if (!f.frozen) {
         float4 wa, wb;
-        field_of(S, a.x, b.x, wa.x, wb.x);
-        field_of(S, a.y, b.y, wa.y, wb.y);
-        field_of(S, a.z, b.z, wa.z, wb.z);
-        field_of(S, a.w, b.w, wa.w, wb.w);
-        *reinterpret_cast<float4*>(S.w + c) = wa;
-        *reinterpret_cast<float4*>(S.w + nc + c) = wb;
+        field_pair(f, a.x, b.x, wa.x, wb.x);
+        field_pair(f, a.y, b.y, wa.y, wb.y);
+        field_pair(f, a.z, b.z, wa.z, wb.z);
+        field_pair(f, a.w, b.w, wa.w, wb.w);
+        w4[i] = wa;
+        w4[n4 + i] = wb;
       }
-      *reinterpret_cast<uint4*>(nxt + c) = make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(nxt + nc + c) = make_uint4(0, 0, 0, 0);
+      nxt4[i] = make_uint4(0, 0, 0, 0);
+      nxt4[n4 + i] = make_uint4(0, 0, 0, 0);
     }
   } else {
-    for (int64_t c = tile.begin + threadIdx.x; c < tile.end; c += blockDim.x) {
-      if (write_w) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
+      if (!f.frozen) {
         float wa, wb;
-        field_of(S, cur[c], cur[nc + c], wa, wb);
-        S.w[c] = wa;
-        S.w[nc + c] = wb;
+        field_pair(f, cur[c], cur[nc + c], wa, wb);
+        w[c] = wa;
+        w[nc + c] = wb;
       }
       nxt[c] = 0u;
       nxt[nc + c] = 0u;
@@ -624,12 +417,6 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __res
 // ---------------------------------------------------------------------------
 // Host-side launchers.
 // ---------------------------------------------------------------------------
-cudaError_t launch_move_bin(const SysDev* systems, const MoveTile* tiles, int n_tiles, int threads,
-                            const unsigned long long* step_base, int step_offset, int bin, cudaStream_t s) {
-  k_move_bin<<<n_tiles, threads, 0, s>>>(systems, tiles, step_base, step_offset, bin);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_move_generic(const SysDev* systems, int sys, int64_t n_poly, int N,
                                 const unsigned long long* step_base, int step_offset, int sm_count,
                                 cudaStream_t s) {
@@ -653,9 +440,12 @@ cudaError_t launch_bin(const SysDev* systems, int sys, int64_t n_b, const unsign
   return cudaGetLastError();
 }
 
-cudaError_t launch_field(const SysDev* systems, const CellTile* tiles, int n_tiles, const unsigned long long* step_base,
-                         int step_offset, cudaStream_t s) {
-  k_field<<<n_tiles, 256, 0, s>>>(systems, tiles, step_base, step_offset);
+cudaError_t launch_field(const FieldArgs& f, int step_offset, cudaStream_t s) {
+  const int64_t groups = (f.n_c & 3) == 0 ? (f.n_c >> 2) : f.n_c;
+  int64_t blocks = (groups + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  if (blocks < 1) blocks = 1;
+  k_field<<<(unsigned)blocks, 256, 0, s>>>(f, step_offset);
   return cudaGetLastError();
 }
 

@@ -8,15 +8,16 @@
 
 namespace soma {
 
-cudaError_t launch_move_bin(const SysDev* systems, const MoveTile* tiles, int n_tiles, int threads,
-                            const unsigned long long* step_base, int step_offset, int bin, cudaStream_t s);
+// Kernel (a) with fused (b), soma_move.cu.
+cudaError_t launch_move(const MoveArgs& a, int grid, int step_offset, cudaStream_t s);
+int move_kernel_max_ctas_per_sm();
+int move_kernel_chains_per_tile(int P);
 cudaError_t launch_move_generic(const SysDev* systems, int sys, int64_t n_poly, int N,
                                 const unsigned long long* step_base, int step_offset, int sm_count,
                                 cudaStream_t s);
 cudaError_t launch_bin(const SysDev* systems, int sys, int64_t n_b, const unsigned long long* step_base,
                        int step_offset, int sm_count, cudaStream_t s);
-cudaError_t launch_field(const SysDev* systems, const CellTile* tiles, int n_tiles,
-                         const unsigned long long* step_base, int step_offset, cudaStream_t s);
+cudaError_t launch_field(const FieldArgs& f, int step_offset, cudaStream_t s);
 cudaError_t launch_field_from_phi(const SysDev* systems, int sys, const float* phi, int sm_count, cudaStream_t s);
 cudaError_t launch_advance(unsigned long long* step_base, long long n, cudaStream_t s);
 cudaError_t launch_init(const SysDev* systems, int sys, int64_t n_poly, cudaStream_t s);
@@ -37,9 +38,9 @@ cudaError_t launch_structure_factor(const SysDev* systems, int sys, int nq, cons
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t s);
 
 // Chain reorder (soma_sort.cu): sort the chains of every system by the
-// Morton key of their first bead's cell and permute positions, images and
-// chain ids into the alternate buffers, then swap the buffer pointers in the
-// device-side system table.
+// Morton key of their first bead's position, permute positions, images and
+// chain ids into the alternate buffers and copy them back, so the arrays
+// keep their addresses.
 struct SortWork {
   unsigned long long* keys_in;
   unsigned long long* keys_out;

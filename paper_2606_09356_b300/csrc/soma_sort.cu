@@ -7,7 +7,7 @@
 // cache-resident cell ranges.  The random numbers follow the logical chain id
 // carried along in chain_id, so a reorder never changes the trajectory.
 // The sort itself is CUB's device radix sort (a library primitive); keys,
-// permutation and pointer swap are kernels of this file.
+// permutation and copy-back are kernels of this file.
 #include <cub/device/device_radix_sort.cuh>
 #include <cuda_runtime.h>
 
@@ -64,16 +64,24 @@ __global__ void k_permute(const SysDev* __restrict__ systems, const int32_t* __r
   }
 }
 
-__global__ void k_swap_buffers(SysDev* systems, int n_sys) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n_sys) return;
-  SysDev& S = systems[s];
-  float* t;
-  t = S.x; S.x = S.x_alt; S.x_alt = t;
-  t = S.y; S.y = S.y_alt; S.y_alt = t;
-  t = S.z; S.z = S.z_alt; S.z_alt = t;
-  int16_t* ti = S.img; S.img = S.img_alt; S.img_alt = ti;
-  uint32_t* tc = S.chain_id; S.chain_id = S.chain_id_alt; S.chain_id_alt = tc;
+// Copy the permuted chains back from the alternate buffers.
+__global__ void k_copy_back(const SysDev* __restrict__ systems, const int32_t* __restrict__ chain_sys,
+                            int64_t n_chains) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_chains; j += warps) {
+    const SysDev& S = systems[chain_sys[j]];
+    const int64_t slot = j - S.chain_base;
+    const int N = S.N;
+    for (int i = lane; i < N; i += 32) {
+      const int64_t b = slot * N + i;
+      S.x[b] = S.x_alt[b];
+      S.y[b] = S.y_alt[b];
+      S.z[b] = S.z_alt[b];
+      reinterpret_cast<short4*>(S.img)[b] = reinterpret_cast<const short4*>(S.img_alt)[b];
+    }
+    if (lane == 0) S.chain_id[slot] = S.chain_id_alt[slot];
+  }
 }
 
 size_t sort_temp_bytes(int64_t n_chains, int end_bit) {
@@ -91,7 +99,7 @@ cudaError_t launch_reorder(SysDev* systems, int n_sys, const SortWork& w, int sm
                                                   w.n_chains, 0, w.end_bit, s);
   if (e != cudaSuccess) return e;
   k_permute<<<blocks, 256, 0, s>>>(systems, w.chain_sys, w.n_chains, w.vals_out);
-  k_swap_buffers<<<(n_sys + 63) / 64, 64, 0, s>>>(systems, n_sys);
+  k_copy_back<<<blocks, 256, 0, s>>>(systems, w.chain_sys, w.n_chains);
   return cudaGetLastError();
 }
 

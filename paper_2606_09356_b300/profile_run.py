@@ -17,12 +17,12 @@ def main():
     p.add_argument("--graph-steps", type=int, default=0)
     p.add_argument("--sort-interval", type=int, default=-1)
     p.add_argument("--hist-mode", type=int, default=0)
-    p.add_argument("--threads", type=int, default=0)
+    p.add_argument("--ctas-per-sm", type=int, default=0)
     a = p.parse_args()
     _build.build()
     s = soma.System(**workloads.system_kwargs(a.workload))
     with soma.Handle(s, graph_steps=a.graph_steps, sort_interval=a.sort_interval, hist_mode=a.hist_mode,
-                     block_threads=a.threads) as h:
+                     ctas_per_sm=a.ctas_per_sm) as h:
         t = time.perf_counter()
         h.mc_steps(a.steps)
         h.sync()
