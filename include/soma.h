@@ -202,6 +202,30 @@ int soma_autotune(soma_handle* h);
  * device function the move kernel uses).  Synchronous. */
 int soma_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n);
 
+/* S(q) of positions the caller already holds on the device, with no device
+ * allocation: the paper has no counterpart; this entry point serves callers
+ * that must not allocate GPU memory at the point of the call -- code whose
+ * device memory comes from a fixed arena or pool it may not bypass, code on a
+ * path where a cudaMalloc/cudaFree would synchronise the device with work in
+ * flight, or a loop that samples S(q) often and cannot pay an allocation per
+ * sample.  It needs no soma handle.
+ *   pos    device FP32 [n_beads][3], wrapped into [0, L), bead = chain*N + i
+ *   N, n_A chain length and A-block length (types as in soma_system_desc)
+ *   box    host double[3], the box edges
+ *   m_xyz  host int32 [nq][3] integer q vectors, q = 2 pi m / L
+ *   S      device double [nq] output, (1/n_beads)|sum_j s_j exp(i q.r_j)|^2
+ *   stream cudaStream_t (NULL = default stream); asynchronous.
+ * Scratch (the q list and the FP64 accumulators) is a fixed static device
+ * array sized for at most 4096 q vectors (about 112 KiB on every GPU that
+ * loads the library, held until exit); nq > 4096 returns SOMA_EINVAL.  The
+ * first call on each device (that device current) looks up the array's
+ * device address and should come before any stream capture.  All calls share
+ * the array and each clears it first: calls that overlap on the GPU race.
+ * Never calls cudaMalloc, cudaFree or an allocating library routine. */
+int soma_structure_factor_noalloc(const float* pos, int64_t n_beads, int32_t N, int32_t n_A,
+                                  const double* box, int nq, const int32_t* m_xyz, double* S,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,7 +36,7 @@ EXPORTS = (
     "soma_mc_steps", "soma_sync", "soma_get_density", "soma_get_fields", "soma_set_density",
     "soma_freeze_fields", "soma_get_state", "soma_set_state", "soma_observables", "soma_get_accepted",
     "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
-    "soma_philox4x32",
+    "soma_philox4x32", "soma_structure_factor_noalloc",
 )
 
 
@@ -120,6 +120,7 @@ def load_library(path=None):
     L.soma_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]
     L.soma_autotune.argtypes = [vp]
     L.soma_philox4x32.argtypes = [vp, vp, vp, sz]
+    L.soma_structure_factor_noalloc.argtypes = [vp, i64, ctypes.c_int32, ctypes.c_int32, vp, i32, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("soma_destroy", "soma_strerror"):
             getattr(L, name).restype = ctypes.c_int
@@ -181,6 +182,18 @@ def soma_philox4x32(ctr, key):
     out = np.zeros_like(ctr)
     _check(load_library().soma_philox4x32(_ptr(ctr), _ptr(key), _ptr(out), len(ctr)), "soma_philox4x32")
     return out
+
+
+def soma_structure_factor_noalloc(pos, n_beads, N, n_A, box, m, S, stream=None):
+    """S(q) of device positions ``pos`` [n,3] into device ``S`` [nq] (torch
+    tensors or raw device pointers); the library allocates nothing."""
+    box = np.ascontiguousarray(box, np.float64)
+    m = np.ascontiguousarray(m, np.int32).reshape(-1, 3)
+    p = pos if isinstance(pos, int) else pos.data_ptr()
+    q = S if isinstance(S, int) else S.data_ptr()
+    _check(load_library().soma_structure_factor_noalloc(ctypes.c_void_p(p), int(n_beads), int(N), int(n_A),
+                                                         _ptr(box), len(m), _ptr(m), ctypes.c_void_p(q), stream),
+           "soma_structure_factor_noalloc")
 
 
 def soma_sync(h, stream=None):
