@@ -4,7 +4,8 @@
                     [--impl reference] [--no-batched] [--no-e2e]
 
 One JSON line on rank 0.  A step is one whole Monte Carlo step of every bead
-(move kernel with fused histogram, then field kernel, plus the periodic chain
+(one move kernel: moves against the fields of the previous step's counts,
+fused histogram, clearing of the next count buffer; plus the periodic chain
 reorder when it falls due).  Inputs are resident in HBM; between timed steps
 a 256 MiB buffer (twice the L2) is written so every step starts from a cold
 L2; each step is bracketed by CUDA events on the library's stream and the
@@ -122,6 +123,28 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def rank_system_kwargs(workload, rank):
+    """Each rank runs its own replica of the workload: same shape, its own
+    random stream (system_id = rank), no data exchanged between ranks."""
+    from paper_2606_09356_b300 import workloads
+    return {**workloads.system_kwargs(workload), "system_id": rank}
+
+
+def aggregate(total_ms, moves_local, pg=None, device=None):
+    """Whole-job throughput: moves of all ranks over the slowest rank's time.
+    Returns (max_ms, total_moves, moves_per_s)."""
+    if pg is None:
+        return total_ms, moves_local, moves_local / (total_ms * 1e-3)
+    import torch
+    t = torch.tensor([float(total_ms), float(moves_local)], dtype=torch.float64, device=device)
+    mx = t[:1].clone()
+    pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+    tot = t[1:].clone()
+    pg.all_reduce(tot, op=pg.ReduceOp.SUM)
+    max_ms, moves = float(mx.item()), float(tot.item())
+    return max_ms, moves, moves / (max_ms * 1e-3)
+
+
 def workload_desc(name, c):
     return (f"{name}: {c['n_poly']} AB diblocks N={c['N']} n_A={c['n_A']}, box {c['box'][0]:g}^3 R_e, "
             f"grid {c['grid'][0]}^3, chiN={c['chiN']:g}, kappaN={c['kappaN']:g}, FP32 positions + int16 image")
@@ -135,9 +158,11 @@ def algorithmic_bytes(n_b, n_c):
 
 
 def move_kernel_bytes(n_b, n_c):
-    """Algorithmic bytes of one move-kernel launch: positions read + written
-    (24 B/bead), fields read (8 B/cell), counts written (8 B/cell)."""
-    return 24 * n_b + 16 * n_c
+    """Algorithmic bytes of one move-kernel launch.  The kernel performs the
+    whole step (moves against the fields of the previous counts, re-binning,
+    clearing of the next count buffer), so its share is the whole step's
+    24 B per bead + 32 B per cell."""
+    return algorithmic_bytes(n_b, n_c)
 
 
 # ---------------------------------------------------------------------------
@@ -240,7 +265,7 @@ def run_gpu(args):
     soma.load_library()
 
     c = workloads.system_kwargs(args.workload)
-    system = soma.System(**{**c, "system_id": rank})
+    system = soma.System(**rank_system_kwargs(args.workload, rank))
     n_b, n_c = system.n_beads, system.n_cells
     hbm_peak, peak_kind = _peaks()
 
@@ -282,14 +307,11 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     kt = h.kernel_times(reset=True)
-    if pg:
-        t = torch.tensor([total_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    moves = args.steps * n_b * ws
-    value = moves / (total_ms * 1e-3)
+    total_ms, moves, value = aggregate(total_ms, args.steps * n_b, pg, device="cuda")
     sorts = kt["reorder"][1]
-    launches = args.steps * 3 + sorts * 3  # move, field, step-counter advance; 3 own kernels per reorder
+    # per step: the move kernel and the step-counter advance; 3 own kernels per reorder
+    launches = args.steps * (kt["move"][1] // max(1, args.steps) + kt["bin"][1] // max(1, args.steps)
+                             + kt["field"][1] // max(1, args.steps) + 1) + sorts * 3
 
     # dominant kernel: the move kernel (its average launch duration)
     mv_ms, mv_n = kt["move"]
@@ -299,7 +321,7 @@ def run_gpu(args):
     traffic = _profiled_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_move", "move_ms": move_avg, "field_ms": fd_ms / max(1, fd_n),
+                "kernel": "k_move", "move_ms": move_avg, "field_ms": (fd_ms / fd_n) if fd_n else None,
                 "step_frac": algorithmic_bytes(n_b, n_c) * args.steps / (total_ms * 1e-3) / 1e9 / hbm_peak}
 
     # steady state without flushes: CUDA-graph replay of many steps (L2-warm)

@@ -1,7 +1,7 @@
 // soma_api.cu -- the C ABI of include/soma.h: handle life cycle, step
-// scheduling (plain launches or CUDA-graph replay; independent systems run as
-// parallel graph branches), state I/O, observables, reorder scheduling,
-// per-kernel timing and the autotuner.
+// scheduling (plain launches or CUDA-graph replay; a batch of independent
+// systems steps in one persistent launch), state I/O, observables, reorder
+// scheduling, per-kernel timing and the autotuner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,7 +23,6 @@ namespace {
 
 constexpr int kDefaultSortInterval = 200;
 constexpr int kDefaultGraphSteps = 16;
-constexpr int kMaxBranchStreams = 32;
 enum { T_MOVE = 0, T_BIN = 1, T_FIELD = 2, T_SORT = 3 };
 
 struct TimedEvent {
@@ -43,9 +42,6 @@ struct soma_handle {
   int device = 0, sm_count = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // dedicated stream for graph capture
-  std::vector<cudaStream_t> branch;   // streams of the per-system graph branches
-  cudaEvent_t fork = nullptr;
-  std::vector<cudaEvent_t> join;
   soma_options opt{};
   int n_sys = 0;
   std::vector<soma_system_desc> desc;
@@ -53,17 +49,24 @@ struct soma_handle {
   SysDev* d_sys = nullptr;
   std::vector<MoveArgs> margs;
   std::vector<FieldArgs> fargs;
+  std::vector<BatchArgs> batches;          // groups of up to kMaxBatch register-path systems
+  std::vector<std::vector<int>> batch_members;
   std::vector<int> n_tiles;
+  std::vector<char> phi_pending;  // next step moves against coupling-supplied fields
   std::vector<void*> owned;
   // launch geometry
   int max_ctas_per_sm = 1;
+  int max_ctas_batch = 1;
   int ctas_per_sm = 1;
   int hist_mode = SOMA_HIST_FUSED;
   int sort_interval = kDefaultSortInterval;
   int acc_per_sys = 1;
   unsigned long long* d_acc = nullptr;
-  // step counter (device base + host mirror of enqueued steps)
+  // Step counters, one per system (all equal), read by CUDA-graph replays;
+  // plain launches carry the step number itself.  h->step mirrors the steps
+  // enqueued; dev_synced says whether the counters hold it.
   unsigned long long* d_step = nullptr;
+  bool dev_synced = true;
   uint64_t step = 0;
   uint64_t acc_since = 0;  // step at which the acceptance counters were last cleared
   uint64_t steps_since_sort = 0;
@@ -161,9 +164,28 @@ int validate_desc(const soma_system_desc& d) {
   return SOMA_OK;
 }
 
-int move_grid(const soma_handle* h, int s) {
-  const int g = std::min(h->n_tiles[s], h->sm_count * h->ctas_per_sm);
-  return std::max(g, 1);
+// Persistent grid of a move launch: every resident slot, at most one CTA per tile.
+int move_grid(const soma_handle* h, int64_t tiles, int max_ctas) {
+  const int64_t capacity = (int64_t)h->sm_count * std::min(h->ctas_per_sm, max_ctas);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(capacity, tiles));
+}
+
+StepRef fixed_step(long long t) {
+  StepRef r;
+  r.counter = nullptr;
+  r.fixed = t;
+  r.use_counter = 0;
+  r.offset = 0;
+  return r;
+}
+
+StepRef counter_step(const unsigned long long* counter, int offset) {
+  StepRef r;
+  r.counter = counter;
+  r.fixed = 0;
+  r.use_counter = 1;
+  r.offset = offset;
+  return r;
 }
 
 void build_args(soma_handle* h) {
@@ -201,8 +223,11 @@ void build_args(soma_handle* h) {
     a.chain_id = S.chain_id;
     a.counts = S.counts;
     a.w = S.w;
+    a.inv_rho = S.inv_rho;
+    a.chiN_N = S.chiN_N;
+    a.kappaN_N = S.kappaN_N;
+    a.from_counts = S.frozen ? 0 : 1;
     a.acc = h->d_acc + S.acc_first;
-    a.step_base = h->d_step;
     a.err = h->d_err;
     h->n_tiles[s] = a.n_tiles;
 
@@ -215,7 +240,29 @@ void build_args(soma_handle* h) {
     f.chiN_N = S.chiN_N;
     f.kappaN_N = S.kappaN_N;
     f.frozen = S.frozen;
-    f.step_base = h->d_step;
+  }
+  // batched launches: register-path systems in groups of at most kMaxBatch
+  h->batches.clear();
+  h->batch_members.clear();
+  if (h->n_sys > 1) {
+    std::vector<int> reg;
+    for (int s = 0; s < h->n_sys; ++s)
+      if (h->host_sys[s].P) reg.push_back(s);
+    for (size_t g0 = 0; g0 < reg.size(); g0 += kMaxBatch) {
+      BatchArgs b;
+      std::memset(&b, 0, sizeof(b));
+      std::vector<int> members(reg.begin() + g0, reg.begin() + std::min(reg.size(), g0 + kMaxBatch));
+      b.n_sys = (int)members.size();
+      int tiles = 0;
+      for (int i = 0; i < b.n_sys; ++i) {
+        b.tile_start[i] = tiles;
+        b.sys[i] = h->margs[members[i]];
+        tiles += h->n_tiles[members[i]];
+      }
+      b.tile_start[b.n_sys] = tiles;
+      h->batches.push_back(b);
+      h->batch_members.push_back(members);
+    }
   }
 }
 
@@ -238,51 +285,79 @@ void end_timed(soma_handle* h, cudaStream_t s, TimedEvent& te) {
   h->launches[te.kind] += 1;
 }
 
-// Steps offset0 .. offset0+n-1 (relative to the device step base) of system
-// `sys` on stream `s`: move (+ fused histogram), [separate histogram], field.
-int enqueue_system(soma_handle* h, cudaStream_t s, int sys, int offset0, int n) {
-  const bool timing = h->opt.kernel_timing != 0;
+// Step i of a sequence: the fixed number t0 + i (plain launches) or the
+// device counter + i (graph capture).
+StepRef step_ref(const soma_handle* h, int sys, bool graph, long long t0, int i) {
+  return graph ? counter_step(h->d_step + sys, i) : fixed_step(t0 + i);
+}
+
+// Histogram, field array and the generic move: the parts of a step that are
+// not the register move kernel.
+int enqueue_aux(soma_handle* h, cudaStream_t s, int sys, StepRef r, bool timing, bool moved) {
   const SysDev& S = h->host_sys[sys];
-  const bool separate_bin = S.P == 0 || h->hist_mode == SOMA_HIST_SEPARATE;
   TimedEvent te;
-  for (int i = 0; i < n; ++i) {
-    const int off = offset0 + i;
+  if (S.P == 0 && !moved) {
     if (timing) begin_timed(h, s, te, T_MOVE);
-    if (S.P)
-      CK(launch_move(h->margs[sys], move_grid(h, sys), off, s));
-    else
-      CK(launch_move_generic(h->d_sys, sys, S.n_poly, S.N, h->d_step, off, h->sm_count, s));
+    CK(launch_move_generic(h->d_sys, sys, S.n_poly, S.N, r, h->sm_count, s));
     if (timing) end_timed(h, s, te);
-    if (separate_bin) {
-      if (timing) begin_timed(h, s, te, T_BIN);
-      CK(launch_bin(h->d_sys, sys, S.n_b, h->d_step, off, h->sm_count, s));
-      if (timing) end_timed(h, s, te);
-    }
+  }
+  if (S.P == 0 || h->hist_mode == SOMA_HIST_SEPARATE) {
+    if (timing) begin_timed(h, s, te, T_BIN);
+    CK(launch_bin(h->d_sys, sys, S.n_b, r, h->sm_count, s));
+    if (timing) end_timed(h, s, te);
+  }
+  if (S.P == 0) {
     if (timing) begin_timed(h, s, te, T_FIELD);
-    CK(launch_field(h->fargs[sys], off, s));
+    CK(launch_field(h->fargs[sys], r, 1, s));
     if (timing) end_timed(h, s, te);
   }
   return SOMA_OK;
 }
 
-// n steps of every system.  A single system runs on `s`; several systems run
-// as independent branches (fork on `s`, one branch stream per system, join
-// back on `s`), so no system waits for another inside the n steps.
-int enqueue_steps(soma_handle* h, cudaStream_t s, int offset0, int n) {
+// n steps of every system on stream `s`.  One system: one move kernel per
+// step (fields from the previous counts, fused histogram, clearing of the
+// next count buffer).  Several systems: one k_move_batch launch per step and
+// group of up to kMaxBatch systems.  Chains longer than 64 beads: generic
+// move, histogram and field array per system.
+int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t0) {
+  const bool timing = h->opt.kernel_timing != 0;
+  const bool batched = h->n_sys > 1;
   int rc;
-  if (h->n_sys == 1 || h->opt.kernel_timing) {
-    for (int sys = 0; sys < h->n_sys; ++sys)
-      if ((rc = enqueue_system(h, s, sys, offset0, n))) return rc;
-    return SOMA_OK;
-  }
-  CK(cudaEventRecord(h->fork, s));
-  const int nb = (int)h->branch.size();
-  for (int b = 0; b < nb; ++b) CK(cudaStreamWaitEvent(h->branch[b], h->fork, 0));
-  for (int sys = 0; sys < h->n_sys; ++sys)
-    if ((rc = enqueue_system(h, h->branch[sys % nb], sys, offset0, n))) return rc;
-  for (int b = 0; b < nb; ++b) {
-    CK(cudaEventRecord(h->join[b], h->branch[b]));
-    CK(cudaStreamWaitEvent(s, h->join[b], 0));
+  for (int i = 0; i < n; ++i) {
+    if (batched) {
+      for (size_t g = 0; g < h->batches.size(); ++g) {
+        const BatchArgs* b = &h->batches[g];
+        BatchArgs pending_copy;
+        if (i == 0) {  // coupling-supplied fields move the first step of their system
+          bool any = false;
+          for (int m = 0; m < b->n_sys; ++m) any |= h->phi_pending[h->batch_members[g][m]] != 0;
+          if (any) {
+            pending_copy = *b;
+            for (int m = 0; m < b->n_sys; ++m)
+              if (h->phi_pending[h->batch_members[g][m]]) pending_copy.sys[m].from_counts = 0;
+            b = &pending_copy;
+          }
+        }
+        TimedEvent te;
+        if (timing) begin_timed(h, s, te, T_MOVE);
+        CK(launch_move_batch(*b, move_grid(h, b->tile_start[b->n_sys], h->max_ctas_batch),
+                             step_ref(h, 0, graph, t0, i), s));
+        if (timing) end_timed(h, s, te);
+      }
+      for (int sys = 0; sys < h->n_sys; ++sys)
+        if ((rc = enqueue_aux(h, s, sys, step_ref(h, sys, graph, t0, i), timing, false))) return rc;
+    } else {
+      const SysDev& S = h->host_sys[0];
+      const StepRef r = step_ref(h, 0, graph, t0, i);
+      if (S.P) {
+        const bool from_counts = !S.frozen && !(i == 0 && h->phi_pending[0]);
+        TimedEvent te;
+        if (timing) begin_timed(h, s, te, T_MOVE);
+        CK(launch_move(h->margs[0], move_grid(h, h->n_tiles[0], h->max_ctas_per_sm), from_counts, r, s));
+        if (timing) end_timed(h, s, te);
+      }
+      if ((rc = enqueue_aux(h, s, 0, r, timing, false))) return rc;
+    }
   }
   return SOMA_OK;
 }
@@ -300,8 +375,8 @@ int capture_graph(soma_handle* h, int steps) {
   drop_graph(h);
   cudaStream_t cs = h->cap_stream;
   CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_steps(h, cs, 0, steps);
-  if (rc == SOMA_OK && launch_advance(h->d_step, steps, cs) != cudaSuccess) rc = SOMA_ECUDA;
+  int rc = enqueue_steps(h, cs, steps, true, 0);
+  if (rc == SOMA_OK && launch_advance(h->d_step, h->n_sys, steps, cs) != cudaSuccess) rc = SOMA_ECUDA;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &g);
   if (rc != SOMA_OK) {
@@ -316,14 +391,14 @@ int capture_graph(soma_handle* h, int steps) {
   return SOMA_OK;
 }
 
-// Bin the current positions into buffer (step - 1) & 1, clear buffer step & 1
-// and rebuild the fields (unless held).
+// Clear the three count buffers, bin the current positions into buffer
+// (step - 1) mod 3 and fill the field array from them (unless held).
 int rebin_all(soma_handle* h, cudaStream_t s) {
   for (int g = 0; g < h->n_sys; ++g) {
     SysDev& S = h->host_sys[g];
-    CK(cudaMemsetAsync(S.counts, 0, sizeof(uint32_t) * 4 * S.n_c, s));
-    CK(launch_bin(h->d_sys, g, S.n_b, h->d_step, -1, h->sm_count, s));
-    CK(launch_field(h->fargs[g], -1, s));
+    CK(cudaMemsetAsync(S.counts, 0, sizeof(uint32_t) * 6 * S.n_c, s));
+    CK(launch_bin(h->d_sys, g, S.n_b, fixed_step((long long)h->step - 1), h->sm_count, s));
+    CK(launch_field(h->fargs[g], fixed_step((long long)h->step - 1), 0, s));
   }
   return SOMA_OK;
 }
@@ -399,11 +474,6 @@ void soma_destroy(soma_handle* h) {
   }
   drop_graph(h);
   dev_free_all(h);
-  for (auto st : h->branch)
-    if (st) cudaStreamDestroy(st);
-  for (auto ev : h->join)
-    if (ev) cudaEventDestroy(ev);
-  if (h->fork) cudaEventDestroy(h->fork);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
@@ -446,23 +516,14 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return bail(SOMA_ECUDA);
   h->sm_count = prop.multiProcessorCount;
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess)
+      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(SOMA_ECUDA);
-  if (n_sys > 1) {
-    const int nb = std::min(n_sys, kMaxBranchStreams);
-    h->branch.resize(nb, nullptr);
-    h->join.resize(nb, nullptr);
-    for (int b = 0; b < nb; ++b)
-      if (cudaStreamCreateWithFlags(&h->branch[b], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&h->join[b], cudaEventDisableTiming) != cudaSuccess)
-        return bail(SOMA_ECUDA);
-  }
   h->max_ctas_per_sm = move_kernel_max_ctas_per_sm();
+  h->max_ctas_batch = move_batch_max_ctas_per_sm();
   h->ctas_per_sm = o.ctas_per_sm ? std::min<int>(o.ctas_per_sm, h->max_ctas_per_sm) : h->max_ctas_per_sm;
   h->hist_mode = o.hist_mode == SOMA_HIST_AUTO ? SOMA_HIST_FUSED : o.hist_mode;
   h->sort_interval = o.sort_interval < 0 ? kDefaultSortInterval : o.sort_interval;
-  h->acc_per_sys = h->sm_count * h->max_ctas_per_sm;
+  h->acc_per_sys = h->sm_count * std::max(h->max_ctas_per_sm, h->max_ctas_batch);
 
   // --- per-system constants and arrays ---------------------------------
   h->host_sys.resize(n_sys);
@@ -517,7 +578,7 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
     S.z_alt = (float*)dev_alloc(h, nb * 4);
     S.img_alt = (int16_t*)dev_alloc(h, nb * 8);
     S.chain_id_alt = (uint32_t*)dev_alloc(h, np * 4);
-    S.counts = (uint32_t*)dev_alloc(h, nc * 16);
+    S.counts = (uint32_t*)dev_alloc(h, nc * 24);
     S.w = (float*)dev_alloc(h, nc * 8);
     if (!S.x || !S.y || !S.z || !S.img || !S.chain_id || !S.x_alt || !S.y_alt || !S.z_alt || !S.img_alt ||
         !S.chain_id_alt || !S.counts || !S.w)
@@ -529,7 +590,7 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   h->d_acc = (unsigned long long*)dev_alloc(h, sizeof(unsigned long long) * (size_t)h->acc_per_sys * n_sys);
   for (int s = 0; s < n_sys; ++s) h->host_sys[s].acc = h->d_acc;
   h->d_sys = (SysDev*)dev_alloc(h, sizeof(SysDev) * n_sys);
-  h->d_step = (unsigned long long*)dev_alloc(h, 8);
+  h->d_step = (unsigned long long*)dev_alloc(h, 8 * (size_t)n_sys);
   h->d_err = (int*)dev_alloc(h, 4);
   h->d_obs = (double*)dev_alloc(h, 8 * sizeof(double));
   h->d_acc_sum = (unsigned long long*)dev_alloc(h, 8);
@@ -562,9 +623,10 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
       return bail(SOMA_ECUDA);
   }
   if (cudaMemcpy(h->d_sys, h->host_sys.data(), sizeof(SysDev) * n_sys, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(h->d_step, 0, 8) != cudaSuccess || cudaMemset(h->d_err, 0, 4) != cudaSuccess ||
+      cudaMemset(h->d_step, 0, 8 * (size_t)n_sys) != cudaSuccess || cudaMemset(h->d_err, 0, 4) != cudaSuccess ||
       cudaMemset(h->d_acc, 0, sizeof(unsigned long long) * (size_t)h->acc_per_sys * n_sys) != cudaSuccess)
     return bail(SOMA_ECUDA);
+  h->phi_pending.assign(n_sys, 0);
   build_args(h);
 
   // --- initial configuration, start-up checks, counts, fields, sort -----
@@ -595,6 +657,19 @@ int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
   cudaStream_t s = pick(h, stream);
   const bool use_graph = h->opt.graph_steps > 0 && !h->opt.kernel_timing;
   int64_t left = n_steps;
+  bool pending = false;
+  for (char p : h->phi_pending) pending |= p != 0;
+  if (pending) {  // one plain step against the coupling-supplied fields
+    if (h->sort_interval > 0 && h->steps_since_sort >= (uint64_t)h->sort_interval) {
+      if ((rc = enqueue_reorder(h, s))) return rc;
+    }
+    if ((rc = enqueue_steps(h, s, 1, false, (long long)h->step))) return rc;
+    h->dev_synced = false;
+    std::fill(h->phi_pending.begin(), h->phi_pending.end(), 0);
+    h->step += 1;
+    h->steps_since_sort += 1;
+    left -= 1;
+  }
   while (left > 0) {
     if (h->sort_interval > 0 && h->steps_since_sort >= (uint64_t)h->sort_interval) {
       rc = enqueue_reorder(h, s);
@@ -607,13 +682,17 @@ int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
         rc = capture_graph(h, h->opt.graph_steps);
         if (rc) return rc;
       }
+      if (!h->dev_synced) {
+        CK(launch_set_step(h->d_step, h->n_sys, h->step, s));
+        h->dev_synced = true;
+      }
       const int64_t reps = chunk / h->graph_steps;
       for (int64_t r = 0; r < reps; ++r) CK(cudaGraphLaunch(h->graph, s));
       chunk = reps * h->graph_steps;
     } else {
       chunk = std::min<int64_t>(chunk, 1 << 16);
-      if ((rc = enqueue_steps(h, s, 0, (int)chunk))) return rc;
-      CK(launch_advance(h->d_step, chunk, s));
+      if ((rc = enqueue_steps(h, s, (int)chunk, false, (long long)h->step))) return rc;
+      h->dev_synced = false;
     }
     left -= chunk;
     h->step += (uint64_t)chunk;
@@ -637,8 +716,11 @@ int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where
   const SysDev& S = h->host_sys[sys];
   if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
   if ((rc = sync_all(h))) return rc;
-  const uint32_t* src = S.counts + (size_t)((h->step + 1) & 1) * 2 * S.n_c;
-  CK(cudaMemcpy(out, src, sizeof(uint32_t) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  const uint32_t* src = count_buffer(S.counts, S.n_c, (long long)h->step - 1);
+  uint32_t* dst = where == SOMA_DEVICE ? out : reinterpret_cast<uint32_t*>(h->d_stage_phi);
+  CK(launch_deinterleave(src, S.n_c, dst, h->sm_count, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (where != SOMA_DEVICE) CK(cudaMemcpy(out, dst, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
   return SOMA_OK;
 }
 
@@ -649,6 +731,12 @@ int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where) {
   const SysDev& S = h->host_sys[sys];
   if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
   if ((rc = sync_all(h))) return rc;
+  // the move kernel evaluates unheld fields from the counts on the fly: fill
+  // the array from the counts of the current configuration first
+  if (!S.frozen && !h->phi_pending[sys]) {
+    CK(launch_field(h->fargs[sys], fixed_step((long long)h->step - 1), 0, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
   CK(cudaMemcpy(out, S.w, sizeof(float) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
   return SOMA_OK;
 }
@@ -662,6 +750,8 @@ int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int wh
   if ((rc = sync_all(h))) return rc;
   CK(cudaMemcpy(h->d_stage_phi, phi, sizeof(float) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
   CK(launch_field_from_phi(h->d_sys, sys, h->d_stage_phi, h->sm_count, h->stream));
+  h->phi_pending[sys] = 1;
+  drop_graph(h);
   return sync_all(h);
 }
 
@@ -674,12 +764,13 @@ int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int wh
   if (w) {
     if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
     if ((rc = set_frozen(h, sys, 1))) return rc;
+    h->phi_pending[sys] = 0;
     CK(cudaMemcpy(S.w, w, sizeof(float) * n, where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
   } else {
     if ((rc = set_frozen(h, sys, 0))) return rc;
-    // rebuild from the counts of the current configuration (buffer (step-1)&1);
-    // this also clears buffer step&1, which holds nothing yet
-    CK(launch_field(h->fargs[sys], -1, h->stream));
+    h->phi_pending[sys] = 0;
+    // the field array again follows the counts of the current configuration
+    CK(launch_field(h->fargs[sys], fixed_step((long long)h->step - 1), 0, h->stream));
   }
   return sync_all(h);
 }
@@ -723,8 +814,10 @@ int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img
   CK(launch_scatter_state(h->d_sys, sys, h->d_stage_pos, h->d_stage_img, h->sm_count, h->stream));
   h->step = step;
   h->acc_since = step;
-  CK(cudaMemcpyAsync(h->d_step, &step, 8, cudaMemcpyHostToDevice, h->stream));
+  CK(launch_set_step(h->d_step, h->n_sys, step, h->stream));
+  h->dev_synced = true;
   CK(cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * (size_t)h->acc_per_sys * h->n_sys, h->stream));
+  std::fill(h->phi_pending.begin(), h->phi_pending.end(), 0);
   if ((rc = rebin_all(h, h->stream))) return rc;
   return sync_all(h);
 }
@@ -749,7 +842,7 @@ int soma_observables(soma_handle* h, int sys, soma_obs* out) {
   if ((rc = sync_all(h))) return rc;
   CK(cudaMemsetAsync(h->d_obs, 0, 8 * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->d_acc_sum, 0, 8, h->stream));
-  CK(launch_observables(h->d_sys, sys, h->d_step, h->d_obs, h->d_acc_sum, h->sm_count, h->stream));
+  CK(launch_observables(h->d_sys, sys, (long long)h->step, h->d_obs, h->d_acc_sum, h->sm_count, h->stream));
   double r[8];
   unsigned long long acc = 0;
   CK(cudaStreamSynchronize(h->stream));
@@ -848,14 +941,14 @@ int soma_autotune(soma_handle* h) {
   std::vector<std::vector<char>> save(h->n_sys);
   for (int s = 0; s < h->n_sys; ++s) {
     const SysDev& S = h->host_sys[s];
-    save[s].resize((size_t)S.n_b * 20 + (size_t)S.n_poly * 4 + (size_t)S.n_c * 24);
+    save[s].resize((size_t)S.n_b * 20 + (size_t)S.n_poly * 4 + (size_t)S.n_c * 32);
     char* p = save[s].data();
     CK(cudaMemcpy(p, S.x, S.n_b * 4, cudaMemcpyDeviceToHost)); p += S.n_b * 4;
     CK(cudaMemcpy(p, S.y, S.n_b * 4, cudaMemcpyDeviceToHost)); p += S.n_b * 4;
     CK(cudaMemcpy(p, S.z, S.n_b * 4, cudaMemcpyDeviceToHost)); p += S.n_b * 4;
     CK(cudaMemcpy(p, S.img, S.n_b * 8, cudaMemcpyDeviceToHost)); p += S.n_b * 8;
     CK(cudaMemcpy(p, S.chain_id, S.n_poly * 4, cudaMemcpyDeviceToHost)); p += S.n_poly * 4;
-    CK(cudaMemcpy(p, S.counts, S.n_c * 16, cudaMemcpyDeviceToHost)); p += S.n_c * 16;
+    CK(cudaMemcpy(p, S.counts, S.n_c * 24, cudaMemcpyDeviceToHost)); p += S.n_c * 24;
     CK(cudaMemcpy(p, S.w, S.n_c * 8, cudaMemcpyDeviceToHost));
   }
   const size_t acc_n = (size_t)h->acc_per_sys * h->n_sys;
@@ -870,12 +963,11 @@ int soma_autotune(soma_handle* h) {
       CK(cudaMemcpy(S.z, p, S.n_b * 4, cudaMemcpyHostToDevice)); p += S.n_b * 4;
       CK(cudaMemcpy(S.img, p, S.n_b * 8, cudaMemcpyHostToDevice)); p += S.n_b * 8;
       CK(cudaMemcpy(S.chain_id, p, S.n_poly * 4, cudaMemcpyHostToDevice)); p += S.n_poly * 4;
-      CK(cudaMemcpy(S.counts, p, S.n_c * 16, cudaMemcpyHostToDevice)); p += S.n_c * 16;
+      CK(cudaMemcpy(S.counts, p, S.n_c * 24, cudaMemcpyHostToDevice)); p += S.n_c * 24;
       CK(cudaMemcpy(S.w, p, S.n_c * 8, cudaMemcpyHostToDevice));
     }
     CK(cudaMemcpy(h->d_acc, acc_save.data(), 8 * acc_n, cudaMemcpyHostToDevice));
     h->step = step0;
-    CK(cudaMemcpy(h->d_step, &step0, 8, cudaMemcpyHostToDevice));
     return SOMA_OK;
   };
   const int steps = 6;
@@ -891,11 +983,9 @@ int soma_autotune(soma_handle* h) {
     for (int hm = SOMA_HIST_FUSED; hm <= SOMA_HIST_SEPARATE; ++hm) {
       if (h->opt.hist_mode != SOMA_HIST_AUTO && hm != h->opt.hist_mode) continue;
       apply_geometry(h, c, hm);
-      if ((rc = enqueue_steps(h, h->stream, 0, 2))) return rc;  // warm-up
-      CK(launch_advance(h->d_step, 2, h->stream));
+      if ((rc = enqueue_steps(h, h->stream, 2, false, (long long)step0))) return rc;  // warm-up
       CK(cudaEventRecord(a, h->stream));
-      if ((rc = enqueue_steps(h, h->stream, 0, steps))) return rc;
-      CK(launch_advance(h->d_step, steps, h->stream));
+      if ((rc = enqueue_steps(h, h->stream, steps, false, (long long)step0 + 2))) return rc;
       CK(cudaEventRecord(b, h->stream));
       CK(cudaEventSynchronize(b));
       float ms = 0.f;

@@ -35,8 +35,8 @@ __device__ __forceinline__ void load_sys(SysDev* dst, const SysDev* src) {
 }
 
 __device__ __forceinline__ int cell_axis(float x, float cps, int n) {
-  const int i = (int)(x * cps);  // x >= 0, so truncation is floor
-  return min(max(i, 0), n - 1);
+  const int i = (int)(x * cps);  // x >= 0 (and a NaN converts to 0), so truncation is floor
+  return min(i, n - 1);
 }
 
 __device__ __forceinline__ int cell_of(const SysDev& S, float x, float y, float z) {
@@ -119,8 +119,5 @@ __device__ __forceinline__ void apply_wrap(int16_t* img, int64_t bead, int wrap)
   }
 }
 
-__device__ __forceinline__ uint32_t current_step(const unsigned long long* step_base, int offset) {
-  return (uint32_t)(*step_base + (long long)offset);
-}
 
 }  // namespace soma

@@ -30,7 +30,7 @@ struct alignas(16) SysDev {
   float* z_alt;
   int16_t* img_alt;
   uint32_t* chain_id_alt;
-  uint32_t* counts;             // [2 buffers][2 types][n_c]
+  uint32_t* counts;             // [3 buffers][n_c][2 types], see count_buffer()
   float* w;                     // [2 types][n_c]
   unsigned long long* acc;      // accepted moves, one counter per move tile
   int32_t acc_first, acc_count; // this system's range of move tiles
@@ -52,22 +52,58 @@ struct MoveArgs {
   float* z;
   int16_t* img;
   const uint32_t* chain_id;
-  uint32_t* counts;          // [2 buffers][2 types][n_c]
-  const float* w;            // [2 types][n_c]
-  unsigned long long* acc;   // one accepted-move slot per CTA of this system
-  const unsigned long long* step_base;
+  uint32_t* counts;          // [3 buffers][n_c][2 types]
+  const float* w;            // [2 types][n_c], read only when fields are held
+  float inv_rho, chiN_N, kappaN_N;
+  int32_t from_counts;       // batched launches: 1 = fields from counts, 0 = field array
+  unsigned long long* acc;   // accepted-move slots of this system, one per CTA of a launch
   int* err;
+  int64_t pad2;
+};
+
+// Up to kMaxBatch systems stepped by one persistent launch: their constants
+// and the first global tile of each (tile_start[n_sys] = total tiles).
+constexpr int kMaxBatch = 64;
+struct BatchArgs {
+  int32_t n_sys;
+  int32_t tile_start[kMaxBatch + 1];
+  int32_t pad[2];
+  MoveArgs sys[kMaxBatch];
+};
+
+// Which step a launch performs: a number the host fixes (plain launches) or
+// a device counter plus an offset (CUDA-graph replays, where the same nodes
+// run again and again; the graph's last node advances the counter).
+struct StepRef {
+  const unsigned long long* counter;
+  long long fixed;
+  int32_t use_counter;
+  int32_t offset;
+#ifdef __CUDACC__
+  __device__ __forceinline__ long long get() const {
+    return use_counter ? (long long)*counter + offset : fixed;
+  }
+#endif
 };
 
 // The field kernel's view of one system (also by value).
 struct FieldArgs {
-  uint32_t* counts;          // [2 buffers][2 types][n_c]
+  uint32_t* counts;          // [3 buffers][n_c][2 types]
   float* w;                  // [2 types][n_c]
   int64_t n_c;
   float inv_rho, chiN_N, kappaN_N;
   int32_t frozen;
-  const unsigned long long* step_base;
 };
+
+// Count buffers: three per system, each [n_c][2] (the two types of a cell
+// side by side, so one 8-byte load serves a cell).  Step t accumulates buffer
+// t mod 3, takes the previous step's counts (its fields) from (t - 1) mod 3
+// and clears (t + 1) mod 3 for the next step, so the three roles never
+// overlap within a step.  t may be -1 (the configuration before step 0).
+__host__ __device__ inline int count_buffer_index(long long t) { return (int)(((t % 3) + 3) % 3); }
+__host__ __device__ inline uint32_t* count_buffer(uint32_t* base, int64_t n_c, long long t) {
+  return base + (size_t)count_buffer_index(t) * 2 * (size_t)n_c;
+}
 
 // Device error word bits.
 constexpr int kErrBounds = 1;

@@ -4,13 +4,14 @@
 //     the generic move path for chains longer than 64 beads.
 // (b) k_bin: stand-alone density histogram (the density-field update of
 //     Sec. 2.2), used at start-up, after a restore and with the generic path.
-// (c) k_field: per-cell field rebuild from the counts, fused with zeroing of
-//     the count buffer of the next step.
+// (c) k_field: per-cell field array from the counts (the register move kernel
+//     evaluates the same fields from the counts on the fly; this kernel
+//     serves the generic path and requests for the field array).
 // plus initialisation, state gather/scatter, validation, observables and S(q).
 //
 // Layout (per system, see soma_internal.cuh): positions as three FP32 arrays
 // x, y, z [n_b] wrapped into [0, L), bead = slot * N + i; images int16
-// [n_b][4]; counts uint32 [2 buffers][2 types][n_c]; fields FP32 [2][n_c].
+// [n_b][4]; counts uint32 [3 buffers][n_c][2 types]; fields FP32 [2][n_c].
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -26,14 +27,12 @@ namespace soma {
 // other set, so they do not change during this launch).  The histogram runs
 // as the separate kernel k_bin afterwards.
 // ---------------------------------------------------------------------------
-__global__ void k_move_set_generic(const SysDev* __restrict__ systems, int sys,
-                                   const unsigned long long* __restrict__ step_base, int step_offset,
-                                   int set) {
+__global__ void k_move_set_generic(const SysDev* __restrict__ systems, int sys, StepRef r, int set) {
   __shared__ SysDev S;
   __shared__ unsigned int s_acc;
   if (threadIdx.x == 0) s_acc = 0;
   load_sys(&S, systems + sys);
-  const uint32_t t = current_step(step_base, step_offset);
+  const uint32_t t = (uint32_t)r.get();
   const int N = S.N;
   const int per_chain = (N - set + 1) / 2;
   const int64_t total = (int64_t)S.n_poly * per_chain;
@@ -64,28 +63,25 @@ __global__ void k_move_set_generic(const SysDev* __restrict__ systems, int sys,
 }
 
 // ---------------------------------------------------------------------------
-// (b) Stand-alone histogram of the current positions into count buffer t & 1
+// (b) Stand-alone histogram of the current positions into count buffer t mod 3
 // (used at start-up, after a state restore and for chains the register move
 // kernel does not cover).  One thread per bead, one global atomic each.
 // ---------------------------------------------------------------------------
-__global__ void k_bin(const SysDev* __restrict__ systems, int sys,
-                      const unsigned long long* __restrict__ step_base, int step_offset) {
+__global__ void k_bin(const SysDev* __restrict__ systems, int sys, StepRef r) {
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
-  const uint32_t t = current_step(step_base, step_offset);
-  uint32_t* cnt = S.counts + (size_t)(t & 1u) * 2 * S.n_c;
+  uint32_t* cnt = count_buffer(S.counts, S.n_c, r.get());
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(b % S.N);
-    atomicAdd(cnt + (i < S.n_A ? 0 : S.n_c) + cell_of(S, S.x[b], S.y[b], S.z[b]), 1u);
+    atomicAdd(cnt + 2 * cell_of(S, S.x[b], S.y[b], S.z[b]) + (i < S.n_A ? 0 : 1), 1u);
   }
 }
 
 // ---------------------------------------------------------------------------
-// (c) Field rebuild from count buffer t & 1, fused with zeroing of buffer
-// (t + 1) & 1 for the next step:  phi_t = n_t / rho_bar,
+// (c) Field array from count buffer t mod 3:  phi_t = n_t / rho_bar,
 //   w_A = chiN/N phi_B + kappaN/N (phi_A + phi_B - 1), w_B = chiN/N phi_A + ...
-// Held (frozen) fields are not overwritten.  One system per launch, one
-// group of four cells per thread (16-byte loads and stores).
+// optionally clearing buffer t+1 mod 3 for the next step.  Held (frozen)
+// fields are not overwritten.  One system per launch, two cells per thread.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void field_pair(const FieldArgs& f, uint32_t nA, uint32_t nB, float& wA, float& wB) {
   const float pA = (float)nA * f.inv_rho, pB = (float)nB * f.inv_rho;
@@ -94,44 +90,52 @@ __device__ __forceinline__ void field_pair(const FieldArgs& f, uint32_t nA, uint
   wB = fmaf(f.chiN_N, pA, ex);
 }
 
-__global__ void __launch_bounds__(256) k_field(const __grid_constant__ FieldArgs f, int step_offset) {
-  const uint32_t t = (uint32_t)(*f.step_base + (long long)step_offset);
+__global__ void __launch_bounds__(256) k_field(const __grid_constant__ FieldArgs f, StepRef r, int zero_next) {
+  const long long t = r.get();
   const int64_t nc = f.n_c;
-  const uint32_t* __restrict__ cur = f.counts + (size_t)(t & 1u) * 2 * nc;
-  uint32_t* __restrict__ nxt = f.counts + (size_t)((t + 1u) & 1u) * 2 * nc;
+  const uint32_t* __restrict__ cur = count_buffer(f.counts, nc, t);
+  uint32_t* __restrict__ nxt = count_buffer(f.counts, nc, t + 1);
   float* __restrict__ w = f.w;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if ((nc & 3) == 0) {
-    const int64_t n4 = nc >> 2;
+  if ((nc & 1) == 0) {
+    const int64_t n2 = nc >> 1;  // pairs of cells
     const uint4* cur4 = reinterpret_cast<const uint4*>(cur);
     uint4* nxt4 = reinterpret_cast<uint4*>(nxt);
-    float4* w4 = reinterpret_cast<float4*>(w);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
-      const uint4 a = __ldg(cur4 + i);
-      const uint4 b = __ldg(cur4 + n4 + i);
+    float2* wa2 = reinterpret_cast<float2*>(w);
+    float2* wb2 = reinterpret_cast<float2*>(w + nc);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+      const uint4 c = __ldg(cur4 + i);  // (nA, nB) of cells 2i and 2i+1
       if (!f.frozen) {
-        float4 wa, wb;
-        field_pair(f, a.x, b.x, wa.x, wb.x);
-        field_pair(f, a.y, b.y, wa.y, wb.y);
-        field_pair(f, a.z, b.z, wa.z, wb.z);
-        field_pair(f, a.w, b.w, wa.w, wb.w);
-        w4[i] = wa;
-        w4[n4 + i] = wb;
+        float2 wa, wb;
+        field_pair(f, c.x, c.y, wa.x, wb.x);
+        field_pair(f, c.z, c.w, wa.y, wb.y);
+        wa2[i] = wa;
+        wb2[i] = wb;
       }
-      nxt4[i] = make_uint4(0, 0, 0, 0);
-      nxt4[n4 + i] = make_uint4(0, 0, 0, 0);
+      if (zero_next) nxt4[i] = make_uint4(0, 0, 0, 0);
     }
   } else {
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
       if (!f.frozen) {
         float wa, wb;
-        field_pair(f, cur[c], cur[nc + c], wa, wb);
+        field_pair(f, cur[2 * c], cur[2 * c + 1], wa, wb);
         w[c] = wa;
         w[nc + c] = wb;
       }
-      nxt[c] = 0u;
-      nxt[nc + c] = 0u;
+      if (zero_next) {
+        nxt[2 * c] = 0u;
+        nxt[2 * c + 1] = 0u;
+      }
     }
+  }
+}
+
+// Interleaved counts [n_c][2] -> the ABI's [2][n_c].
+__global__ void k_deinterleave(const uint32_t* __restrict__ counts, int64_t nc, uint32_t* __restrict__ out) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 v = reinterpret_cast<const uint2*>(counts)[c];
+    out[c] = v.x;
+    out[nc + c] = v.y;
   }
 }
 
@@ -148,8 +152,13 @@ __global__ void k_field_from_phi(const SysDev* __restrict__ systems, int sys, co
   }
 }
 
-__global__ void k_advance_step(unsigned long long* step_base, long long n) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *step_base += (unsigned long long)n;
+// Step counters of graph replays: advance n_sys counters by n, or set them.
+__global__ void k_advance_step(unsigned long long* counters, int n_sys, long long n) {
+  for (int i = threadIdx.x; i < n_sys; i += blockDim.x) counters[i] += (unsigned long long)n;
+}
+
+__global__ void k_set_step(unsigned long long* counters, int n_sys, unsigned long long value) {
+  for (int i = threadIdx.x; i < n_sys; i += blockDim.x) counters[i] = value;
 }
 
 // ---------------------------------------------------------------------------
@@ -322,18 +331,17 @@ __global__ void k_obs_chains(const SysDev* __restrict__ systems, int sys, double
   }
 }
 
-__global__ void k_obs_cells(const SysDev* __restrict__ systems, int sys, const unsigned long long* __restrict__ step_base,
+__global__ void k_obs_cells(const SysDev* __restrict__ systems, int sys, long long t_done,
                             double* __restrict__ out, unsigned long long* __restrict__ acc_out) {
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
-  // counts of the current configuration sit in buffer (steps_done - 1) & 1
-  const uint32_t t = (uint32_t)(*step_base - 1ull);
-  const uint32_t* cur = S.counts + (size_t)(t & 1u) * 2 * S.n_c;
+  // counts of the current configuration sit in buffer (steps_done - 1) mod 3
+  const uint32_t* cur = count_buffer(S.counts, S.n_c, t_done - 1);
   const double rho = (double)S.n_b / (double)S.n_c;
   const double chiN = (double)S.chiN_N * S.N, kappaN = (double)S.kappaN_N * S.N;
   double f = 0;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_c; c += (int64_t)gridDim.x * blockDim.x) {
-    const double pA = cur[c] / rho, pB = cur[S.n_c + c] / rho, ex = pA + pB - 1.0;
+    const double pA = cur[2 * c] / rho, pB = cur[2 * c + 1] / rho, ex = pA + pB - 1.0;
     f += chiN * pA * pB + 0.5 * kappaN * ex * ex;
   }
   f = warp_sum(f);
@@ -417,35 +425,38 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __res
 // ---------------------------------------------------------------------------
 // Host-side launchers.
 // ---------------------------------------------------------------------------
-cudaError_t launch_move_generic(const SysDev* systems, int sys, int64_t n_poly, int N,
-                                const unsigned long long* step_base, int step_offset, int sm_count,
+cudaError_t launch_move_generic(const SysDev* systems, int sys, int64_t n_poly, int N, StepRef r, int sm_count,
                                 cudaStream_t s) {
   for (int set = 0; set < 2; ++set) {
     const int64_t work = n_poly * ((N - set + 1) / 2);
     int blocks = (int)((work + 255) / 256);
     if (blocks > sm_count * 8) blocks = sm_count * 8;
     if (blocks < 1) blocks = 1;
-    k_move_set_generic<<<blocks, 256, 0, s>>>(systems, sys, step_base, step_offset, set);
+    k_move_set_generic<<<blocks, 256, 0, s>>>(systems, sys, r, set);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin(const SysDev* systems, int sys, int64_t n_b, const unsigned long long* step_base,
-                       int step_offset, int sm_count, cudaStream_t s) {
+cudaError_t launch_bin(const SysDev* systems, int sys, int64_t n_b, StepRef r, int sm_count, cudaStream_t s) {
   const int threads = 512;
   int64_t blocks = (n_b + threads - 1) / threads;
   if (blocks > (int64_t)sm_count * 16) blocks = (int64_t)sm_count * 16;
   if (blocks < 1) blocks = 1;
-  k_bin<<<(unsigned)blocks, threads, 0, s>>>(systems, sys, step_base, step_offset);
+  k_bin<<<(unsigned)blocks, threads, 0, s>>>(systems, sys, r);
   return cudaGetLastError();
 }
 
-cudaError_t launch_field(const FieldArgs& f, int step_offset, cudaStream_t s) {
-  const int64_t groups = (f.n_c & 3) == 0 ? (f.n_c >> 2) : f.n_c;
+cudaError_t launch_field(const FieldArgs& f, StepRef r, int zero_next, cudaStream_t s) {
+  const int64_t groups = (f.n_c & 1) == 0 ? (f.n_c >> 1) : f.n_c;
   int64_t blocks = (groups + 255) / 256;
   if (blocks > 65535) blocks = 65535;
   if (blocks < 1) blocks = 1;
-  k_field<<<(unsigned)blocks, 256, 0, s>>>(f, step_offset);
+  k_field<<<(unsigned)blocks, 256, 0, s>>>(f, r, zero_next);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deinterleave(const uint32_t* counts, int64_t n_c, uint32_t* out, int sm_count, cudaStream_t s) {
+  k_deinterleave<<<sm_count * 8, 256, 0, s>>>(counts, n_c, out);
   return cudaGetLastError();
 }
 
@@ -454,8 +465,13 @@ cudaError_t launch_field_from_phi(const SysDev* systems, int sys, const float* p
   return cudaGetLastError();
 }
 
-cudaError_t launch_advance(unsigned long long* step_base, long long n, cudaStream_t s) {
-  k_advance_step<<<1, 32, 0, s>>>(step_base, n);
+cudaError_t launch_advance(unsigned long long* counters, int n_sys, long long n, cudaStream_t s) {
+  k_advance_step<<<1, 256, 0, s>>>(counters, n_sys, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_step(unsigned long long* counters, int n_sys, unsigned long long value, cudaStream_t s) {
+  k_set_step<<<1, 256, 0, s>>>(counters, n_sys, value);
   return cudaGetLastError();
 }
 
@@ -498,10 +514,10 @@ cudaError_t launch_zero_acc(const SysDev* systems, int sys, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_observables(const SysDev* systems, int sys, const unsigned long long* step_base, double* out,
+cudaError_t launch_observables(const SysDev* systems, int sys, long long t_done, double* out,
                                unsigned long long* acc_out, int sm_count, cudaStream_t s) {
   k_obs_chains<<<sm_count * 4, 256, 0, s>>>(systems, sys, out);
-  k_obs_cells<<<sm_count * 4, 256, 0, s>>>(systems, sys, step_base, out, acc_out);
+  k_obs_cells<<<sm_count * 4, 256, 0, s>>>(systems, sys, t_done, out, acc_out);
   return cudaGetLastError();
 }
 

@@ -9,17 +9,19 @@
 namespace soma {
 
 // Kernel (a) with fused (b), soma_move.cu.
-cudaError_t launch_move(const MoveArgs& a, int grid, int step_offset, cudaStream_t s);
+cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s);
+cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStream_t s);
+int move_batch_max_ctas_per_sm();
 int move_kernel_max_ctas_per_sm();
 int move_kernel_chains_per_tile(int P);
-cudaError_t launch_move_generic(const SysDev* systems, int sys, int64_t n_poly, int N,
-                                const unsigned long long* step_base, int step_offset, int sm_count,
+cudaError_t launch_move_generic(const SysDev* systems, int sys, int64_t n_poly, int N, StepRef r, int sm_count,
                                 cudaStream_t s);
-cudaError_t launch_bin(const SysDev* systems, int sys, int64_t n_b, const unsigned long long* step_base,
-                       int step_offset, int sm_count, cudaStream_t s);
-cudaError_t launch_field(const FieldArgs& f, int step_offset, cudaStream_t s);
+cudaError_t launch_bin(const SysDev* systems, int sys, int64_t n_b, StepRef r, int sm_count, cudaStream_t s);
+cudaError_t launch_field(const FieldArgs& f, StepRef r, int zero_next, cudaStream_t s);
+cudaError_t launch_deinterleave(const uint32_t* counts, int64_t n_c, uint32_t* out, int sm_count, cudaStream_t s);
 cudaError_t launch_field_from_phi(const SysDev* systems, int sys, const float* phi, int sm_count, cudaStream_t s);
-cudaError_t launch_advance(unsigned long long* step_base, long long n, cudaStream_t s);
+cudaError_t launch_advance(unsigned long long* counters, int n_sys, long long n, cudaStream_t s);
+cudaError_t launch_set_step(unsigned long long* counters, int n_sys, unsigned long long value, cudaStream_t s);
 cudaError_t launch_init(const SysDev* systems, int sys, int64_t n_poly, cudaStream_t s);
 cudaError_t launch_gather_state(const SysDev* systems, int sys, float* pos, int16_t* img, int sm_count,
                                 cudaStream_t s);
@@ -30,7 +32,7 @@ cudaError_t launch_validate_pos(const float* pos, int64_t n, const float* L, int
                                 cudaStream_t s);
 cudaError_t launch_sum_acc(const SysDev* systems, int sys, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_zero_acc(const SysDev* systems, int sys, cudaStream_t s);
-cudaError_t launch_observables(const SysDev* systems, int sys, const unsigned long long* step_base, double* out,
+cudaError_t launch_observables(const SysDev* systems, int sys, long long t_done, double* out,
                                unsigned long long* acc_out, int sm_count, cudaStream_t s);
 cudaError_t launch_structure_factor(const SysDev* systems, int sys, int nq, const int32_t* m, double* out,
                                     int sm_count, cudaStream_t s);

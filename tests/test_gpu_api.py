@@ -77,8 +77,9 @@ def test_info_and_kernel_timing():
         assert info["k_b"] == 46.5 and abs(info["A"] - 0.5 / np.sqrt(31)) < 1e-7
         h.mc_steps(10)
         t = h.kernel_times()
-        assert t["move"][1] == 10 and t["field"][1] == 10 and t["reorder"][1] == 2
-        assert t["move"][0] > 0 and t["field"][0] > 0
+        # one kernel per step: the fields come from the counts inside the move kernel
+        assert t["move"][1] == 10 and t["field"][1] == 0 and t["reorder"][1] == 2
+        assert t["move"][0] > 0
 
 
 def test_many_handles_and_destroy():
