@@ -23,7 +23,6 @@ import json
 import os
 import re
 import statistics
-import subprocess
 import sys
 import time
 
@@ -74,53 +73,83 @@ def _profiled_traffic(workload):
     return float(t.group(1))
 
 
+class _Nvml:
+    """Minimal ctypes binding of the NVML calls used for clock sampling
+    (libnvidia-ml ships with the driver; the pynvml module may be absent)."""
+
+    def __init__(self, index):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("nvmlDeviceGetHandleByIndex failed")
+        reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = reasons or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sm_clock(self, max_clock=False):
+        v = self.ct.c_uint()
+        fn = self.lib.nvmlDeviceGetMaxClockInfo if max_clock else self.lib.nvmlDeviceGetClockInfo
+        if fn(self.h, self.ct.c_int(1), self.ct.byref(v)) != 0:  # NVML_CLOCK_SM = 1
+            raise RuntimeError("clock query failed")
+        return v.value
+
+    def reasons(self):
+        v = self.ct.c_ulonglong()
+        if self.reasons_fn(self.h, self.ct.byref(v)) != 0:
+            raise RuntimeError("reason query failed")
+        return v.value
+
+
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clock and clock-event (throttle) reasons sampled during the timed
+    region: NVML polled every millisecond from a thread (the timed region of
+    a default run lasts a few milliseconds)."""
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
 
     def __init__(self, index):
         self.index = index
-        self.proc = None
+        self.sm, self.reasons, self.max_mhz, self.error = [], set(), None, None
+
+    def _poll(self):
+        while not self._stop.is_set():
+            try:
+                self.sm.append(self._nvml.sm_clock())
+                bits = self._nvml.reasons()
+                for name, bit in self.REASONS:
+                    if bits & bit:
+                        self.reasons.add(name)
+            except Exception as e:  # keep sampling; report the last error
+                self.error = repr(e)
+            self._stop.wait(0.001)
 
     def __enter__(self):
+        import threading
+        self._stop = threading.Event()
+        self._thread = None
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except Exception:
-            self.proc = None
+            self._nvml = _Nvml(self.index)
+            self.max_mhz = self._nvml.sm_clock(max_clock=True)
+            self._thread = threading.Thread(target=self._poll, daemon=True)
+            self._thread.start()
+        except Exception as e:
+            self.error = repr(e)
         return self
 
     def __exit__(self, *a):
-        self.lines = []
-        if self.proc:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except Exception:
-                self.proc.kill()
-                out = ""
-            self.lines = [l for l in out.splitlines() if l.strip()]
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join(2)
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
-            f = [x.strip() for x in l.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(self.sm) if self.sm else None, "sm_max_mhz": self.max_mhz,
+               "reasons": sorted(self.reasons), "samples": len(self.sm), "source": "NVML, 1 ms polling"}
+        if self.error and not self.sm:
+            out["error"] = self.error
+        return out
 
 
 def rank_system_kwargs(workload, rank):
@@ -276,14 +305,14 @@ def run_gpu(args):
 
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    h = soma.Handle(system, device=local, kernel_timing=1, graph_steps=0)
+    h = soma.Handle(system, device=local, kernel_timing=1, graph_steps=0, autotune=1)
     sort_interval = h.info()["sort_interval"]
     sptr = stream.cuda_stream
 
     def one_step():
         h.mc_steps(1, stream=sptr)
 
-    # warm-up
+    # warm-up (the first call runs the autotuner, which restores the state it tried on)
     for _ in range(args.warmup):
         one_step()
     torch.cuda.synchronize()
@@ -307,11 +336,12 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     kt = h.kernel_times(reset=True)
+    info_after = h.info()
     total_ms, moves, value = aggregate(total_ms, args.steps * n_b, pg, device="cuda")
     sorts = kt["reorder"][1]
-    # per step: the move kernel and the step-counter advance; 3 own kernels per reorder
-    launches = args.steps * (kt["move"][1] // max(1, args.steps) + kt["bin"][1] // max(1, args.steps)
-                             + kt["field"][1] // max(1, args.steps) + 1) + sorts * 3
+    # the library's own kernels in the timed region: move (+ bin / field where
+    # used) per step, and three per chain reorder (keys, permute, copy back)
+    launches = kt["move"][1] + kt["bin"][1] + kt["field"][1] + sorts * 3
 
     # dominant kernel: the move kernel (its average launch duration)
     mv_ms, mv_n = kt["move"]
@@ -382,6 +412,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, c), "n_beads": n_b, "n_cells": n_c,
                        "l2": "flushed between timed steps (256 MiB write)", "sort_interval": sort_interval,
+                       "tuned": {k: info_after[k] for k in ("ctas_per_sm", "hist_mode")},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "steady_state": steady, "batched": batched,

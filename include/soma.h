@@ -119,6 +119,8 @@ typedef struct soma_info {
   int32_t ctas_per_sm;     /* move-kernel CTAs per SM in use */
   int32_t sort_interval;   /* reorder interval in use */
   int32_t hist_mode;       /* histogram strategy in use */
+  int32_t reserved;
+  int32_t reserved2;
 } soma_info;
 
 typedef struct soma_handle soma_handle;

@@ -426,7 +426,7 @@ int set_frozen(soma_handle* h, int sys, int frozen) {
 }
 
 void apply_geometry(soma_handle* h, int ctas_per_sm, int hist_mode) {
-  h->ctas_per_sm = std::max(1, std::min(ctas_per_sm, h->max_ctas_per_sm));
+  h->ctas_per_sm = std::max(1, std::min(ctas_per_sm, std::max(h->max_ctas_per_sm, h->max_ctas_batch)));
   h->hist_mode = hist_mode;
   build_args(h);
   drop_graph(h);
@@ -901,6 +901,7 @@ int soma_get_info(soma_handle* h, int sys, soma_info* out) {
   out->ctas_per_sm = h->ctas_per_sm;
   out->sort_interval = h->sort_interval;
   out->hist_mode = h->hist_mode;
+  out->reserved = 0;
   return SOMA_OK;
 }
 
@@ -978,7 +979,8 @@ int soma_autotune(soma_handle* h) {
   CK(cudaEventCreate(&b));
   const int timing = h->opt.kernel_timing;
   h->opt.kernel_timing = 0;
-  for (int c = 1; c <= h->max_ctas_per_sm; ++c) {
+  const int max_c = h->n_sys > 1 ? h->max_ctas_batch : h->max_ctas_per_sm;
+  for (int c = 1; c <= max_c; ++c) {
     if (h->opt.ctas_per_sm && c != h->opt.ctas_per_sm) continue;
     for (int hm = SOMA_HIST_FUSED; hm <= SOMA_HIST_SEPARATE; ++hm) {
       if (h->opt.hist_mode != SOMA_HIST_AUTO && hm != h->opt.hist_mode) continue;

@@ -103,6 +103,27 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 __device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
 
+// Stage reads as volatile shared loads: each is performed exactly once, in
+// program order before the warp releases the stage to the producer.  (A
+// plain load may legally be re-executed later by the compiler to save a
+// register, and after the release the stage may already hold the next tile,
+// written by the copy engine outside the compiler's view.)
+__device__ __forceinline__ float2 lds2(const float* p) {
+  float2 v;
+  asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ float lds1(const float* p) {
+  float v;
+  asm volatile("ld.volatile.shared.f32 %0, [%1];" : "=f"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t lds1(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ int cell_idx(const MoveArgs& a, float x, float y, float z) {
   return (cell_axis(x, a.cps[0], a.n[0]) * a.n[1] + cell_axis(y, a.cps[1], a.n[1])) * a.n[2] +
          cell_axis(z, a.cps[2], a.n[2]);
@@ -142,16 +163,16 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   float xe = 0.f, ye = 0.f, ze = 0.f, xo = 0.f, yo = 0.f, zo = 0.f;
   if ((N & 1) == 0) {
     if (he) {
-      const float2 vx = *reinterpret_cast<const float2*>(st.x + lb);
-      const float2 vy = *reinterpret_cast<const float2*>(st.y + lb);
-      const float2 vz = *reinterpret_cast<const float2*>(st.z + lb);
+      const float2 vx = lds2(st.x + lb);
+      const float2 vy = lds2(st.y + lb);
+      const float2 vz = lds2(st.z + lb);
       xe = vx.x; xo = vx.y; ye = vy.x; yo = vy.y; ze = vz.x; zo = vz.y;
     }
   } else {
-    if (he) { xe = st.x[lb]; ye = st.y[lb]; ze = st.z[lb]; }
-    if (ho) { xo = st.x[lb + 1]; yo = st.y[lb + 1]; zo = st.z[lb + 1]; }
+    if (he) { xe = lds1(st.x + lb); ye = lds1(st.y + lb); ze = lds1(st.z + lb); }
+    if (ho) { xo = lds1(st.x + lb + 1); yo = lds1(st.y + lb + 1); zo = lds1(st.z + lb + 1); }
   }
-  const uint32_t cid = chain_ok ? st.cid[chain_in_tile] : 0u;
+  const uint32_t cid = chain_ok ? lds1(st.cid + chain_in_tile) : 0u;
   __syncwarp();
   if (lane == 0) mbar_arrive(empty);  // this warp is done with the stage
 
@@ -286,8 +307,9 @@ __device__ __forceinline__ void drain(uint64_t* full, int issued, int* err) {
     if (!mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u, err)) break;
 }
 
+// Register budget for 3 resident CTAs per SM (72 registers, no spill).
 template <bool kFromCounts>
-__global__ void __launch_bounds__((kConsumerWarps + 1) * 32) k_move(const __grid_constant__ MoveArgs a, StepRef r) {
+__global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __grid_constant__ MoveArgs a, StepRef r) {
   __shared__ MoveStage stage[kStages];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
@@ -379,7 +401,8 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
 // one another).
 int move_kernel_max_ctas_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<true>, (kConsumerWarps + 1) * 32, 0) != cudaSuccess) {
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<true>, (kConsumerWarps + 1) * 32, 0);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -389,10 +412,11 @@ int move_kernel_max_ctas_per_sm() {
 int move_kernel_chains_per_tile(int P) { return kConsumerWarps * (32 / P); }
 
 cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s) {
+  const int threads = (kConsumerWarps + 1) * 32;
   if (from_counts)
-    k_move<true><<<grid, (kConsumerWarps + 1) * 32, 0, s>>>(a, r);
+    k_move<true><<<grid, threads, 0, s>>>(a, r);
   else
-    k_move<false><<<grid, (kConsumerWarps + 1) * 32, 0, s>>>(a, r);
+    k_move<false><<<grid, threads, 0, s>>>(a, r);
   return cudaGetLastError();
 }
 

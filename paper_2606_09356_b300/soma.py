@@ -81,6 +81,7 @@ class soma_info(ctypes.Structure):
         ("n_beads", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("k_b", ctypes.c_double),
         ("A", ctypes.c_double), ("rho_bar", ctypes.c_double), ("lanes_per_chain", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32), ("sort_interval", ctypes.c_int32), ("hist_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 

@@ -35,7 +35,7 @@ def _same(a, b):
 def test_launch_shape_histogram_graph_and_reorder_invariance():
     s = soma.System(**SMALL)
     ref = _run(s, 40, ctas_per_sm=2, hist_mode=soma.SOMA_HIST_FUSED, graph_steps=0, sort_interval=0)
-    for opts in (dict(ctas_per_sm=1), dict(ctas_per_sm=0), dict(hist_mode=soma.SOMA_HIST_SEPARATE),
+    for opts in (dict(ctas_per_sm=1), dict(ctas_per_sm=0), dict(ctas_per_sm=2), dict(hist_mode=soma.SOMA_HIST_SEPARATE),
                  dict(graph_steps=16), dict(graph_steps=7, sort_interval=5), dict(sort_interval=1),
                  dict(autotune=1)):
         _same(ref, _run(s, 40, **{**dict(graph_steps=0, sort_interval=0), **opts}))

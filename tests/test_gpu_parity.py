@@ -72,7 +72,7 @@ def test_step_parity_config0_ten_steps():
     dict(n_poly=1, N=2, n_A=1, box=(12.0, 12.0, 12.0), grid=(3, 3, 3), chiN=5.0, kappaN=5.0),       # a single dimer
     dict(n_poly=200, N=1, n_A=1, box=(2.0, 2.0, 2.0), grid=(4, 4, 4), chiN=5.0, kappaN=10.0, A=0.3),  # monomers
 ])
-@pytest.mark.parametrize("ctas", [1, 2])
+@pytest.mark.parametrize("ctas", [1, 3])
 def test_step_parity_shapes(kw, ctas):
     sysm = soma.System(seed=7, **kw)
     with soma.Handle(sysm, ctas_per_sm=ctas, graph_steps=0) as h:
