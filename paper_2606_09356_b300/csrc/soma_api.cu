@@ -200,6 +200,7 @@ void build_args(soma_handle* h) {
       a.L[i] = S.L[i];
       a.invL[i] = S.invL[i];
       a.cps[i] = S.cps[i];
+      a.Lm[i] = std::nextafter(S.L[i], 0.0f);
     }
     a.n[0] = S.nx;
     a.n[1] = S.ny;

@@ -41,6 +41,8 @@ struct alignas(16) SysDev {
 // __grid_constant__ kernel parameter (constant bank: no loads in the loop).
 struct MoveArgs {
   float L[3], invL[3], cps[3];
+  float Lm[3];               // largest float below L
+  float pad0;
   int32_t n[3];
   float A, kb;
   uint32_t rk[10][2];        // Philox round keys

@@ -44,6 +44,9 @@ constexpr int kTileChains = kConsumerWarps * 32;  // at most 32 chains per warp 
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz: a wait that long is an error
 constexpr float kLog2e = 1.4426950408889634f;
 
+// A batch rides in the kernel's parameter space (at most 32,764 bytes).
+static_assert(sizeof(BatchArgs) <= 32000, "BatchArgs exceeds the kernel parameter limit");
+
 struct __align__(128) MoveStage {
   float x[kTileBeads];
   float y[kTileBeads];
@@ -124,6 +127,30 @@ __device__ __forceinline__ uint32_t lds1(const uint32_t* p) {
   return v;
 }
 
+// Periodic wrap of a proposed coordinate p in (-L, 2L) into [0, L): the
+// image step fl in {-1, 0, 1}, then p - fl L, kept strictly below L (p just
+// below 0 would round to L; the largest float below L, Lm, is the same
+// point to within rounding and lies in the last cell, as the exact wrap
+// does).  For fl = 1 the subtraction is exact.
+__device__ __forceinline__ float wrap_step(float p, float L, float Lm, float& fl) {
+  fl = p >= L ? 1.f : (p < 0.f ? -1.f : 0.f);
+  return fminf(fmaf(-L, fl, p), Lm);
+}
+
+// Image steps of the three axes packed as fx + 3 fy + 9 fz (balanced
+// ternary: zero only when nothing wrapped), applied in the rare case.
+__device__ __forceinline__ void apply_image_steps(int16_t* img, int64_t bead, float code) {
+  if (code != 0.f) {
+    const int c = __float2int_rn(code) + 13;  // 0 .. 26, digits fx+1, fy+1, fz+1
+    short4* p = reinterpret_cast<short4*>(img) + bead;
+    short4 v = *p;
+    v.x += (short)(c % 3 - 1);
+    v.y += (short)((c / 3) % 3 - 1);
+    v.z += (short)(c / 9 - 1);
+    *p = v;
+  }
+}
+
 __device__ __forceinline__ int cell_idx(const MoveArgs& a, float x, float y, float z) {
   return (cell_axis(x, a.cps[0], a.n[0]) * a.n[1] + cell_axis(y, a.cps[1], a.n[1])) * a.n[2] +
          cell_axis(z, a.cps[2], a.n[2]);
@@ -188,15 +215,15 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   const float dox = fmaf((float)(ro.x >> 8), A23, -a.A);
   const float doy = fmaf((float)(ro.y >> 8), A23, -a.A);
   const float doz = fmaf((float)(ro.z >> 8), A23, -a.A);
-  int wx, wy, wz;
-  const float pex = wrap_coord(xe + dex, a.L[0], wx);
-  const float pey = wrap_coord(ye + dey, a.L[1], wy);
-  const float pez = wrap_coord(ze + dez, a.L[2], wz);
-  const int wrap_e = (wx + 1) | ((wy + 1) << 2) | ((wz + 1) << 4);
-  const float pox = wrap_coord(xo + dox, a.L[0], wx);
-  const float poy = wrap_coord(yo + doy, a.L[1], wy);
-  const float poz = wrap_coord(zo + doz, a.L[2], wz);
-  const int wrap_o = (wx + 1) | ((wy + 1) << 2) | ((wz + 1) << 4);
+  float fx, fy, fz;
+  const float pex = wrap_step(xe + dex, a.L[0], a.Lm[0], fx);
+  const float pey = wrap_step(ye + dey, a.L[1], a.Lm[1], fy);
+  const float pez = wrap_step(ze + dez, a.L[2], a.Lm[2], fz);
+  const float wrap_e = fmaf(9.f, fz, fmaf(3.f, fy, fx));
+  const float pox = wrap_step(xo + dox, a.L[0], a.Lm[0], fx);
+  const float poy = wrap_step(yo + doy, a.L[1], a.Lm[1], fy);
+  const float poz = wrap_step(zo + doz, a.L[2], a.Lm[2], fz);
+  const float wrap_o = fmaf(9.f, fz, fmaf(3.f, fy, fx));
   const int ce0 = cell_idx(a, xe, ye, ze), ce1 = cell_idx(a, pex, pey, pez);
   const int co0 = cell_idx(a, xo, yo, zo), co1 = cell_idx(a, pox, poy, poz);
   float fe, fo;
@@ -271,8 +298,8 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
     if (acc) { a.x[gb] = xe; a.y[gb] = ye; a.z[gb] = ze; }
     if (acco) { a.x[gb + 1] = xo; a.y[gb + 1] = yo; a.z[gb + 1] = zo; }
   }
-  if (acc && wrap_e != 21) apply_wrap(a.img, gb, wrap_e);
-  if (acco && wrap_o != 21) apply_wrap(a.img, gb + 1, wrap_o);
+  if (acc) apply_image_steps(a.img, gb, wrap_e);
+  if (acco) apply_image_steps(a.img, gb + 1, wrap_o);
   if (a.bin) {
     uint32_t* __restrict__ cnt = count_buffer(a.counts, a.n_c, tl);
     if (he) atomicAdd(cnt + 2 * (acc ? ce1 : ce0) + te, 1u);

@@ -82,3 +82,19 @@ def test_reorder_keeps_logical_state():
         h.reorder()
         b = h.get_state()
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_persistent_grid_invariance_full_size():
+    """config1 at full size: with 1, 2 and 3 resident CTAs per SM every CTA
+    cycles its stage ring many times per step; the trajectory must not
+    depend on how the tiles are spread over the persistent CTAs."""
+    s = soma.System(**workloads.system_kwargs("config1"))
+    ref = None
+    for c in (3, 1, 2):
+        with soma.Handle(s, ctas_per_sm=c, graph_steps=0, sort_interval=0) as h:
+            h.mc_steps(6)
+            st = (h.get_state()[0], h.get_density(), h.accepted())
+        if ref is None:
+            ref = st
+        else:
+            _same(ref, st)
