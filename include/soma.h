@@ -60,6 +60,11 @@ extern "C" {
 #define SOMA_HOST 0
 #define SOMA_DEVICE 1
 
+/* Position precision of a handle (soma_options.precision). */
+#define SOMA_PREC_FP32 0  /* FP32 wrapped positions + int16 images: the throughput path */
+#define SOMA_PREC_FP64 1  /* FP64 wrapped positions + int16 images: a precision reference
+                             (one system per handle, no chain reorder, no autotuning) */
+
 /* Histogram strategies of kernel (b) (soma_options.hist_mode). */
 #define SOMA_HIST_AUTO 0
 #define SOMA_HIST_FUSED 1     /* binned in the epilogue of the move kernel */
@@ -93,7 +98,7 @@ typedef struct soma_options {
   int32_t graph_steps;   /* steps per captured CUDA graph; 0 = plain launches */
   int32_t kernel_timing; /* 1 = record CUDA events around each kernel (plain launches) */
   int32_t autotune;      /* 1 = time candidate shapes on the first soma_mc_steps */
-  int32_t reserved;
+  int32_t precision;     /* SOMA_PREC_FP32 or SOMA_PREC_FP64 */
   soma_alloc_fn alloc;   /* optional device allocator, with free and ctx */
   soma_free_fn free;
   void* alloc_ctx;
@@ -172,6 +177,12 @@ int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* 
  * counters and re-bins; the step counter is shared by all systems. */
 int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img, uint64_t step,
                    int where);
+
+/* The same for handles created with SOMA_PREC_FP64: positions FP64 [n][3].
+ * (soma_get_state / soma_set_state return SOMA_ENOTSUP on such handles.) */
+int soma_get_state64(soma_handle* h, int sys, double* pos, int16_t* img, uint64_t* step, int where);
+int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* img, uint64_t step,
+                     int where);
 
 /* FP64 observables of the current configuration. */
 int soma_observables(soma_handle* h, int sys, soma_obs* out);

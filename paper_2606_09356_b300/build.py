@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsoma.so")
-SOURCES = ["soma_move.cu", "soma_kernels.cu", "soma_sort.cu", "soma_api.cu", "soma_noalloc.cu"]
+SOURCES = ["soma_move.cu", "soma_kernels.cu", "soma_f64.cu", "soma_sort.cu", "soma_api.cu", "soma_noalloc.cu"]
 HEADERS = ["soma_internal.cuh", "soma_launch.h", "soma_device.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -89,6 +89,8 @@ struct soma_handle {
   double ms[4] = {0, 0, 0, 0};
   int64_t launches[4] = {0, 0, 0, 0};
   bool tuned = false;
+  bool f64 = false;  // SOMA_PREC_FP64 handle
+  double* d_stage_pos64 = nullptr;
   int sticky = SOMA_OK;
 };
 
@@ -347,6 +349,11 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
       }
       for (int sys = 0; sys < h->n_sys; ++sys)
         if ((rc = enqueue_aux(h, s, sys, step_ref(h, sys, graph, t0, i), timing, false))) return rc;
+    } else if (h->f64) {
+      TimedEvent te;
+      if (timing) begin_timed(h, s, te, T_MOVE);
+      CK(launch_move64(h->d_sys, 0, step_ref(h, 0, graph, t0, i), h->sm_count, s));
+      if (timing) end_timed(h, s, te);
     } else {
       const SysDev& S = h->host_sys[0];
       const StepRef r = step_ref(h, 0, graph, t0, i);
@@ -398,7 +405,10 @@ int rebin_all(soma_handle* h, cudaStream_t s) {
   for (int g = 0; g < h->n_sys; ++g) {
     SysDev& S = h->host_sys[g];
     CK(cudaMemsetAsync(S.counts, 0, sizeof(uint32_t) * 6 * S.n_c, s));
-    CK(launch_bin(h->d_sys, g, S.n_b, fixed_step((long long)h->step - 1), h->sm_count, s));
+    if (h->f64)
+      CK(launch_bin64(h->d_sys, g, (long long)h->step - 1, h->sm_count, s));
+    else
+      CK(launch_bin(h->d_sys, g, S.n_b, fixed_step((long long)h->step - 1), h->sm_count, s));
     CK(launch_field(h->fargs[g], fixed_step((long long)h->step - 1), 0, s));
   }
   return SOMA_OK;
@@ -492,6 +502,12 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   else
     soma_options_default(&o);
   if (o.ctas_per_sm < 0 || o.ctas_per_sm > 64) return SOMA_EINVAL;
+  if (o.precision != SOMA_PREC_FP32 && o.precision != SOMA_PREC_FP64) return SOMA_EINVAL;
+  if (o.precision == SOMA_PREC_FP64) {
+    if (n_sys != 1) return SOMA_EINVAL;  // the FP64 form steps one system per handle
+    for (int s = 0; s < n_sys; ++s)
+      if (sys[s].N > 64) return SOMA_ENOTSUP;
+  }
   if (o.hist_mode < SOMA_HIST_AUTO || o.hist_mode > SOMA_HIST_SEPARATE) return SOMA_EINVAL;
   if (o.graph_steps < 0 || o.graph_steps > 4096) return SOMA_EINVAL;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SOMA_EINVAL;
@@ -524,6 +540,8 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   h->ctas_per_sm = o.ctas_per_sm ? std::min<int>(o.ctas_per_sm, h->max_ctas_per_sm) : h->max_ctas_per_sm;
   h->hist_mode = o.hist_mode == SOMA_HIST_AUTO ? SOMA_HIST_FUSED : o.hist_mode;
   h->sort_interval = o.sort_interval < 0 ? kDefaultSortInterval : o.sort_interval;
+  h->f64 = o.precision == SOMA_PREC_FP64;
+  if (h->f64) h->sort_interval = 0;  // the precision reference keeps its storage order
   h->acc_per_sys = h->sm_count * std::max(h->max_ctas_per_sm, h->max_ctas_batch);
 
   // --- per-system constants and arrays ---------------------------------
@@ -560,6 +578,17 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
+    for (int a = 0; a < 3; ++a) {
+      S.L64[a] = d.box[a];
+      S.invL64[a] = 1.0 / d.box[a];
+      S.cps64[a] = (double)d.grid[a] / d.box[a];
+    }
+    // field differences of the FP64 form: (chiN dn_other + kappaN dn_total) / (N rho_bar)
+    {
+      const double rho = (double)S.n_b / (double)S.n_c;
+      S.chiN64 = d.chiN / d.N / rho;
+      S.kappaN64 = d.kappaN / d.N / rho;
+    }
     S.chain_base = chain_base;
     chain_base += d.n_poly;
     S.acc_first = s * h->acc_per_sys;
@@ -584,6 +613,12 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
     if (!S.x || !S.y || !S.z || !S.img || !S.chain_id || !S.x_alt || !S.y_alt || !S.z_alt || !S.img_alt ||
         !S.chain_id_alt || !S.counts || !S.w)
       return bail(SOMA_ENOMEM);
+    if (h->f64) {
+      S.x64 = (double*)dev_alloc(h, nb * 8);
+      S.y64 = (double*)dev_alloc(h, nb * 8);
+      S.z64 = (double*)dev_alloc(h, nb * 8);
+      if (!S.x64 || !S.y64 || !S.z64) return bail(SOMA_ENOMEM);
+    }
     if (cudaMemset(S.x, 0, nb * 4) != cudaSuccess || cudaMemset(S.y, 0, nb * 4) != cudaSuccess ||
         cudaMemset(S.z, 0, nb * 4) != cudaSuccess || cudaMemset(S.chain_id, 0, np * 4) != cudaSuccess)
       return bail(SOMA_ECUDA);
@@ -598,6 +633,10 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   h->d_stage_pos = (float*)dev_alloc(h, (size_t)h->max_nb * 12);
   h->d_stage_img = (int16_t*)dev_alloc(h, (size_t)h->max_nb * 6);
   h->d_stage_phi = (float*)dev_alloc(h, (size_t)h->max_nc * 8);
+  if (h->f64) {
+    h->d_stage_pos64 = (double*)dev_alloc(h, (size_t)h->max_nb * 24);
+    if (!h->d_stage_pos64) return bail(SOMA_ENOMEM);
+  }
   if (!h->d_acc || !h->d_sys || !h->d_step || !h->d_err || !h->d_obs || !h->d_acc_sum || !h->d_stage_pos ||
       !h->d_stage_img || !h->d_stage_phi)
     return bail(SOMA_ENOMEM);
@@ -632,15 +671,20 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
 
   // --- initial configuration, start-up checks, counts, fields, sort -----
   for (int s = 0; s < n_sys && rc == SOMA_OK; ++s) {
-    if (launch_init(h->d_sys, s, h->host_sys[s].n_poly, h->stream) != cudaSuccess) rc = SOMA_ECUDA;
-    else if (launch_validate(h->d_sys, s, h->d_err, h->sm_count, h->stream) != cudaSuccess) rc = SOMA_ECUDA;
+    if (h->f64) {
+      if (launch_init64(h->d_sys, s, h->host_sys[s].n_poly, h->stream) != cudaSuccess) rc = SOMA_ECUDA;
+    } else if (launch_init(h->d_sys, s, h->host_sys[s].n_poly, h->stream) != cudaSuccess) {
+      rc = SOMA_ECUDA;
+    } else if (launch_validate(h->d_sys, s, h->d_err, h->sm_count, h->stream) != cudaSuccess) {
+      rc = SOMA_ECUDA;
+    }
   }
   if (rc == SOMA_OK) rc = rebin_all(h, h->stream);
   if (rc == SOMA_OK && h->sort_interval != 0) rc = enqueue_reorder(h, h->stream);
   if (rc == SOMA_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = SOMA_ECUDA;
   if (rc == SOMA_OK) rc = check_device_error(h);
   if (rc != SOMA_OK) return bail(rc);
-  h->tuned = !o.autotune;
+  h->tuned = !o.autotune || h->f64;
   *out = h;
   return SOMA_OK;
 }
@@ -745,6 +789,7 @@ int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where) {
 int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int where) {
   int rc = check_live(h);
   if (rc) return rc;
+  if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys || !phi) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
@@ -759,6 +804,7 @@ int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int wh
 int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int where) {
   int rc = check_live(h);
   if (rc) return rc;
+  if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if ((rc = sync_all(h))) return rc;
@@ -779,6 +825,7 @@ int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int wh
 int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* step, int where) {
   int rc = check_live(h);
   if (rc) return rc;
+  if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if ((rc = sync_all(h))) return rc;
@@ -796,6 +843,7 @@ int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* 
 int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img, uint64_t step, int where) {
   int rc = check_live(h);
   if (rc) return rc;
+  if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys || !pos || !img) return SOMA_EINVAL;
   if (step >= (uint64_t)kInitStep) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
@@ -813,6 +861,55 @@ int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img
     return SOMA_EINVAL;  // a position outside [0, L): rejected, the state is untouched
   }
   CK(launch_scatter_state(h->d_sys, sys, h->d_stage_pos, h->d_stage_img, h->sm_count, h->stream));
+  h->step = step;
+  h->acc_since = step;
+  CK(launch_set_step(h->d_step, h->n_sys, step, h->stream));
+  h->dev_synced = true;
+  CK(cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * (size_t)h->acc_per_sys * h->n_sys, h->stream));
+  std::fill(h->phi_pending.begin(), h->phi_pending.end(), 0);
+  if ((rc = rebin_all(h, h->stream))) return rc;
+  return sync_all(h);
+}
+
+int soma_get_state64(soma_handle* h, int sys, double* pos, int16_t* img, uint64_t* step, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (!h->f64) return SOMA_ENOTSUP;
+  if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if ((rc = sync_all(h))) return rc;
+  if (pos || img) {
+    CK(launch_gather_state64(h->d_sys, sys, h->d_stage_pos64, h->d_stage_img, h->sm_count, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const cudaMemcpyKind k = where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (pos) CK(cudaMemcpy(pos, h->d_stage_pos64, (size_t)S.n_b * 24, k));
+    if (img) CK(cudaMemcpy(img, h->d_stage_img, (size_t)S.n_b * 6, k));
+  }
+  if (step) *step = h->step;
+  return SOMA_OK;
+}
+
+int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* img, uint64_t step, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (!h->f64) return SOMA_ENOTSUP;
+  if (sys < 0 || sys >= h->n_sys || !pos || !img) return SOMA_EINVAL;
+  if (step >= (uint64_t)kInitStep) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if ((rc = sync_all(h))) return rc;
+  const cudaMemcpyKind k = where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpy(h->d_stage_pos64, pos, (size_t)S.n_b * 24, k));
+  CK(cudaMemcpy(h->d_stage_img, img, (size_t)S.n_b * 6, k));
+  CK(cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+  CK(launch_validate_pos64(h->d_stage_pos64, S.n_b, S.L64, h->d_err, h->sm_count, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int err = 0;
+  CK(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
+  if (err) {
+    CK(cudaMemset(h->d_err, 0, 4));
+    return SOMA_EINVAL;
+  }
+  CK(launch_scatter_state64(h->d_sys, sys, h->d_stage_pos64, h->d_stage_img, h->sm_count, h->stream));
   h->step = step;
   h->acc_since = step;
   CK(launch_set_step(h->d_step, h->n_sys, step, h->stream));
@@ -844,6 +941,10 @@ int soma_observables(soma_handle* h, int sys, soma_obs* out) {
   CK(cudaMemsetAsync(h->d_obs, 0, 8 * sizeof(double), h->stream));
   CK(cudaMemsetAsync(h->d_acc_sum, 0, 8, h->stream));
   CK(launch_observables(h->d_sys, sys, (long long)h->step, h->d_obs, h->d_acc_sum, h->sm_count, h->stream));
+  if (h->f64) {  // the chain sums again, from the FP64 positions
+    CK(cudaMemsetAsync(h->d_obs, 0, 3 * sizeof(double), h->stream));
+    CK(launch_obs_chains64(h->d_sys, sys, h->d_obs, h->sm_count, h->stream));
+  }
   double r[8];
   unsigned long long acc = 0;
   CK(cudaStreamSynchronize(h->stream));
@@ -875,7 +976,10 @@ int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz,
   }
   CK(cudaMemcpy(h->d_m, m_xyz, sizeof(int32_t) * 3 * nq, cudaMemcpyHostToDevice));
   CK(cudaMemsetAsync(h->d_sq, 0, sizeof(double) * 2 * nq, h->stream));
-  CK(launch_structure_factor(h->d_sys, sys, nq, h->d_m, h->d_sq, h->sm_count, h->stream));
+  if (h->f64)
+    CK(launch_structure_factor64(h->d_sys, sys, nq, h->d_m, h->d_sq, h->sm_count, h->stream));
+  else
+    CK(launch_structure_factor(h->d_sys, sys, nq, h->d_m, h->d_sq, h->sm_count, h->stream));
   std::vector<double> acc(2 * (size_t)nq);
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(acc.data(), h->d_sq, sizeof(double) * 2 * nq, cudaMemcpyDeviceToHost));
@@ -887,6 +991,7 @@ int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz,
 int soma_reorder(soma_handle* h, void* stream) {
   int rc = check_live(h);
   if (rc) return rc;
+  if (h->f64) return SOMA_ENOTSUP;
   return enqueue_reorder(h, pick(h, stream));
 }
 

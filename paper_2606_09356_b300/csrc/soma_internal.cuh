@@ -33,8 +33,15 @@ struct alignas(16) SysDev {
   uint32_t* counts;             // [3 buffers][n_c][2 types], see count_buffer()
   float* w;                     // [2 types][n_c]
   unsigned long long* acc;      // accepted moves, one counter per move tile
-  int32_t acc_first, acc_count; // this system's range of move tiles
+  int32_t acc_first, acc_count; // this system's range of accepted-move slots
   int64_t chain_base;           // first chain of this system in the global chain order
+  // FP64-position form (precision reference): wrapped FP64 positions
+  double* x64;
+  double* y64;
+  double* z64;
+  double L64[3];
+  double invL64[3], cps64[3];  // 1/L and n/L in FP64
+  double chiN64, kappaN64;
 };
 
 // Everything the move kernel needs for one system, passed by value as a

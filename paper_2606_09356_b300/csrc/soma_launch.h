@@ -39,6 +39,20 @@ cudaError_t launch_structure_factor(const SysDev* systems, int sys, int nq, cons
 
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t s);
 
+// FP64-position form (soma_f64.cu).
+cudaError_t launch_move64(const SysDev* systems, int sys, StepRef r, int sm_count, cudaStream_t s);
+cudaError_t launch_init64(const SysDev* systems, int sys, int64_t n_poly, cudaStream_t s);
+cudaError_t launch_bin64(const SysDev* systems, int sys, long long t, int sm_count, cudaStream_t s);
+cudaError_t launch_gather_state64(const SysDev* systems, int sys, double* pos, int16_t* img, int sm_count,
+                                  cudaStream_t s);
+cudaError_t launch_scatter_state64(const SysDev* systems, int sys, const double* pos, const int16_t* img,
+                                   int sm_count, cudaStream_t s);
+cudaError_t launch_validate_pos64(const double* pos, int64_t n, const double* L, int* err, int sm_count,
+                                  cudaStream_t s);
+cudaError_t launch_obs_chains64(const SysDev* systems, int sys, double* out, int sm_count, cudaStream_t s);
+cudaError_t launch_structure_factor64(const SysDev* systems, int sys, int nq, const int32_t* m, double* out,
+                                      int sm_count, cudaStream_t s);
+
 // Chain reorder (soma_sort.cu): sort the chains of every system by the
 // Morton key of their first bead's position, permute positions, images and
 // chain ids into the alternate buffers and copy them back, so the arrays

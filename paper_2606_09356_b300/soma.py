@@ -26,6 +26,8 @@ SOMA_ESTATE = -6
 SOMA_ENOTSUP = -7
 SOMA_HOST = 0
 SOMA_DEVICE = 1
+SOMA_PREC_FP32 = 0
+SOMA_PREC_FP64 = 1
 SOMA_HIST_AUTO = 0
 SOMA_HIST_FUSED = 1
 SOMA_HIST_SEPARATE = 2
@@ -34,7 +36,8 @@ SOMA_HIST_SEPARATE = 2
 EXPORTS = (
     "soma_options_default", "soma_create", "soma_destroy", "soma_strerror", "soma_last_error",
     "soma_mc_steps", "soma_sync", "soma_get_density", "soma_get_fields", "soma_set_density",
-    "soma_freeze_fields", "soma_get_state", "soma_set_state", "soma_observables", "soma_get_accepted",
+    "soma_freeze_fields", "soma_get_state", "soma_set_state", "soma_get_state64", "soma_set_state64",
+    "soma_observables", "soma_get_accepted",
     "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
     "soma_philox4x32", "soma_structure_factor_noalloc",
 )
@@ -63,7 +66,7 @@ class soma_options(ctypes.Structure):
     _fields_ = [
         ("device", ctypes.c_int32), ("sort_interval", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
         ("hist_mode", ctypes.c_int32), ("graph_steps", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
-        ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("autotune", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p),
     ]
 
@@ -113,6 +116,8 @@ def load_library(path=None):
     L.soma_freeze_fields.argtypes = [vp, i32, vp, sz, i32]
     L.soma_get_state.argtypes = [vp, i32, vp, vp, ctypes.POINTER(u64), i32]
     L.soma_set_state.argtypes = [vp, i32, vp, vp, u64, i32]
+    L.soma_get_state64.argtypes = [vp, i32, vp, vp, ctypes.POINTER(u64), i32]
+    L.soma_set_state64.argtypes = [vp, i32, vp, vp, u64, i32]
     L.soma_observables.argtypes = [vp, i32, ctypes.POINTER(soma_obs)]
     L.soma_get_accepted.argtypes = [vp, i32, ctypes.POINTER(u64)]
     L.soma_structure_factor.argtypes = [vp, i32, i32, vp, vp]
@@ -243,6 +248,7 @@ class Handle:
             if not hasattr(o, k):
                 raise TypeError(f"unknown soma option {k}")
             setattr(o, k, v)
+        self.precision = o.precision
         self.h = soma_create([s.desc() for s in self.systems], o)
 
     def close(self):
@@ -316,9 +322,27 @@ class Handle:
             img = np.ascontiguousarray(img, np.int16)
         _check(self.lib.soma_set_state(self.h, sys, _ptr(pos), _ptr(img), int(step), where), "soma_set_state")
 
+    def get_state64(self, sys=0):
+        nb = self.systems[sys].n_beads
+        pos = np.zeros((nb, 3), np.float64)
+        img = np.zeros((nb, 3), np.int16)
+        step = ctypes.c_uint64()
+        _check(self.lib.soma_get_state64(self.h, sys, _ptr(pos), _ptr(img), ctypes.byref(step), SOMA_HOST),
+               "soma_get_state64")
+        return pos, img, step.value
+
+    def set_state64(self, pos, img, step, sys=0):
+        pos = np.ascontiguousarray(pos, np.float64)
+        img = np.ascontiguousarray(img, np.int16)
+        _check(self.lib.soma_set_state64(self.h, sys, _ptr(pos), _ptr(img), int(step), SOMA_HOST),
+               "soma_set_state64")
+
     def unwrapped(self, sys=0):
         """FP64 unwrapped positions x + image * L in logical order."""
-        pos, img, _ = self.get_state(sys)
+        if getattr(self, "precision", 0) == SOMA_PREC_FP64:
+            pos, img, _ = self.get_state64(sys)
+        else:
+            pos, img, _ = self.get_state(sys)
         return pos.astype(np.float64) + img.astype(np.float64) * np.array(self.systems[sys].box)
 
     # -- measurements ----------------------------------------------------
