@@ -34,7 +34,7 @@ class OrcDesc(ctypes.Structure):
         ("n_A", ctypes.c_int32),
         ("sys_index", ctypes.c_int32),
         ("grid", ctypes.c_int32 * 3),
-        ("pad_", ctypes.c_int32),
+        ("move", ctypes.c_int32),
         ("box", ctypes.c_double * 3),
         ("chiN", ctypes.c_double),
         ("kappaN", ctypes.c_double),
@@ -82,6 +82,8 @@ class Oracle:
             L.orc_init.argtypes = [dp, f64p]
             L.orc_density.argtypes = [dp, f64p, u32p]
             L.orc_fields.argtypes = [dp, u32p, f64p]
+            L.orc_normal_quantile.argtypes = [ctypes.c_double]
+            L.orc_normal_quantile.restype = ctypes.c_double
             L.orc_energy_nb.argtypes = [dp, u32p]
             L.orc_energy_nb.restype = ctypes.c_double
             L.orc_fields_from_phi.argtypes = [dp, f64p, f64p]
@@ -98,9 +100,10 @@ class Oracle:
             cls._lib = L
         return cls._lib
 
-    def __init__(self, n_poly, N, n_A, box, grid, chiN, kappaN, A=0.0, seed=1, sys_index=0):
+    def __init__(self, n_poly, N, n_A, box, grid, chiN, kappaN, A=0.0, seed=1, sys_index=0, move=0):
         self.d = OrcDesc()
         self.d.n_poly, self.d.N, self.d.n_A, self.d.sys_index = n_poly, N, n_A, sys_index
+        self.d.move = int(move)
         for a in range(3):
             self.d.grid[a] = int(grid[a])
             self.d.box[a] = float(box[a])
@@ -199,6 +202,10 @@ class Oracle:
         self.lib().orc_structure_factor(ctypes.byref(self.d), _p(pos, ctypes.c_double), len(m),
                                         _p(m, ctypes.c_int32), _p(S, ctypes.c_double))
         return S
+
+    @classmethod
+    def normal_quantile(cls, p):
+        return float(cls.lib().orc_normal_quantile(float(p)))
 
     @classmethod
     def philox(cls, ctr, key):

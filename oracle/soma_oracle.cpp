@@ -32,6 +32,9 @@
 //                         dimer on a 2^3 grid.
 //   orc_observables       pinned through the same closed forms (R_e^2, R_g^2).
 //   orc_structure_factor  pinned: ideal-chain closed form at chiN = kappaN = 0.
+//   force-biased moves    pinned: the same Gaussian-chain statistics, the
+//                         one-bead Boltzmann law and the dimer cell-pair law
+//                         (detailed balance makes them stationary).
 //   The chiN, kappaN > 0 statistics of a dense melt have no closed form:
 //   parity unpinned there except against this oracle itself.
 #include <cmath>
@@ -51,7 +54,7 @@ typedef struct {
   int32_t n_A;        // beads 0..n_A-1 are type A, the rest type B
   int32_t sys_index;  // system number s, the fourth Philox counter word
   int32_t grid[3];    // cells per axis
-  int32_t pad_;
+  int32_t move;       // 0: uniform proposal; 1: bond-force-biased (smart) proposal
   double box[3];      // box edge per axis, R_e units
   double chiN, kappaN;
   double A;           // proposal half-width; A <= 0 means 0.5/sqrt(N-1)
@@ -109,6 +112,26 @@ static void draw(const orc_desc* d, uint32_t bead, uint32_t chain, uint32_t step
 static double unit_closed_open(uint32_t w) { return (double)(w >> 8) * 0x1p-24; }
 static double unit_open(uint32_t w) { return ((double)(w >> 9) + 0.5) * 0x1p-23; }
 static double unit_open24(uint32_t w) { return ((double)(w >> 8) + 0.5) * 0x1p-24; }
+
+// The standard normal quantile x = Phi^-1(p), p in (0, 1): bisection to a
+// bracket, then Newton steps on Phi(x) - p with Phi(x) = erfc(-x/sqrt 2)/2.
+static double normal_quantile(double p) {
+  double lo = -40.0, hi = 40.0;
+  for (int it = 0; it < 60; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (0.5 * std::erfc(-mid / std::sqrt(2.0)) < p) lo = mid; else hi = mid;
+    if (hi - lo < 1e-6) break;
+  }
+  double x = 0.5 * (lo + hi);
+  for (int it = 0; it < 4; ++it) {
+    double f = 0.5 * std::erfc(-x / std::sqrt(2.0)) - p;
+    double dens = std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI);
+    x -= f / dens;
+  }
+  return x;
+}
+
+double orc_normal_quantile(double p) { return normal_quantile(p); }
 
 // ---------------------------------------------------------------------------
 // Model constants.
@@ -283,21 +306,60 @@ static int64_t move_set(const orc_desc* d, double* pos, const double* w, uint32_
       draw(d, (uint32_t)i, chain, t, r);
       double* ri = p + 3 * i;
       double rn[3];
-      for (int a = 0; a < 3; ++a) rn[a] = ri[a] + A * (2.0 * unit_closed_open(r[a]) - 1.0);
-      double dEb = 0.0;
-      for (int j = i - 1; j <= i + 1; j += 2) {
-        if (j < 0 || j >= N) continue;
-        const double* rj = p + 3 * j;
-        double new2 = 0.0, old2 = 0.0;
-        for (int a = 0; a < 3; ++a) {
-          new2 += (rn[a] - rj[a]) * (rn[a] - rj[a]);
-          old2 += (ri[a] - rj[a]) * (ri[a] - rj[a]);
+      double dEb = 0.0, bias = 0.0;
+      if (d->move == 0) {
+        for (int a = 0; a < 3; ++a) rn[a] = ri[a] + A * (2.0 * unit_closed_open(r[a]) - 1.0);
+        for (int j = i - 1; j <= i + 1; j += 2) {
+          if (j < 0 || j >= N) continue;
+          const double* rj = p + 3 * j;
+          double new2 = 0.0, old2 = 0.0;
+          for (int a = 0; a < 3; ++a) {
+            new2 += (rn[a] - rj[a]) * (rn[a] - rj[a]);
+            old2 += (ri[a] - rj[a]) * (ri[a] - rj[a]);
+          }
+          dEb += new2 - old2;
         }
-        dEb += new2 - old2;
+      } else {
+        // Bond-force-biased move (Sec. 2 names the method; reading: the
+        // force-biased Metropolis scheme with a Gaussian proposal of variance
+        // s2 = A^2/3 per axis, the uniform proposal's variance, centred on the
+        // drift (s2/2) F with F = -dE_bond/dr; the log-ratio of reverse and
+        // forward proposal densities enters the acceptance, so detailed
+        // balance holds).  Normals from words 0-2 by the inverse CDF of
+        // ((w >> 8) + 1/2) 2^-24.
+        const double s2 = A * A / 3.0;
+        double F[3] = {0, 0, 0}, Fn[3] = {0, 0, 0};
+        for (int j = i - 1; j <= i + 1; j += 2) {
+          if (j < 0 || j >= N) continue;
+          for (int a = 0; a < 3; ++a) F[a] -= 2.0 * k_b * (ri[a] - p[3 * j + a]);
+        }
+        double fwd = 0.0, rev = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          const double xi = normal_quantile(unit_open24(r[a]));
+          rn[a] = ri[a] + 0.5 * s2 * F[a] + std::sqrt(s2) * xi;
+        }
+        for (int j = i - 1; j <= i + 1; j += 2) {
+          if (j < 0 || j >= N) continue;
+          const double* rj = p + 3 * j;
+          double new2 = 0.0, old2 = 0.0;
+          for (int a = 0; a < 3; ++a) {
+            new2 += (rn[a] - rj[a]) * (rn[a] - rj[a]);
+            old2 += (ri[a] - rj[a]) * (ri[a] - rj[a]);
+            Fn[a] -= 2.0 * k_b * (rn[a] - rj[a]);
+          }
+          dEb += new2 - old2;
+        }
+        for (int a = 0; a < 3; ++a) {
+          const double f = rn[a] - ri[a] - 0.5 * s2 * F[a];   // forward: r -> r'
+          const double b = ri[a] - rn[a] - 0.5 * s2 * Fn[a];  // reverse: r' -> r
+          fwd += f * f;
+          rev += b * b;
+        }
+        bias = (rev - fwd) / (2.0 * s2);  // -ln[q(r'->r) / q(r->r')]
       }
       const double* wt = w + (int64_t)type_of(d, i) * nc;
       double dE = k_b * dEb + wt[cell_of(d, rn)] - wt[cell_of(d, ri)];
-      double margin = dE + std::log(unit_open(r[3]));
+      double margin = dE + bias + std::log(unit_open(r[3]));
       bool ok = margin < 0.0;
       int64_t b = c * N + i;
       if (acc_out) acc_out[b] = ok ? 1 : 0;

@@ -268,6 +268,78 @@ def pin_structure_factor_ideal(O, seeds=12):
     return fails
 
 
+# ---------------------------------------------------------------------------
+# Bond-force-biased (smart) moves: detailed balance makes the same Boltzmann
+# laws stationary, so the same closed forms pin them.
+def pin_smart_ideal_dynamics(O, steps=300):
+    fails = []
+    n_poly, N = 4096, 32
+    o = O(n_poly, N, 16, (4.0, 4.0, 4.0), (16, 16, 16), 0.0, 0.0, seed=13, move=1)
+    pos = o.init()
+    res = o.run(pos, 0, steps, n_threads=NTHREADS, re2_trace=True)
+    p = pos.reshape(n_poly, N, 3)
+    b2 = (np.diff(p, axis=1) ** 2).sum(-1).mean() * (N - 1)
+    _check(fails, "smart: <b^2>(N-1) after the run", b2, 1.0, 5 * np.sqrt(2.0 / 3.0 / (n_poly * (N - 1))))
+    _check(fails, "smart: time-averaged <R_e^2>", res["re2"].mean(), 1.0, 5 * np.sqrt(2.0 / 3.0 / n_poly))
+    acc = res["accepted"] / (o.n_b * steps)
+    if not (0.5 < acc < 1.0):
+        fails.append(f"smart: acceptance {acc:.3f} outside (0.5, 1)")
+    return fails
+
+
+def pin_smart_single_bead_field(O, blocks=16, per_block=15):
+    fails = []
+    rng = np.random.default_rng(12)
+    o = O(4096, 1, 1, (1.0, 1.5, 2.0), (2, 3, 4), 0.0, 0.0, A=0.6, seed=15, move=1)
+    w = rng.normal(0.0, 0.8, size=(2, o.n_c))
+    pos = o.init()
+    o.run(pos, 0, 10, w_frozen=w, n_threads=NTHREADS)
+    samples = []
+    for b in range(blocks):
+        r = o.run(pos, 10 + b * per_block, per_block, w_frozen=w, n_threads=NTHREADS, occ=True)
+        occ = r["occ"].reshape(2, o.n_c)[0].astype(np.float64)
+        samples.append(occ / occ.sum())
+    p = np.exp(-w[0])
+    _block_test(fails, "smart single bead occupancy", np.array(samples), p / p.sum())
+    return fails
+
+
+def pin_smart_dimer_cell_pairs(O, blocks=16, per_block=15):
+    fails = []
+    rng = np.random.default_rng(22)
+    box, grid = (1.0, 1.0, 1.0), (2, 2, 2)
+    o = O(4096, 2, 1, box, grid, 0.0, 0.0, seed=19, move=1)
+    kb, _, _ = o.params()
+    w = rng.normal(0.0, 0.7, size=(2, o.n_c))
+    Ks = [_bond_cell_kernel(box[a], grid[a], kb) for a in range(3)]
+    cells = [(ix, iy, iz) for ix in range(2) for iy in range(2) for iz in range(2)]
+    P = np.zeros((o.n_c, o.n_c))
+    for c1, (a1, b1, z1) in enumerate(cells):
+        for c2, (a2, b2, z2) in enumerate(cells):
+            P[c1, c2] = np.exp(-w[0, c1] - w[1, c2]) * Ks[0][a1, a2] * Ks[1][b1, b2] * Ks[2][z1, z2]
+    P /= P.sum()
+    pos = o.init()
+    o.run(pos, 0, 20, w_frozen=w, n_threads=NTHREADS)
+    samples = []
+    for b in range(blocks):
+        r = o.run(pos, 20 + b * per_block, per_block, w_frozen=w, n_threads=NTHREADS, pair_hist=True)
+        h = r["pair_hist"].astype(np.float64)
+        samples.append(h / h.sum())
+    _block_test(fails, "smart AB dimer cell-pair law", np.array(samples), P.reshape(-1))
+    return fails
+
+
+def pin_normal_quantile(O):
+    """The oracle's inverse normal CDF against scipy's (a library routine of
+    the same definition) and the symmetry Phi^-1(1 - p) = -Phi^-1(p)."""
+    from scipy.special import ndtri
+    fails = []
+    for p in (2.0 ** -25, 1e-6, 0.01, 0.2, 0.5, 0.7, 0.999, 1 - 2.0 ** -25):
+        _check(fails, f"quantile({p})", O.normal_quantile(p), float(ndtri(p)), 1e-9)
+        _check(fails, f"symmetry({p})", O.normal_quantile(1 - p) + O.normal_quantile(p), 0.0, 1e-8)
+    return fails
+
+
 ALL_PINS = {
     "philox_triton": pin_philox_triton,
     "init_statistics": pin_init_statistics,
@@ -277,4 +349,8 @@ ALL_PINS = {
     "density_bruteforce": pin_density_bruteforce,
     "fields_derivative": pin_fields_derivative,
     "structure_factor_ideal": pin_structure_factor_ideal,
+    "smart_ideal_dynamics": pin_smart_ideal_dynamics,
+    "smart_single_bead_field": pin_smart_single_bead_field,
+    "smart_dimer_cell_pairs": pin_smart_dimer_cell_pairs,
+    "normal_quantile": pin_normal_quantile,
 }

@@ -20,8 +20,9 @@ MUTATIONS = [
     ("field term sign", "dE = k_b * dEb + wt[cell_of(d, rn)] - wt[cell_of(d, ri)];",
      "dE = k_b * dEb - wt[cell_of(d, rn)] + wt[cell_of(d, ri)];", "single_bead_field"),
     ("types swapped", "return i < d->n_A ? 0 : 1;", "return i < d->n_A ? 1 : 0;", "dimer_cell_pairs"),
-    ("right neighbour dropped", "for (int j = i - 1; j <= i + 1; j += 2)",
-     "for (int j = i - 1; j <= i - 1; j += 2)", "ideal_dynamics"),
+    ("right neighbour dropped",
+     "unit_closed_open(r[a]) - 1.0);\n        for (int j = i - 1; j <= i + 1; j += 2)",
+     "unit_closed_open(r[a]) - 1.0);\n        for (int j = i - 1; j <= i - 1; j += 2)", "ideal_dynamics"),
     ("acceptance inverted", "bool ok = margin < 0.0;", "bool ok = margin > 0.0;", "ideal_dynamics"),
     ("cell axes transposed", "return (idx[0] * d->grid[1] + idx[1]) * d->grid[2] + idx[2];",
      "return (idx[2] * d->grid[1] + idx[1]) * d->grid[0] + idx[0];", "density_bruteforce"),
@@ -38,6 +39,15 @@ MUTATIONS = [
      "structure_factor_ideal"),
     ("bond of second bead anchored to bead 0", "p[3 * i + 0] = p[3 * (i - 1) + 0] + sigma * z0;",
      "p[3 * i + 0] = p[0] + sigma * z0;", "init_statistics"),
+    ("force-bias asymmetry term dropped", "bias = (rev - fwd) / (2.0 * s2);", "bias = 0.0;",
+     "smart_ideal_dynamics"),
+    ("force-bias drift sign flipped", "rn[a] = ri[a] + 0.5 * s2 * F[a] + std::sqrt(s2) * xi;",
+     "rn[a] = ri[a] - 0.5 * s2 * F[a] + std::sqrt(s2) * xi;", "smart_ideal_dynamics"),
+    ("force-bias reverse drift from the old force", "const double b = ri[a] - rn[a] - 0.5 * s2 * Fn[a];",
+     "const double b = ri[a] - rn[a] - 0.5 * s2 * F[a];", "smart_ideal_dynamics"),
+    ("normal quantile Newton step sign", "x -= f / dens;", "x += f / dens;", "normal_quantile"),
+    ("force-bias normals from the wrong word", "normal_quantile(unit_open24(r[a]))",
+     "normal_quantile(unit_open24(r[0]))", "smart_ideal_dynamics"),
 ]
 
 
