@@ -399,6 +399,13 @@ def run_gpu(args):
                        "then soma_get_density to pinned host; host wall clock"}
         _ = acc
 
+    # the bond-force-biased (smart) move on the same workload, timed like the
+    # headline (L2 flushed between steps, CUDA events around each step)
+    smart = None
+    if not args.no_smart:
+        smart = bench_smart(soma, torch, rank_system_kwargs(args.workload, rank), local, sptr, stream, flush,
+                            args.steps, args.warmup, hbm_peak, n_b, n_c)
+
     # batched replicas vs sequential plain runs of the same 64 systems
     batched = None
     if rank == 0 and not args.no_batched:
@@ -415,13 +422,45 @@ def run_gpu(args):
                        "tuned": {k: info_after[k] for k in ("ctas_per_sm", "hist_mode")},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "steady_state": steady, "batched": batched,
+            "clocks": clk.summary(), "steady_state": steady, "smart_moves": smart, "batched": batched,
             "wall_s_timed": wall,
         }
         print(json.dumps(out))
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def bench_smart(soma, torch, kw, device, sptr, stream, flush, steps, warmup, hbm_peak, n_b, n_c):
+    """The workload with bond-force-biased trial moves: moves/s over flushed
+    steps and the move kernel's fraction of the HBM roofline (same
+    algorithmic bytes as the uniform move)."""
+    h = soma.Handle(soma.System(**{**kw, "move": soma.SOMA_MOVE_SMART}), device=device, kernel_timing=1,
+                    graph_steps=0, autotune=1)
+    for _ in range(warmup):
+        h.mc_steps(1, stream=sptr)
+    torch.cuda.synchronize()
+    h.kernel_times(reset=True)
+    a0 = h.accepted()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+        h.mc_steps(1, stream=sptr)
+        with torch.cuda.stream(stream):
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = sum(x.elapsed_time(y) for x, y in ev)
+    kt = h.kernel_times(reset=True)
+    acc = (h.accepted() - a0) / (steps * n_b)
+    h.close()
+    mv_ms, mv_n = kt["move"]
+    move_avg = mv_ms / max(1, mv_n)
+    achieved = move_kernel_bytes(n_b, n_c) / (move_avg * 1e-3) / 1e9
+    return {"value": steps * n_b / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / steps,
+            "move_ms": move_avg, "achieved_gbs": achieved, "frac": achieved / hbm_peak, "acceptance": acc,
+            "note": "SOMA_MOVE_SMART, same workload, L2 flushed between timed steps"}
 
 
 def bench_batched(soma, workloads, torch, sptr, stream, steps=20):
@@ -474,6 +513,7 @@ def main():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-steady", action="store_true")
+    p.add_argument("--no-smart", action="store_true")
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be at least 3")

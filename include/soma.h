@@ -70,6 +70,16 @@ extern "C" {
 #define SOMA_HIST_FUSED 1     /* binned in the epilogue of the move kernel */
 #define SOMA_HIST_SEPARATE 2  /* separate histogram kernel after the moves */
 
+/* Trial-move kinds (soma_system_desc.move). */
+#define SOMA_MOVE_UNIFORM 0 /* displacement uniform in [-A, A)^3 (Sec. 2.1, step (a)) */
+#define SOMA_MOVE_SMART 1   /* bond-force-biased ("smart") move named in Sec. 2: a
+                               Gaussian displacement of per-axis variance s2 = A^2/3
+                               centred on (s2/2) F, F the bond force on the bead, with
+                               the proposal asymmetry in the acceptance.  N <= 64,
+                               SOMA_PREC_FP32 only (else SOMA_ENOTSUP); needs
+                               A^2 (N-1)/2 <= 1/2 and 6.93 A < every box edge
+                               (else SOMA_EINVAL), so a proposal wraps at most once. */
+
 /* One system: an AB diblock melt A_{n_A} B_{N - n_A} in a periodic box. */
 typedef struct soma_system_desc {
   int32_t n_poly;  /* chains, >= 1 */
@@ -79,7 +89,7 @@ typedef struct soma_system_desc {
                         need distinct ids.  A system's trajectory depends on
                         (seed, system_id) only, not on its place in a batch. */
   int32_t grid[3]; /* cells per axis, >= 1 each; total cells < 2^31 */
-  int32_t reserved1;
+  int32_t move;    /* SOMA_MOVE_UNIFORM or SOMA_MOVE_SMART */
   double box[3];   /* box edges in R_e */
   double chiN;     /* Flory-Huggins chi times N */
   double kappaN;   /* Helfand compressibility kappa times N */

@@ -163,6 +163,14 @@ int validate_desc(const soma_system_desc& d) {
   const double A = d.A > 0 ? d.A : 0.5 / std::sqrt((double)(d.N - 1));
   for (int a = 0; a < 3; ++a)
     if (A >= d.box[a]) return SOMA_EINVAL;  // a proposal must wrap at most once
+  if (d.move != SOMA_MOVE_UNIFORM && d.move != SOMA_MOVE_SMART) return SOMA_EINVAL;
+  if (d.move == SOMA_MOVE_SMART) {
+    // |drift s| <= (A^2 (N-1)/2) L and |sig xi| < 6 A/sqrt(3) with |xi| < 6:
+    // both below L/2 keeps a proposal within one image of the box
+    if (0.5 * A * A * (d.N - 1) > 0.5) return SOMA_EINVAL;
+    for (int a = 0; a < 3; ++a)
+      if (12.0 / std::sqrt(3.0) * A >= d.box[a]) return SOMA_EINVAL;
+  }
   return SOMA_OK;
 }
 
@@ -232,6 +240,13 @@ void build_args(soma_handle* h) {
     a.from_counts = S.frozen ? 0 : 1;
     a.acc = h->d_acc + S.acc_first;
     a.err = h->d_err;
+    a.smart = h->desc[s].move == SOMA_MOVE_SMART ? 1 : 0;
+    {
+      const double s2 = (double)S.A * (double)S.A / 3.0;
+      a.sig = (float)std::sqrt(s2);
+      a.drift = (float)(s2 * (double)S.kb);
+      a.inv2s2 = (float)(0.5 / s2);
+    }
     h->n_tiles[s] = a.n_tiles;
 
     FieldArgs& f = h->fargs[s];
@@ -248,23 +263,26 @@ void build_args(soma_handle* h) {
   h->batches.clear();
   h->batch_members.clear();
   if (h->n_sys > 1) {
-    std::vector<int> reg;
-    for (int s = 0; s < h->n_sys; ++s)
-      if (h->host_sys[s].P) reg.push_back(s);
-    for (size_t g0 = 0; g0 < reg.size(); g0 += kMaxBatch) {
-      BatchArgs b;
-      std::memset(&b, 0, sizeof(b));
-      std::vector<int> members(reg.begin() + g0, reg.begin() + std::min(reg.size(), g0 + kMaxBatch));
-      b.n_sys = (int)members.size();
-      int tiles = 0;
-      for (int i = 0; i < b.n_sys; ++i) {
-        b.tile_start[i] = tiles;
-        b.sys[i] = h->margs[members[i]];
-        tiles += h->n_tiles[members[i]];
+    // a group holds one move kind (the batch kernel is specialised on it)
+    for (int kind = SOMA_MOVE_UNIFORM; kind <= SOMA_MOVE_SMART; ++kind) {
+      std::vector<int> reg;
+      for (int s = 0; s < h->n_sys; ++s)
+        if (h->host_sys[s].P && h->desc[s].move == kind) reg.push_back(s);
+      for (size_t g0 = 0; g0 < reg.size(); g0 += kMaxBatch) {
+        BatchArgs b;
+        std::memset(&b, 0, sizeof(b));
+        std::vector<int> members(reg.begin() + g0, reg.begin() + std::min(reg.size(), g0 + kMaxBatch));
+        b.n_sys = (int)members.size();
+        int tiles = 0;
+        for (int i = 0; i < b.n_sys; ++i) {
+          b.tile_start[i] = tiles;
+          b.sys[i] = h->margs[members[i]];
+          tiles += h->n_tiles[members[i]];
+        }
+        b.tile_start[b.n_sys] = tiles;
+        h->batches.push_back(b);
+        h->batch_members.push_back(members);
       }
-      b.tile_start[b.n_sys] = tiles;
-      h->batches.push_back(b);
-      h->batch_members.push_back(members);
     }
   }
 }
@@ -506,8 +524,10 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   if (o.precision == SOMA_PREC_FP64) {
     if (n_sys != 1) return SOMA_EINVAL;  // the FP64 form steps one system per handle
     for (int s = 0; s < n_sys; ++s)
-      if (sys[s].N > 64) return SOMA_ENOTSUP;
+      if (sys[s].N > 64 || sys[s].move != SOMA_MOVE_UNIFORM) return SOMA_ENOTSUP;
   }
+  for (int s = 0; s < n_sys; ++s)
+    if (sys[s].move == SOMA_MOVE_SMART && sys[s].N > 64) return SOMA_ENOTSUP;
   if (o.hist_mode < SOMA_HIST_AUTO || o.hist_mode > SOMA_HIST_SEPARATE) return SOMA_EINVAL;
   if (o.graph_steps < 0 || o.graph_steps > 4096) return SOMA_EINVAL;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SOMA_EINVAL;

@@ -49,7 +49,7 @@ struct alignas(16) SysDev {
 struct MoveArgs {
   float L[3], invL[3], cps[3];
   float Lm[3];               // largest float below L
-  float pad0;
+  int32_t smart;             // 1: bond-force-biased proposals (host-side flag; kernels are templated)
   int32_t n[3];
   float A, kb;
   uint32_t rk[10][2];        // Philox round keys
@@ -67,7 +67,10 @@ struct MoveArgs {
   int32_t from_counts;       // batched launches: 1 = fields from counts, 0 = field array
   unsigned long long* acc;   // accepted-move slots of this system, one per CTA of a launch
   int* err;
-  int64_t pad2;
+  // bond-force-biased proposal d = -drift s + sig xi, s the sum of the bead's
+  // bond vectors, xi standard normal; s2 = A^2/3, drift = s2 k_b, sig = sqrt(s2)
+  float sig, drift, inv2s2;  // inv2s2 = 1 / (2 s2)
+  float pad2;
 };
 
 // Up to kMaxBatch systems stepped by one persistent launch: their constants

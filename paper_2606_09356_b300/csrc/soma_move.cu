@@ -170,39 +170,35 @@ __device__ __forceinline__ void produce_tile(const MoveArgs& a, int tile, MoveSt
   bulk_g2s(st.cid, a.chain_id + c0, cbytes, full);
 }
 
-// Consumer warp: one tile of system a at step t.  Reads the stage, releases
-// it, moves the even then the odd beads of its chains, writes back, bins.
-// Returns the number of accepted moves of this lane.
+// Field difference w_t(c1) - w_t(c0) for a bead of type t from the integer
+// counts n0 = (nA, nB) of c0 and n1 of c1 (the chi term couples to the other
+// type's count, the kappa term to the total).
+__device__ __forceinline__ float field_from_counts(const MoveArgs& a, int type, uint2 n0, uint2 n1) {
+  const int d_other = type ? (int)(n1.x - n0.x) : (int)(n1.y - n0.y);
+  const int d_tot = (int)(n1.x + n1.y) - (int)(n0.x + n0.y);
+  return a.inv_rho * fmaf(a.chiN_N, (float)d_other, a.kappaN_N * (float)d_tot);
+}
+
+// Standard normal deviate of a Philox word: Phi^-1(((w >> 8) + 1/2) 2^-24).
+// The argument is formed exactly in FP32 by evaluating the lower tail of
+// whichever half of (0, 1) it falls in (Phi^-1(1 - v) = -Phi^-1(v)).
+__device__ __forceinline__ float normal_of_word(uint32_t w) {
+  const uint32_t m = w >> 8;
+  const bool upper = m >= (1u << 23);
+  const uint32_t odd = upper ? (0x2000000u - 2u * m - 1u) : (2u * m + 1u);  // odd < 2^24: exact
+  const float v = normcdfinvf((float)odd * 0x1p-25f);
+  return upper ? -v : v;
+}
+
+// The bead pair of one lane: positions in, decisions, final cells and image
+// codes out.  Uniform proposals (Sec. 2.1, step (a)).
 template <bool kFromCounts>
-__device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, const MoveStage& st, uint64_t* empty,
-                                                 long long tl, int warp, int lane) {
+__device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, uint32_t cid, int k, int e, int o,
+                                             int te, int to, bool he, bool ho, float& xe, float& ye, float& ze,
+                                             float& xo, float& yo, float& zo, bool& acc, bool& acco, int& ce,
+                                             int& co, float& wrap_e, float& wrap_o) {
   const uint32_t t = (uint32_t)tl;
   const int P = a.P, N = a.N;
-  const int k = lane & (P - 1);
-  const int chain_in_tile = warp * (32 / P) + lane / P;
-  const int e = 2 * k, o = 2 * k + 1;
-  const int te = e < a.n_A ? 0 : 1, to = o < a.n_A ? 0 : 1;
-  const int c0 = tile * a.chains_per_tile;
-  const int nch = min(a.chains_per_tile, a.n_poly - c0);
-  const bool chain_ok = chain_in_tile < nch;
-  const bool he = chain_ok && e < N, ho = chain_ok && o < N;
-  const int lb = chain_in_tile * N + e;  // bead e within the tile
-  float xe = 0.f, ye = 0.f, ze = 0.f, xo = 0.f, yo = 0.f, zo = 0.f;
-  if ((N & 1) == 0) {
-    if (he) {
-      const float2 vx = lds2(st.x + lb);
-      const float2 vy = lds2(st.y + lb);
-      const float2 vz = lds2(st.z + lb);
-      xe = vx.x; xo = vx.y; ye = vy.x; yo = vy.y; ze = vz.x; zo = vz.y;
-    }
-  } else {
-    if (he) { xe = lds1(st.x + lb); ye = lds1(st.y + lb); ze = lds1(st.z + lb); }
-    if (ho) { xo = lds1(st.x + lb + 1); yo = lds1(st.y + lb + 1); zo = lds1(st.z + lb + 1); }
-  }
-  const uint32_t cid = chain_ok ? lds1(st.cid + chain_in_tile) : 0u;
-  __syncwarp();
-  if (lane == 0) mbar_arrive(empty);  // this warp is done with the stage
-
   // ---- proposals of both beads, then all four gathers ----
   const uint4 re = philox10(make_uint4((uint32_t)e, cid, t, (uint32_t)a.sys_index), a.rk);
   const uint4 ro = philox10(make_uint4((uint32_t)o, cid, t, (uint32_t)a.sys_index), a.rk);
@@ -219,11 +215,11 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   const float pex = wrap_step(xe + dex, a.L[0], a.Lm[0], fx);
   const float pey = wrap_step(ye + dey, a.L[1], a.Lm[1], fy);
   const float pez = wrap_step(ze + dez, a.L[2], a.Lm[2], fz);
-  const float wrap_e = fmaf(9.f, fz, fmaf(3.f, fy, fx));
+  wrap_e = fmaf(9.f, fz, fmaf(3.f, fy, fx));
   const float pox = wrap_step(xo + dox, a.L[0], a.Lm[0], fx);
   const float poy = wrap_step(yo + doy, a.L[1], a.Lm[1], fy);
   const float poz = wrap_step(zo + doz, a.L[2], a.Lm[2], fz);
-  const float wrap_o = fmaf(9.f, fz, fmaf(3.f, fy, fx));
+  wrap_o = fmaf(9.f, fz, fmaf(3.f, fy, fx));
   const int ce0 = cell_idx(a, xe, ye, ze), ce1 = cell_idx(a, pex, pey, pez);
   const int co0 = cell_idx(a, xo, yo, zo), co1 = cell_idx(a, pox, poy, poz);
   float fe, fo;
@@ -231,13 +227,8 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
     const uint2* __restrict__ prev = reinterpret_cast<const uint2*>(count_buffer(a.counts, a.n_c, tl - 1));
     const uint2 ne0 = __ldg(prev + ce0), ne1 = __ldg(prev + ce1);
     const uint2 no0 = __ldg(prev + co0), no1 = __ldg(prev + co1);
-    // the chi term couples to the other type's count, the kappa term to the total
-    const int de_other = te ? (int)(ne1.x - ne0.x) : (int)(ne1.y - ne0.y);
-    const int do_other = to ? (int)(no1.x - no0.x) : (int)(no1.y - no0.y);
-    const int de_tot = (int)(ne1.x + ne1.y) - (int)(ne0.x + ne0.y);
-    const int do_tot = (int)(no1.x + no1.y) - (int)(no0.x + no0.y);
-    fe = a.inv_rho * fmaf(a.chiN_N, (float)de_other, a.kappaN_N * (float)de_tot);
-    fo = a.inv_rho * fmaf(a.chiN_N, (float)do_other, a.kappaN_N * (float)do_tot);
+    fe = field_from_counts(a, te, ne0, ne1);
+    fo = field_from_counts(a, to, no0, no1);
   } else {
     const float* __restrict__ wte = a.w + (te ? a.n_c : 0);
     const float* __restrict__ wto = a.w + (to ? a.n_c : 0);
@@ -265,7 +256,7 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   // accept iff dE + ln u < 0, u = ((r3 >> 9) + 1/2) 2^-23 in (0, 1),
   // evaluated as dE log2(e) + log2(u) < 0
   const float u = fmaf((float)(re.w >> 9), 0x1p-23f, 0x1p-24f);
-  const bool acc = he && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
+  acc = he && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
   // displacement actually applied to bead e (0 if rejected)
   const float ax = acc ? dex : 0.f, ay = acc ? dey : 0.f, az = acc ? dez : 0.f;
   if (acc) {
@@ -281,10 +272,176 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   const float dEbo = fmaf(2.f, fmaf(dox, ox, fmaf(doy, oy, doz * oz)), (1.f + wR1) * o2);
   const float dEo = fmaf(a.kb, dEbo, fo);
   const float uo = fmaf((float)(ro.w >> 9), 0x1p-23f, 0x1p-24f);
-  const bool acco = ho && (fmaf(dEo, kLog2e, __log2f(uo)) < 0.f);
+  acco = ho && (fmaf(dEo, kLog2e, __log2f(uo)) < 0.f);
   if (acco) {
     xo = pox; yo = poy; zo = poz;
   }
+  ce = acc ? ce1 : ce0;
+  co = acco ? co1 : co0;
+}
+
+// Bond-force-biased proposals (the smart moves named in Sec. 2): bead i is
+// displaced by d = -drift s + sig xi, with s the sum of its bond vectors
+// (the bond force is F = -2 k_b s, so -drift s = (s2/2) F), xi standard
+// normal from Philox words x, y, z, and the Metropolis margin gains
+//   ln q(r -> r') - ln q(r' -> r) = (|b|^2 - |f|^2) / (2 s2),
+// f = sig xi the forward residual, b = -d + drift (s + n d) the reverse one
+// (n bonds).  The odd bead's force depends on set 0's outcome, so its
+// proposal and its new-cell gather follow the even bead's decision.  Every
+// bond vector is minimum-imaged, so |s| <= L per axis and, with the bounds
+// the host enforces (drift <= k_b A^2/3 <= 1/2, 6 sig < L/2), a proposal
+// stays within one image of the box.
+template <bool kFromCounts>
+__device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, uint32_t cid, int k, int e, int o,
+                                           int te, int to, bool he, bool ho, float& xe, float& ye, float& ze,
+                                           float& xo, float& yo, float& zo, bool& acc, bool& acco, int& ce,
+                                           int& co, float& wrap_e, float& wrap_o) {
+  const uint32_t t = (uint32_t)tl;
+  const int P = a.P, N = a.N;
+  const uint4 re = philox10(make_uint4((uint32_t)e, cid, t, (uint32_t)a.sys_index), a.rk);
+  const uint4 ro = philox10(make_uint4((uint32_t)o, cid, t, (uint32_t)a.sys_index), a.rk);
+  const float wR0 = (o < N) ? 1.f : 0.f;
+  const float wL0 = (k > 0) ? 1.f : 0.f;
+  const float wR1 = (o + 1 < N) ? 1.f : 0.f;
+  // ---- set 0: even bead ----
+  const float lx = __shfl_up_sync(0xffffffffu, xo, 1, P);
+  const float ly = __shfl_up_sync(0xffffffffu, yo, 1, P);
+  const float lz = __shfl_up_sync(0xffffffffu, zo, 1, P);
+  const float bLx = min_image(xe - lx, a.L[0], a.invL[0]);
+  const float bLy = min_image(ye - ly, a.L[1], a.invL[1]);
+  const float bLz = min_image(ze - lz, a.L[2], a.invL[2]);
+  const float bRx = min_image(xe - xo, a.L[0], a.invL[0]);
+  const float bRy = min_image(ye - yo, a.L[1], a.invL[1]);
+  const float bRz = min_image(ze - zo, a.L[2], a.invL[2]);
+  const float sx = fmaf(wL0, bLx, wR0 * bRx), sy = fmaf(wL0, bLy, wR0 * bRy), sz = fmaf(wL0, bLz, wR0 * bRz);
+  const float n0 = wL0 + wR0;
+  const float fex = a.sig * normal_of_word(re.x);
+  const float fey = a.sig * normal_of_word(re.y);
+  const float fez = a.sig * normal_of_word(re.z);
+  const float dex = fmaf(-a.drift, sx, fex);
+  const float dey = fmaf(-a.drift, sy, fey);
+  const float dez = fmaf(-a.drift, sz, fez);
+  float fx, fy, fz;
+  const float pex = wrap_step(xe + dex, a.L[0], a.Lm[0], fx);
+  const float pey = wrap_step(ye + dey, a.L[1], a.Lm[1], fy);
+  const float pez = wrap_step(ze + dez, a.L[2], a.Lm[2], fz);
+  wrap_e = fmaf(9.f, fz, fmaf(3.f, fy, fx));
+  const int ce0 = cell_idx(a, xe, ye, ze), ce1 = cell_idx(a, pex, pey, pez);
+  const int co0 = cell_idx(a, xo, yo, zo);
+  const uint2* __restrict__ prev = reinterpret_cast<const uint2*>(count_buffer(a.counts, a.n_c, tl - 1));
+  const float* __restrict__ wte = a.w + (te ? a.n_c : 0);
+  const float* __restrict__ wto = a.w + (to ? a.n_c : 0);
+  float fe;
+  uint2 no0 = make_uint2(0u, 0u);
+  float wo0 = 0.f;
+  if (kFromCounts) {
+    const uint2 ne0 = __ldg(prev + ce0), ne1 = __ldg(prev + ce1);
+    no0 = __ldg(prev + co0);
+    fe = field_from_counts(a, te, ne0, ne1);
+  } else {
+    fe = __ldg(wte + ce1) - __ldg(wte + ce0);
+    wo0 = __ldg(wto + co0);
+  }
+  {
+    const float d2 = fmaf(dex, dex, fmaf(dey, dey, dez * dez));
+    const float dEb = fmaf(2.f, fmaf(dex, sx, fmaf(dey, sy, dez * sz)), n0 * d2);
+    const float brx = fmaf(a.drift, fmaf(n0, dex, sx), -dex);
+    const float bry = fmaf(a.drift, fmaf(n0, dey, sy), -dey);
+    const float brz = fmaf(a.drift, fmaf(n0, dez, sz), -dez);
+    const float rev = fmaf(brx, brx, fmaf(bry, bry, brz * brz));
+    const float fwd = fmaf(fex, fex, fmaf(fey, fey, fez * fez));
+    const float dE = fmaf(a.kb, dEb, fe) + (rev - fwd) * a.inv2s2;
+    const float u = fmaf((float)(re.w >> 9), 0x1p-23f, 0x1p-24f);
+    acc = he && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
+  }
+  const float ax = acc ? dex : 0.f, ay = acc ? dey : 0.f, az = acc ? dez : 0.f;
+  if (acc) {
+    xe = pex; ye = pey; ze = pez;
+  }
+  // ---- set 1: odd bead, force from the bonds after set 0 ----
+  const float qx = __shfl_down_sync(0xffffffffu, bLx + ax, 1, P);
+  const float qy = __shfl_down_sync(0xffffffffu, bLy + ay, 1, P);
+  const float qz = __shfl_down_sync(0xffffffffu, bLz + az, 1, P);
+  const float ox = fmaf(wR1, min_image(-qx, a.L[0], a.invL[0]), min_image(-(bRx + ax), a.L[0], a.invL[0]));
+  const float oy = fmaf(wR1, min_image(-qy, a.L[1], a.invL[1]), min_image(-(bRy + ay), a.L[1], a.invL[1]));
+  const float oz = fmaf(wR1, min_image(-qz, a.L[2], a.invL[2]), min_image(-(bRz + az), a.L[2], a.invL[2]));
+  const float n1 = 1.f + wR1;
+  const float fox = a.sig * normal_of_word(ro.x);
+  const float foy = a.sig * normal_of_word(ro.y);
+  const float foz = a.sig * normal_of_word(ro.z);
+  const float dox = fmaf(-a.drift, ox, fox);
+  const float doy = fmaf(-a.drift, oy, foy);
+  const float doz = fmaf(-a.drift, oz, foz);
+  const float pox = wrap_step(xo + dox, a.L[0], a.Lm[0], fx);
+  const float poy = wrap_step(yo + doy, a.L[1], a.Lm[1], fy);
+  const float poz = wrap_step(zo + doz, a.L[2], a.Lm[2], fz);
+  wrap_o = fmaf(9.f, fz, fmaf(3.f, fy, fx));
+  const int co1 = cell_idx(a, pox, poy, poz);
+  float fo;
+  if (kFromCounts)
+    fo = field_from_counts(a, to, no0, __ldg(prev + co1));
+  else
+    fo = __ldg(wto + co1) - wo0;
+  {
+    const float d2 = fmaf(dox, dox, fmaf(doy, doy, doz * doz));
+    const float dEb = fmaf(2.f, fmaf(dox, ox, fmaf(doy, oy, doz * oz)), n1 * d2);
+    const float brx = fmaf(a.drift, fmaf(n1, dox, ox), -dox);
+    const float bry = fmaf(a.drift, fmaf(n1, doy, oy), -doy);
+    const float brz = fmaf(a.drift, fmaf(n1, doz, oz), -doz);
+    const float rev = fmaf(brx, brx, fmaf(bry, bry, brz * brz));
+    const float fwd = fmaf(fox, fox, fmaf(foy, foy, foz * foz));
+    const float dE = fmaf(a.kb, dEb, fo) + (rev - fwd) * a.inv2s2;
+    const float u = fmaf((float)(ro.w >> 9), 0x1p-23f, 0x1p-24f);
+    acco = ho && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
+  }
+  if (acco) {
+    xo = pox; yo = poy; zo = poz;
+  }
+  ce = acc ? ce1 : ce0;
+  co = acco ? co1 : co0;
+}
+
+// Consumer warp: one tile of system a at step t.  Reads the stage, releases
+// it, moves the even then the odd beads of its chains, writes back, bins.
+// Returns the number of accepted moves of this lane.
+template <bool kFromCounts, bool kSmart>
+__device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, const MoveStage& st, uint64_t* empty,
+                                                 long long tl, int warp, int lane) {
+  const int P = a.P, N = a.N;
+  const int k = lane & (P - 1);
+  const int chain_in_tile = warp * (32 / P) + lane / P;
+  const int e = 2 * k, o = 2 * k + 1;
+  const int te = e < a.n_A ? 0 : 1, to = o < a.n_A ? 0 : 1;
+  const int c0 = tile * a.chains_per_tile;
+  const int nch = min(a.chains_per_tile, a.n_poly - c0);
+  const bool chain_ok = chain_in_tile < nch;
+  const bool he = chain_ok && e < N, ho = chain_ok && o < N;
+  const int lb = chain_in_tile * N + e;  // bead e within the tile
+  float xe = 0.f, ye = 0.f, ze = 0.f, xo = 0.f, yo = 0.f, zo = 0.f;
+  if ((N & 1) == 0) {
+    if (he) {
+      const float2 vx = lds2(st.x + lb);
+      const float2 vy = lds2(st.y + lb);
+      const float2 vz = lds2(st.z + lb);
+      xe = vx.x; xo = vx.y; ye = vy.x; yo = vy.y; ze = vz.x; zo = vz.y;
+    }
+  } else {
+    if (he) { xe = lds1(st.x + lb); ye = lds1(st.y + lb); ze = lds1(st.z + lb); }
+    if (ho) { xo = lds1(st.x + lb + 1); yo = lds1(st.y + lb + 1); zo = lds1(st.z + lb + 1); }
+  }
+  const uint32_t cid = chain_ok ? lds1(st.cid + chain_in_tile) : 0u;
+  __syncwarp();
+  if (lane == 0) mbar_arrive(empty);  // this warp is done with the stage
+
+  bool acc, acco;
+  int ce, co;
+  float wrap_e, wrap_o;
+  if (kSmart)
+    smart_pair<kFromCounts>(a, tl, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co, wrap_e,
+                            wrap_o);
+  else
+    uniform_pair<kFromCounts>(a, tl, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co,
+                              wrap_e, wrap_o);
 
   // ---- write back, images on wrap, fused histogram ----
   const int64_t gb = (int64_t)c0 * N + lb;
@@ -302,8 +459,8 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   if (acco) apply_image_steps(a.img, gb + 1, wrap_o);
   if (a.bin) {
     uint32_t* __restrict__ cnt = count_buffer(a.counts, a.n_c, tl);
-    if (he) atomicAdd(cnt + 2 * (acc ? ce1 : ce0) + te, 1u);
-    if (ho) atomicAdd(cnt + 2 * (acco ? co1 : co0) + to, 1u);
+    if (he) atomicAdd(cnt + 2 * ce + te, 1u);
+    if (ho) atomicAdd(cnt + 2 * co + to, 1u);
   }
   return (acc ? 1u : 0u) + (acco ? 1u : 0u);
 }
@@ -335,7 +492,7 @@ __device__ __forceinline__ void drain(uint64_t* full, int issued, int* err) {
 }
 
 // Register budget for 3 resident CTAs per SM (72 registers, no spill).
-template <bool kFromCounts>
+template <bool kFromCounts, bool kSmart>
 __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __grid_constant__ MoveArgs a, StepRef r) {
   __shared__ MoveStage stage[kStages];
   __shared__ __align__(8) uint64_t full[kStages];
@@ -362,7 +519,7 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __g
   for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
     const int s = it % kStages;
     if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, a.err)) break;
-    nacc += consume_tile<kFromCounts>(a, tile, stage[s], &empty[s], tl, warp, lane);
+    nacc += consume_tile<kFromCounts, kSmart>(a, tile, stage[s], &empty[s], tl, warp, lane);
   }
   nacc = __reduce_add_sync(0xffffffffu, nacc);
   if (lane == 0 && nacc) atomicAdd(a.acc + blockIdx.x, (unsigned long long)nacc);
@@ -382,6 +539,8 @@ __device__ __forceinline__ int batch_system(const BatchArgs& p, int tile) {
   return lo;
 }
 
+// One move kind per launch (the host groups systems by kind).
+template <bool kSmart>
 __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
     k_move_batch(const __grid_constant__ BatchArgs p, StepRef r) {
   __shared__ MoveStage stage[kStages];
@@ -414,8 +573,8 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
     const int sys = batch_system(p, tile);
     const MoveArgs& a = p.sys[sys];
     unsigned n = a.from_counts
-                     ? consume_tile<true>(a, tile - p.tile_start[sys], stage[s], &empty[s], tl, warp, lane)
-                     : consume_tile<false>(a, tile - p.tile_start[sys], stage[s], &empty[s], tl, warp, lane);
+                     ? consume_tile<true, kSmart>(a, tile - p.tile_start[sys], stage[s], &empty[s], tl, warp, lane)
+                     : consume_tile<false, kSmart>(a, tile - p.tile_start[sys], stage[s], &empty[s], tl, warp, lane);
     n = __reduce_add_sync(0xffffffffu, n);
     if (lane == 0 && n) atomicAdd(a.acc + blockIdx.x, (unsigned long long)n);
   }
@@ -428,7 +587,8 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
 // one another).
 int move_kernel_max_ctas_per_sm() {
   int n = 0;
-  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<true>, (kConsumerWarps + 1) * 32, 0);
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<true, false>, (kConsumerWarps + 1) * 32, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -440,21 +600,32 @@ int move_kernel_chains_per_tile(int P) { return kConsumerWarps * (32 / P); }
 
 cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s) {
   const int threads = (kConsumerWarps + 1) * 32;
-  if (from_counts)
-    k_move<true><<<grid, threads, 0, s>>>(a, r);
-  else
-    k_move<false><<<grid, threads, 0, s>>>(a, r);
+  if (a.smart) {
+    if (from_counts)
+      k_move<true, true><<<grid, threads, 0, s>>>(a, r);
+    else
+      k_move<false, true><<<grid, threads, 0, s>>>(a, r);
+  } else {
+    if (from_counts)
+      k_move<true, false><<<grid, threads, 0, s>>>(a, r);
+    else
+      k_move<false, false><<<grid, threads, 0, s>>>(a, r);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStream_t s) {
-  k_move_batch<<<grid, (kConsumerWarps + 1) * 32, 0, s>>>(p, r);
+  if (p.n_sys > 0 && p.sys[0].smart)
+    k_move_batch<true><<<grid, (kConsumerWarps + 1) * 32, 0, s>>>(p, r);
+  else
+    k_move_batch<false><<<grid, (kConsumerWarps + 1) * 32, 0, s>>>(p, r);
   return cudaGetLastError();
 }
 
 int move_batch_max_ctas_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move_batch, (kConsumerWarps + 1) * 32, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move_batch<false>, (kConsumerWarps + 1) * 32, 0) !=
+      cudaSuccess) {
     cudaGetLastError();
     return 1;
   }

@@ -28,6 +28,8 @@ SOMA_HOST = 0
 SOMA_DEVICE = 1
 SOMA_PREC_FP32 = 0
 SOMA_PREC_FP64 = 1
+SOMA_MOVE_UNIFORM = 0
+SOMA_MOVE_SMART = 1
 SOMA_HIST_AUTO = 0
 SOMA_HIST_FUSED = 1
 SOMA_HIST_SEPARATE = 2
@@ -52,7 +54,7 @@ class SomaError(RuntimeError):
 class soma_system_desc(ctypes.Structure):
     _fields_ = [
         ("n_poly", ctypes.c_int32), ("N", ctypes.c_int32), ("n_A", ctypes.c_int32),
-        ("system_id", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("reserved1", ctypes.c_int32),
+        ("system_id", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("move", ctypes.c_int32),
         ("box", ctypes.c_double * 3), ("chiN", ctypes.c_double), ("kappaN", ctypes.c_double),
         ("A", ctypes.c_double), ("seed", ctypes.c_uint64),
     ]
@@ -210,9 +212,11 @@ def soma_sync(h, stream=None):
 class System:
     """One AB diblock melt (the fields of soma_system_desc)."""
 
-    def __init__(self, n_poly, N, n_A, box, grid, chiN, kappaN, A=0.0, seed=1, system_id=0):
+    def __init__(self, n_poly, N, n_A, box, grid, chiN, kappaN, A=0.0, seed=1, system_id=0,
+                 move=SOMA_MOVE_UNIFORM):
         self.n_poly, self.N, self.n_A = int(n_poly), int(N), int(n_A)
         self.system_id = int(system_id)
+        self.move = int(move)
         self.box = tuple(float(b) for b in box)
         self.grid = tuple(int(g) for g in grid)
         self.chiN, self.kappaN, self.A, self.seed = float(chiN), float(kappaN), float(A), int(seed)
@@ -228,6 +232,7 @@ class System:
     def desc(self):
         d = soma_system_desc()
         d.n_poly, d.N, d.n_A, d.system_id = self.n_poly, self.N, self.n_A, self.system_id
+        d.move = self.move
         for a in range(3):
             d.grid[a] = self.grid[a]
             d.box[a] = self.box[a]

@@ -18,7 +18,7 @@ def lib():
 
 def oracle_for(system):
     return Oracle(system.n_poly, system.N, system.n_A, system.box, system.grid, system.chiN, system.kappaN,
-                  A=system.A, seed=system.seed, sys_index=system.system_id)
+                  A=system.A, seed=system.seed, sys_index=system.system_id, move=system.move)
 
 
 def unwrapped(h, sys=0):
