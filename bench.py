@@ -58,10 +58,10 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(workload):
+def _profiled_traffic(workload, variant=""):
     """DRAM bytes per launch of the move kernel from the committed ncu summary,
     if that summary was taken from the current kernel source."""
-    path = os.path.join(ROOT, "profiles", f"k_move_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"k_move{variant}_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -403,8 +403,8 @@ def run_gpu(args):
     # headline (L2 flushed between steps, CUDA events around each step)
     smart = None
     if not args.no_smart:
-        smart = bench_smart(soma, torch, rank_system_kwargs(args.workload, rank), local, sptr, stream, flush,
-                            args.steps, args.warmup, hbm_peak, n_b, n_c)
+        smart = bench_smart(soma, torch, args.workload, rank_system_kwargs(args.workload, rank), local, sptr, stream,
+                            flush, args.steps, args.warmup, hbm_peak, n_b, n_c)
 
     # batched replicas vs sequential plain runs of the same 64 systems
     batched = None
@@ -431,7 +431,7 @@ def run_gpu(args):
         pg.destroy_process_group()
 
 
-def bench_smart(soma, torch, kw, device, sptr, stream, flush, steps, warmup, hbm_peak, n_b, n_c):
+def bench_smart(soma, torch, workload, kw, device, sptr, stream, flush, steps, warmup, hbm_peak, n_b, n_c):
     """The workload with bond-force-biased trial moves: moves/s over flushed
     steps and the move kernel's fraction of the HBM roofline (same
     algorithmic bytes as the uniform move)."""
@@ -460,6 +460,7 @@ def bench_smart(soma, torch, kw, device, sptr, stream, flush, steps, warmup, hbm
     achieved = move_kernel_bytes(n_b, n_c) / (move_avg * 1e-3) / 1e9
     return {"value": steps * n_b / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / steps,
             "move_ms": move_avg, "achieved_gbs": achieved, "frac": achieved / hbm_peak, "acceptance": acc,
+            "traffic": _profiled_traffic(workload, "_smart"),
             "note": "SOMA_MOVE_SMART, same workload, L2 flushed between timed steps"}
 
 
