@@ -94,8 +94,13 @@ class Oracle:
             L.orc_mc_step_chains.restype = ctypes.c_int64
             L.orc_observables.argtypes = [dp, f64p, ctypes.POINTER(OrcObs)]
             L.orc_structure_factor.argtypes = [dp, f64p, ctypes.c_int, i32p, f64p]
-            L.orc_run.argtypes = [dp, f64p, ctypes.c_uint32, ctypes.c_int64, f64p, ctypes.c_int,
-                                  u64p, u64p, f64p, i64p]
+            L.orc_run.argtypes = [dp, f64p, ctypes.c_uint32, ctypes.c_int64, f64p, f64p, ctypes.c_double,
+                                  ctypes.c_int, u64p, u64p, f64p, i64p]
+            L.orc_energy_umbrella.argtypes = [dp, u32p, f64p, ctypes.c_double]
+            L.orc_energy_umbrella.restype = ctypes.c_double
+            L.orc_fields_umbrella.argtypes = [dp, u32p, f64p, ctypes.c_double, f64p]
+            L.orc_place.argtypes = [dp, ctypes.POINTER(ctypes.c_float), f64p]
+            L.orc_place.restype = ctypes.c_int
             L.orc_run.restype = ctypes.c_int64
             cls._lib = L
         return cls._lib
@@ -145,6 +150,29 @@ class Oracle:
         self.lib().orc_fields_from_phi(ctypes.byref(self.d), _p(phi, ctypes.c_double), _p(w, ctypes.c_double))
         return w
 
+    def energy_umbrella(self, counts, target, lambdaN):
+        counts = np.ascontiguousarray(counts, np.uint32)
+        target = np.ascontiguousarray(target, np.float64)
+        return float(self.lib().orc_energy_umbrella(ctypes.byref(self.d), _p(counts, ctypes.c_uint32),
+                                                    _p(target, ctypes.c_double), float(lambdaN)))
+
+    def fields_umbrella(self, counts, target, lambdaN):
+        counts = np.ascontiguousarray(counts, np.uint32)
+        target = np.ascontiguousarray(target, np.float64)
+        w = np.zeros((2, self.n_c), np.float64)
+        self.lib().orc_fields_umbrella(ctypes.byref(self.d), _p(counts, ctypes.c_uint32),
+                                       _p(target, ctypes.c_double), float(lambdaN), _p(w, ctypes.c_double))
+        return w
+
+    def place(self, target):
+        """Positions [n_b, 3] of molecules placed from float32 target volume
+        fractions [2, n_c]; raises ValueError when bead 0's type has no weight."""
+        target = np.ascontiguousarray(target, np.float32)
+        pos = np.zeros((self.n_b, 3), np.float64)
+        if self.lib().orc_place(ctypes.byref(self.d), _p(target, ctypes.c_float), _p(pos, ctypes.c_double)):
+            raise ValueError("target weights of bead 0's type sum to zero")
+        return pos
+
     def cell_index(self, r):
         r = np.ascontiguousarray(r, np.float64)
         return int(self.lib().orc_cell_index(ctypes.byref(self.d), _p(r, ctypes.c_double)))
@@ -177,15 +205,17 @@ class Oracle:
         return n, acc, margin, face
 
     def run(self, pos, t0, n_steps, w_frozen=None, n_threads=1, occ=False, pair_hist=False,
-            re2_trace=False, acc_trace=False):
+            re2_trace=False, acc_trace=False, target=None, lambdaN=0.0):
         assert pos.dtype == np.float64 and pos.flags.c_contiguous
         wf = np.ascontiguousarray(w_frozen, np.float64) if w_frozen is not None else None
+        tg = np.ascontiguousarray(target, np.float64) if target is not None else None
         o = np.zeros(2 * self.n_c, np.uint64) if occ else None
         ph = np.zeros(self.n_c * self.n_c, np.uint64) if pair_hist else None
         rt = np.zeros(n_steps, np.float64) if re2_trace else None
         at = np.zeros(n_steps, np.int64) if acc_trace else None
         total = self.lib().orc_run(ctypes.byref(self.d), _p(pos, ctypes.c_double), ctypes.c_uint32(t0),
-                                   n_steps, _p(wf, ctypes.c_double), n_threads, _p(o, ctypes.c_uint64),
+                                   n_steps, _p(wf, ctypes.c_double), _p(tg, ctypes.c_double),
+                                   float(lambdaN), n_threads, _p(o, ctypes.c_uint64),
                                    _p(ph, ctypes.c_uint64), _p(rt, ctypes.c_double), _p(at, ctypes.c_int64))
         return dict(accepted=total, occ=o, pair_hist=ph, re2=rt, acc=at)
 

@@ -35,6 +35,10 @@
 //   force-biased moves    pinned: the same Gaussian-chain statistics, the
 //                         one-bead Boltzmann law and the dimer cell-pair law
 //                         (detailed balance makes them stationary).
+//   orc_fields_umbrella   pinned: central difference of H_nb + H_umb.
+//   orc_place             pinned: the exact law of the bead-0 cell (target
+//                         weights convolved with the uniform offset) and the
+//                         Gaussian bond statistics of the placed chains.
 //   The chiN, kappaN > 0 statistics of a dense melt have no closed form:
 //   parity unpinned there except against this oracle itself.
 #include <cmath>
@@ -275,6 +279,102 @@ void orc_fields_from_phi(const orc_desc* d, const double* phi, double* w) {
 }
 
 // ---------------------------------------------------------------------------
+// Umbrella potential toward target volume fractions phi*_t(c) (the coupling
+// of Sec. 3.2 equilibrates freshly placed molecules under an umbrella
+// potential toward the supplied concentration fields).
+// Reading: a harmonic restraint on every cell and type in the units of the
+// compressibility term, with strength lambdaN >= 0,
+//   H_umb = (rho_bar/N) (lambdaN/2) sum_c sum_t (phi_t(c) - phi*_t(c))^2,
+// so the field it adds for a bead of type t in cell c is dH_umb/dn_t(c):
+//   w_t^umb(c) = lambdaN (phi_t(c) - phi*_t(c)) / N.
+// target is [type][cell].
+// ---------------------------------------------------------------------------
+double orc_energy_umbrella(const orc_desc* d, const uint32_t* counts, const double* target, double lambdaN) {
+  const int64_t nc = n_cells(d);
+  const double rho_bar = (double)n_beads(d) / (double)nc;
+  double sum = 0.0;
+  for (int64_t c = 0; c < 2 * nc; ++c) {
+    const double dev = counts[c] / rho_bar - target[c];
+    sum += dev * dev;
+  }
+  return rho_bar / (double)d->N * 0.5 * lambdaN * sum;
+}
+
+// The full fields with the umbrella term: w = w_nb + w^umb.
+void orc_fields_umbrella(const orc_desc* d, const uint32_t* counts, const double* target, double lambdaN,
+                         double* w) {
+  const int64_t nc = n_cells(d);
+  const double rho_bar = (double)n_beads(d) / (double)nc;
+  orc_fields(d, counts, w);
+  if (target)
+    for (int64_t c = 0; c < 2 * nc; ++c) w[c] += lambdaN * (counts[c] / rho_bar - target[c]) / (double)d->N;
+}
+
+// ---------------------------------------------------------------------------
+// Placement of molecules from target concentration fields (Sec. 3.2: a
+// particle run starts from positions that reproduce the supplied fields,
+// each molecule within half a mean end-to-end distance of its target).
+// Reading: the target position of chain c is a point drawn from the target
+// volume fraction of its bead-0 type, and bead 0 is put there plus a
+// displacement uniform in [-h, h)^3 with h = 1/(2 sqrt 3), so |offset| <= 1/2;
+// the chain keeps the Gaussian conformation of the initial configuration
+// (the same bond draws), translated.  The target cell is chosen exactly:
+// weights q(c) = floor(phi*(c) 2^16) (0 where phi* <= 0 or NaN; at most
+// 2^32 - 256), running sums P(c) in 64-bit integers, k = floor(r Q / 2^64)
+// with r = (w1 << 32 | w0) from counter (0, c, 0xFFFFFFFE, s) and Q the
+// total; the cell is the first with P(c) > k.  Within the cell the point is
+// (i_a + U(word a)) L_a/n_a from counter (1, c, 0xFFFFFFFE, s), and the
+// offset is h (2 U(word a) - 1) from counter (2, c, 0xFFFFFFFE, s).
+// target is the float32 [type][cell] array.  Returns 0, or -1 when the
+// weights of bead 0's type sum to zero.
+// ---------------------------------------------------------------------------
+static uint32_t place_weight(float phi) {
+  if (!(phi > 0.0f)) return 0u;
+  const float v = std::fmin(phi * 65536.0f, 4294967040.0f);
+  return (uint32_t)v;
+}
+
+int orc_place(const orc_desc* d, const float* target, double* pos) {
+  const int64_t nc = n_cells(d);
+  const float* phi = target + (int64_t)type_of(d, 0) * nc;
+  std::vector<uint64_t> P(nc);
+  uint64_t Q = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    Q += place_weight(phi[c]);
+    P[c] = Q;
+  }
+  if (Q == 0) return -1;
+  orc_init(d, pos);  // conformations (bead 0 is replaced below)
+  const double h = 0.5 / std::sqrt(3.0);
+  for (int c = 0; c < d->n_poly; ++c) {
+    uint32_t r0[4], r1[4], r2[4];
+    draw(d, 0u, (uint32_t)c, 0xFFFFFFFEu, r0);
+    draw(d, 1u, (uint32_t)c, 0xFFFFFFFEu, r1);
+    draw(d, 2u, (uint32_t)c, 0xFFFFFFFEu, r2);
+    const uint64_t r = ((uint64_t)r0[1] << 32) | r0[0];
+    const uint64_t k = (uint64_t)(((unsigned __int128)r * Q) >> 64);
+    int64_t lo = 0, hi = nc - 1;  // first cell with P > k
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (P[mid] > k) hi = mid; else lo = mid + 1;
+    }
+    const int64_t cell = lo;
+    const int64_t idx[3] = {cell / ((int64_t)d->grid[1] * d->grid[2]), (cell / d->grid[2]) % d->grid[1],
+                            cell % d->grid[2]};
+    double* p = pos + (int64_t)c * d->N * 3;
+    double shift[3];
+    for (int a = 0; a < 3; ++a) {
+      const double x0 = ((double)idx[a] + unit_closed_open(r1[a])) * d->box[a] / d->grid[a] +
+                        h * (2.0 * unit_closed_open(r2[a]) - 1.0);
+      shift[a] = x0 - p[a];
+    }
+    for (int i = 0; i < d->N; ++i)
+      for (int a = 0; a < 3; ++a) p[3 * i + a] += shift[a];
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
 // One Monte Carlo step t with frozen fields w.
 // Reading: the beads of a linear chain split into two sets, even i and odd
 // i, that share no bond; set 0 (even) moves first for every chain, then set
@@ -457,13 +557,13 @@ void orc_structure_factor(const orc_desc* d, const double* pos, int nq, const in
 // ---------------------------------------------------------------------------
 // A run of n_steps steps starting at step t0.  Unless w_frozen is given, the
 // fields entering step t come from the counts after step t-1 (or after the
-// initial configuration).  Optional accumulators per step: occupancy counts
+// initial configuration), with the umbrella term when target is given.  Optional accumulators per step: occupancy counts
 // summed over steps, the joint cell histogram of two-bead chains, R_e^2 and
 // the accepted count.  Returns the total accepted count.
 // ---------------------------------------------------------------------------
 int64_t orc_run(const orc_desc* d, double* pos, uint32_t t0, int64_t n_steps,
-                const double* w_frozen, int n_threads, uint64_t* occ, uint64_t* pair_hist,
-                double* re2_trace, int64_t* acc_trace) {
+                const double* w_frozen, const double* target, double lambdaN, int n_threads, uint64_t* occ,
+                uint64_t* pair_hist, double* re2_trace, int64_t* acc_trace) {
   const int64_t nc = n_cells(d);
   std::vector<uint32_t> counts(2 * nc);
   std::vector<double> w(2 * nc);
@@ -471,7 +571,7 @@ int64_t orc_run(const orc_desc* d, double* pos, uint32_t t0, int64_t n_steps,
     std::memcpy(w.data(), w_frozen, sizeof(double) * 2 * nc);
   } else {
     orc_density(d, pos, counts.data());
-    orc_fields(d, counts.data(), w.data());
+    orc_fields_umbrella(d, counts.data(), target, lambdaN, w.data());
   }
   int64_t total = 0;
   for (int64_t s = 0; s < n_steps; ++s) {
@@ -480,7 +580,7 @@ int64_t orc_run(const orc_desc* d, double* pos, uint32_t t0, int64_t n_steps,
     total += a;
     if (acc_trace) acc_trace[s] = a;
     if (!w_frozen || occ) orc_density(d, pos, counts.data());
-    if (!w_frozen) orc_fields(d, counts.data(), w.data());
+    if (!w_frozen) orc_fields_umbrella(d, counts.data(), target, lambdaN, w.data());
     if (occ)
       for (int64_t c = 0; c < 2 * nc; ++c) occ[c] += counts[c];
     if (pair_hist && d->N == 2)

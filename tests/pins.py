@@ -20,6 +20,11 @@ list means the pin holds.  The facts used:
 * Fields: the exact central difference of the energy functional H_nb, and the
   exchange field chiN (phiB - phiA)/N of an incompressible cell.
 * S(q) of ideal chains: (1/N) sum_ij s_i s_j exp(-q^2 |i-j| / (6(N-1))).
+* Umbrella fields: the exact central difference of H_nb + H_umb.
+* Placement from target fields: the exact law of the bead-0 cell, the
+  quantised target weights convolved with the uniform offset (piecewise-
+  linear integrals, integrated exactly between their kinks), and Gaussian
+  bond statistics of the placed chains.
 """
 import os
 import subprocess
@@ -340,6 +345,106 @@ def pin_normal_quantile(O):
     return fails
 
 
+# ---------------------------------------------------------------------------
+def pin_umbrella_fields_derivative(O):
+    fails = []
+    rng = np.random.default_rng(43)
+    o = O(64, 16, 5, (2.0, 2.0, 2.0), (4, 4, 4), 23.0, 47.0, seed=1)
+    counts = rng.integers(1, 40, size=(2, o.n_c)).astype(np.uint32)
+    target = rng.uniform(0.0, 2.0, size=(2, o.n_c))
+    lam = 31.0
+    w = o.fields_umbrella(counts, target, lam)
+
+    def H(n):
+        return o.energy_nb(n) + o.energy_umbrella(n, target, lam)
+
+    for t in range(2):
+        for c in rng.choice(o.n_c, 12, replace=False):
+            up, dn = counts.copy(), counts.copy()
+            up[t, c] += 1
+            dn[t, c] -= 1
+            fd = (H(up) - H(dn)) / 2.0
+            _check(fails, f"umbrella w[{t},{c}] vs dH/dn", w[t, c], fd, 1e-9 * max(1.0, abs(fd)) + 1e-9)
+    # at the target itself the restraint adds nothing
+    _, _, rho = o.params()
+    at = counts / rho
+    _check(fails, "umbrella vanishes at the target", float(np.abs(o.fields_umbrella(counts, at, lam) -
+                                                                  o.fields(counts)).max()), 0.0, 1e-12)
+    return fails
+
+
+def _offset_kernel(L, n, h, gl=4):
+    """K[i, j] = P(cell of (i + U) L/n + h (2 U' - 1), periodic, is j)."""
+    D = L / n
+    x, wq = leggauss(gl)
+
+    def overlap(xs, j):
+        tot = np.zeros_like(xs)
+        for m in range(-3, 4):
+            a, b = j * D + m * L, (j + 1) * D + m * L
+            tot += np.clip(np.minimum(xs + h, b) - np.maximum(xs - h, a), 0.0, None)
+        return tot / (2 * h)
+
+    K = np.zeros((n, n))
+    for i in range(n):
+        lo, hi = i * D, (i + 1) * D
+        kinks = [lo, hi]
+        for j in range(n + 1):
+            for m in range(-3, 4):
+                for sgn in (-1, 1):
+                    k = j * D + m * L + sgn * h
+                    if lo < k < hi:
+                        kinks.append(k)
+        kinks = np.unique(kinks)
+        for a, b in zip(kinks[:-1], kinks[1:]):
+            xs = 0.5 * (b - a) * x + 0.5 * (a + b)
+            for j in range(n):
+                K[i, j] += 0.5 * (b - a) * (wq * overlap(xs, j)).sum() / D
+    return K
+
+
+def pin_place_bead0_law(O):
+    fails = []
+    rng = np.random.default_rng(47)
+    box, grid = (1.0, 0.75, 2.0), (4, 3, 5)
+    n_poly = 300000
+    o = O(n_poly, 1, 1, box, grid, 0.0, 0.0, A=0.2, seed=29)
+    target = rng.uniform(0.0, 1.0, size=(2, o.n_c)).astype(np.float32)
+    target[0, rng.choice(o.n_c, 7, replace=False)] = 0.0
+    target[0, 3] = -0.5  # negative volume fractions carry no weight
+    pos = o.place(target)
+    q = np.where(target[0] > 0, np.floor(target[0].astype(np.float64) * 65536.0), 0.0)
+    p0 = (q / q.sum()).reshape(grid)
+    h = 0.5 / np.sqrt(3.0)
+    Ks = [_offset_kernel(box[a], grid[a], h) for a in range(3)]
+    P = np.einsum("abc,ai,bj,ck->ijk", p0, Ks[0], Ks[1], Ks[2]).reshape(-1)
+    cells = np.array([o.cell_index(pos[k]) for k in range(0, n_poly)])
+    cnt = np.bincount(cells, minlength=o.n_c)
+    z = (cnt - n_poly * P) / np.sqrt(n_poly * P * (1 - P) + 1e-12)
+    k = int(np.argmax(np.abs(z)))
+    if abs(z[k]) > 5.0:
+        fails.append(f"placed bead-0 cell {k}: {cnt[k]} vs exact {n_poly * P[k]:.1f} (z={z[k]:.1f})")
+    _check(fails, "kernel rows sum to one", float(np.abs(Ks[2].sum(1) - 1).max()), 0.0, 1e-12)
+    return fails
+
+
+def pin_place_bond_statistics(O):
+    fails = []
+    rng = np.random.default_rng(53)
+    n_poly, N = 8192, 16
+    o = O(n_poly, N, 8, (4.0, 4.0, 4.0), (16, 16, 16), 0.0, 0.0, seed=31)
+    target = rng.uniform(0.0, 1.0, size=(2, o.n_c)).astype(np.float32)
+    pos = o.place(target).reshape(n_poly, N, 3)
+    b = np.diff(pos, axis=1)
+    nb = b.shape[0] * b.shape[1]
+    for a in range(3):
+        v = (b[:, :, a] ** 2).mean() * 3 * (N - 1)
+        _check(fails, f"placed bond variance axis {a} x 3(N-1)", v, 1.0, 5 * np.sqrt(2.0 / nb))
+    re2 = ((pos[:, -1] - pos[:, 0]) ** 2).sum(-1)
+    _check(fails, "placed <R_e^2>", re2.mean(), 1.0, 5 * np.sqrt(2.0 / 3.0 / n_poly))
+    return fails
+
+
 ALL_PINS = {
     "philox_triton": pin_philox_triton,
     "init_statistics": pin_init_statistics,
@@ -353,4 +458,7 @@ ALL_PINS = {
     "smart_single_bead_field": pin_smart_single_bead_field,
     "smart_dimer_cell_pairs": pin_smart_dimer_cell_pairs,
     "normal_quantile": pin_normal_quantile,
+    "umbrella_fields_derivative": pin_umbrella_fields_derivative,
+    "place_bead0_law": pin_place_bead0_law,
+    "place_bond_statistics": pin_place_bond_statistics,
 }

@@ -48,6 +48,20 @@ MUTATIONS = [
     ("normal quantile Newton step sign", "x -= f / dens;", "x += f / dens;", "normal_quantile"),
     ("force-bias normals from the wrong word", "normal_quantile(unit_open24(r[a]))",
      "normal_quantile(unit_open24(r[0]))", "smart_ideal_dynamics"),
+    ("umbrella field doubled", "w[c] += lambdaN * (counts[c] / rho_bar - target[c]) / (double)d->N;",
+     "w[c] += 2.0 * lambdaN * (counts[c] / rho_bar - target[c]) / (double)d->N;", "umbrella_fields_derivative"),
+    ("umbrella field sign", "w[c] += lambdaN * (counts[c] / rho_bar - target[c]) / (double)d->N;",
+     "w[c] += lambdaN * (target[c] - counts[c] / rho_bar) / (double)d->N;", "umbrella_fields_derivative"),
+    ("placement offset dropped", "h * (2.0 * unit_closed_open(r2[a]) - 1.0);", "0.0;", "place_bead0_law"),
+    ("placement offset width R_e/2 per axis", "const double h = 0.5 / std::sqrt(3.0);", "const double h = 0.5;",
+     "place_bead0_law"),
+    ("placement cell axes transposed",
+     "const int64_t idx[3] = {cell / ((int64_t)d->grid[1] * d->grid[2]), (cell / d->grid[2]) % d->grid[1],\n"
+     "                            cell % d->grid[2]};",
+     "const int64_t idx[3] = {cell % d->grid[0], (cell / d->grid[0]) % d->grid[1],\n"
+     "                            cell / ((int64_t)d->grid[0] * d->grid[1])};", "place_bead0_law"),
+    ("placement weights of the other type", "const float* phi = target + (int64_t)type_of(d, 0) * nc;",
+     "const float* phi = target + (int64_t)(1 - type_of(d, 0)) * nc;", "place_bead0_law"),
 ]
 
 
