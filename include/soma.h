@@ -176,6 +176,34 @@ int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where);
  * (Sec. 3.2: the particle run is handed the continuum's concentrations.) */
 int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int where);
 
+/* Coupling start-up (Sec. 3.2: molecules placed from the supplied
+ * concentration fields are equilibrated under an umbrella potential).
+ * Turn on a harmonic restraint toward target volume fractions
+ * phi_target [2][n_cells] (FP32, host or device per `where`; copied):
+ *   H_umb = (rho_bar/N) (lambdaN/2) sum_c sum_t (phi_t(c) - phi_target_t(c))^2,
+ * which adds lambdaN (phi_t(c) - phi_target_t(c)) / N to the field of a
+ * type-t bead in cell c from the next step on.  phi_target == NULL or
+ * lambdaN == 0 turns it off.  lambdaN must be finite and >= 0
+ * (SOMA_EINVAL); n must be 2 n_cells when on (SOMA_EINVAL); target values
+ * are not checked.  While on, each step fills the field array from the
+ * previous counts before the move kernel (one more launch per step).
+ * soma_observables' Enb excludes the restraint.  SOMA_ENOTSUP on
+ * SOMA_PREC_FP64 handles.  Synchronises. */
+int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n, double lambdaN, int where);
+
+/* Coupling start-up: replace system `sys`'s configuration by molecules
+ * placed from target volume fractions phi_target [2][n_cells] (FP32, host
+ * or device; not retained).  Chain c's bead 0 goes to a point drawn from
+ * the target of bead 0's type (cell weights floor(phi 2^16), 0 where
+ * phi <= 0 or NaN) plus an offset uniform in [-h, h)^3, h = 1/(2 sqrt 3),
+ * so within R_e/2 of it (Sec. 3.2); the chain keeps the Gaussian
+ * conformation of the initial configuration.  Random numbers: Philox
+ * counters (j, c, 0xFFFFFFFE, system_id), j = 0, 1, 2.  The step counter is
+ * kept; counts, fields and acceptance counters restart from the new state.
+ * SOMA_EINVAL (state kept) when the weights of bead 0's type sum to zero or
+ * n != 2 n_cells; SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises. */
+int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int where);
+
 /* Test mode: hold the fields at w [2][n_cells] (FP32) for every later step
  * (w == NULL releases them and rebuilds from the current counts). */
 int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int where);

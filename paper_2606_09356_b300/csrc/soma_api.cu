@@ -79,6 +79,8 @@ struct soma_handle {
   float* d_stage_pos = nullptr;
   int16_t* d_stage_img = nullptr;
   float* d_stage_phi = nullptr;
+  void* place_temp = nullptr;  // CUB scan scratch of soma_place (allocated on first use)
+  size_t place_temp_bytes = 0;
   int64_t max_nb = 0, max_nc = 0;
   SortWork sort{};
   // graph
@@ -237,7 +239,7 @@ void build_args(soma_handle* h) {
     a.inv_rho = S.inv_rho;
     a.chiN_N = S.chiN_N;
     a.kappaN_N = S.kappaN_N;
-    a.from_counts = S.frozen ? 0 : 1;
+    a.from_counts = (S.frozen || S.umbrella) ? 0 : 1;
     a.acc = h->d_acc + S.acc_first;
     a.err = h->d_err;
     a.smart = h->desc[s].move == SOMA_MOVE_SMART ? 1 : 0;
@@ -258,6 +260,9 @@ void build_args(soma_handle* h) {
     f.chiN_N = S.chiN_N;
     f.kappaN_N = S.kappaN_N;
     f.frozen = S.frozen;
+    f.target = S.phi_target;
+    f.umbN_N = S.umbN_N;
+    f.umbrella = S.umbrella;
   }
   // batched launches: register-path systems in groups of at most kMaxBatch
   h->batches.clear();
@@ -335,6 +340,21 @@ int enqueue_aux(soma_handle* h, cudaStream_t s, int sys, StepRef r, bool timing,
   return SOMA_OK;
 }
 
+// With the umbrella restraint on, the register move reads the field array,
+// filled before each step from the previous step's counts (the restraint's
+// target term is not folded into the move kernel).  Not for held fields or
+// a step whose fields came from soma_set_density.
+int enqueue_umbrella_fields(soma_handle* h, cudaStream_t s, int sys, bool graph, long long t0, int i) {
+  const SysDev& S = h->host_sys[sys];
+  if (!S.P || !S.umbrella || S.frozen || (i == 0 && h->phi_pending[sys])) return SOMA_OK;
+  TimedEvent te;
+  const bool timing = h->opt.kernel_timing != 0;
+  if (timing) begin_timed(h, s, te, T_FIELD);
+  CK(launch_field(h->fargs[sys], step_ref(h, sys, graph, t0, i - 1), 0, s));
+  if (timing) end_timed(h, s, te);
+  return SOMA_OK;
+}
+
 // n steps of every system on stream `s`.  One system: one move kernel per
 // step (fields from the previous counts, fused histogram, clearing of the
 // next count buffer).  Several systems: one k_move_batch launch per step and
@@ -360,6 +380,8 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
           }
         }
         TimedEvent te;
+        for (int m = 0; m < b->n_sys; ++m)
+          if ((rc = enqueue_umbrella_fields(h, s, h->batch_members[g][m], graph, t0, i))) return rc;
         if (timing) begin_timed(h, s, te, T_MOVE);
         CK(launch_move_batch(*b, move_grid(h, b->tile_start[b->n_sys], h->max_ctas_batch),
                              step_ref(h, 0, graph, t0, i), s));
@@ -376,7 +398,8 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
       const SysDev& S = h->host_sys[0];
       const StepRef r = step_ref(h, 0, graph, t0, i);
       if (S.P) {
-        const bool from_counts = !S.frozen && !(i == 0 && h->phi_pending[0]);
+        const bool from_counts = !S.frozen && !S.umbrella && !(i == 0 && h->phi_pending[0]);
+        if ((rc = enqueue_umbrella_fields(h, s, 0, graph, t0, i))) return rc;
         TimedEvent te;
         if (timing) begin_timed(h, s, te, T_MOVE);
         CK(launch_move(h->margs[0], move_grid(h, h->n_tiles[0], h->max_ctas_per_sm), from_counts, r, s));
@@ -1006,6 +1029,76 @@ int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz,
   const double nb = (double)h->host_sys[sys].n_b;
   for (int q = 0; q < nq; ++q) S_out[q] = (acc[2 * q] * acc[2 * q] + acc[2 * q + 1] * acc[2 * q + 1]) / nb;
   return SOMA_OK;
+}
+
+int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n, double lambdaN, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (h->f64) return SOMA_ENOTSUP;
+  if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
+  if (!std::isfinite(lambdaN) || lambdaN < 0.0) return SOMA_EINVAL;
+  SysDev& S = h->host_sys[sys];
+  const bool on = phi_target != nullptr && lambdaN > 0.0;
+  if (on && n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
+  if ((rc = sync_all(h))) return rc;
+  if (on) {
+    if (!S.phi_target) {
+      S.phi_target = (float*)dev_alloc(h, sizeof(float) * 2 * (size_t)S.n_c);
+      if (!S.phi_target) return SOMA_ENOMEM;
+    }
+    CK(cudaMemcpy(S.phi_target, phi_target, sizeof(float) * n,
+                  where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    S.umbN_N = (float)(lambdaN / S.N);
+    S.umbrella = 1;
+  } else {
+    S.umbN_N = 0.f;
+    S.umbrella = 0;
+  }
+  CK(cudaMemcpy(h->d_sys + sys, &S, sizeof(SysDev), cudaMemcpyHostToDevice));
+  build_args(h);
+  drop_graph(h);
+  // the field array (read by the generic move and by the next step when the
+  // restraint is on) follows the new functional at once
+  if (h->phi_pending[sys])
+    CK(launch_field_from_phi(h->d_sys, sys, h->d_stage_phi + 0, h->sm_count, h->stream));
+  else if (!S.frozen)
+    CK(launch_field(h->fargs[sys], fixed_step((long long)h->step - 1), 0, h->stream));
+  return sync_all(h);
+}
+
+int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int where) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (h->f64) return SOMA_ENOTSUP;
+  if (sys < 0 || sys >= h->n_sys || !phi_target) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
+  if ((rc = sync_all(h))) return rc;
+  if (!h->place_temp) {
+    h->place_temp_bytes = place_temp_bytes(h->max_nc);
+    h->place_temp = dev_alloc(h, h->place_temp_bytes);
+    if (!h->place_temp) return SOMA_ENOMEM;
+  }
+  CK(cudaMemcpy(h->d_stage_phi, phi_target, sizeof(float) * n,
+                where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  // the count buffers (24 bytes per cell) serve as the weights' scratch; the
+  // counts are rebuilt below either way
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(S.counts);
+  unsigned long long total = 0;
+  CK(launch_place(h->d_sys, sys, S, h->d_stage_phi, q, q + S.n_c, h->place_temp, h->place_temp_bytes, &total,
+                  h->sm_count, h->stream));
+  if (total == 0) {
+    if ((rc = rebin_all(h, h->stream))) return rc;
+    if ((rc = sync_all(h))) return rc;
+    return SOMA_EINVAL;  // no weight for bead 0's type: nothing placed
+  }
+  h->acc_since = h->step;
+  CK(cudaMemsetAsync(h->d_acc, 0, sizeof(unsigned long long) * (size_t)h->acc_per_sys * h->n_sys, h->stream));
+  std::fill(h->phi_pending.begin(), h->phi_pending.end(), 0);
+  if ((rc = rebin_all(h, h->stream))) return rc;
+  // placement leaves the chains in logical order: restore the cell order
+  if (h->sort_interval > 0 && (rc = enqueue_reorder(h, h->stream))) return rc;
+  return sync_all(h);
 }
 
 int soma_reorder(soma_handle* h, void* stream) {

@@ -42,6 +42,11 @@ struct alignas(16) SysDev {
   double L64[3];
   double invL64[3], cps64[3];  // 1/L and n/L in FP64
   double chiN64, kappaN64;
+  // umbrella restraint toward target volume fractions (coupling start-up):
+  // w_t += umbN_N (phi_t - phi*_t) with umbN_N = lambdaN / N
+  float* phi_target;            // [2 types][n_c], allocated on first use
+  float umbN_N;
+  int32_t umbrella;             // 1: the restraint is on
 };
 
 // Everything the move kernel needs for one system, passed by value as a
@@ -105,6 +110,9 @@ struct FieldArgs {
   int64_t n_c;
   float inv_rho, chiN_N, kappaN_N;
   int32_t frozen;
+  const float* target;       // [2 types][n_c] umbrella target (read when umbrella = 1)
+  float umbN_N;
+  int32_t umbrella;
 };
 
 // Count buffers: three per system, each [n_c][2] (the two types of a cell

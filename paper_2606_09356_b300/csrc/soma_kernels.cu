@@ -15,6 +15,9 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include <algorithm>
+#include <cub/device/device_scan.cuh>
+
 #include "soma_device.cuh"
 #include "soma_internal.cuh"
 #include "soma_launch.h"
@@ -90,6 +93,13 @@ __device__ __forceinline__ void field_pair(const FieldArgs& f, uint32_t nA, uint
   wB = fmaf(f.chiN_N, pA, ex);
 }
 
+// The umbrella restraint's share, umbN_N (phi_t - phi*_t), of a cell's fields.
+__device__ __forceinline__ void umbrella_pair(const FieldArgs& f, uint32_t nA, uint32_t nB, float tA, float tB,
+                                              float& wA, float& wB) {
+  wA = fmaf(f.umbN_N, fmaf((float)nA, f.inv_rho, -tA), wA);
+  wB = fmaf(f.umbN_N, fmaf((float)nB, f.inv_rho, -tB), wB);
+}
+
 __global__ void __launch_bounds__(256) k_field(const __grid_constant__ FieldArgs f, StepRef r, int zero_next) {
   const long long t = r.get();
   const int64_t nc = f.n_c;
@@ -109,6 +119,12 @@ __global__ void __launch_bounds__(256) k_field(const __grid_constant__ FieldArgs
         float2 wa, wb;
         field_pair(f, c.x, c.y, wa.x, wb.x);
         field_pair(f, c.z, c.w, wa.y, wb.y);
+        if (f.umbrella) {
+          const float2 ta = __ldg(reinterpret_cast<const float2*>(f.target) + i);
+          const float2 tb = __ldg(reinterpret_cast<const float2*>(f.target + nc) + i);
+          umbrella_pair(f, c.x, c.y, ta.x, tb.x, wa.x, wb.x);
+          umbrella_pair(f, c.z, c.w, ta.y, tb.y, wa.y, wb.y);
+        }
         wa2[i] = wa;
         wb2[i] = wb;
       }
@@ -119,6 +135,7 @@ __global__ void __launch_bounds__(256) k_field(const __grid_constant__ FieldArgs
       if (!f.frozen) {
         float wa, wb;
         field_pair(f, cur[2 * c], cur[2 * c + 1], wa, wb);
+        if (f.umbrella) umbrella_pair(f, cur[2 * c], cur[2 * c + 1], f.target[c], f.target[nc + c], wa, wb);
         w[c] = wa;
         w[nc + c] = wb;
       }
@@ -147,8 +164,13 @@ __global__ void k_field_from_phi(const SysDev* __restrict__ systems, int sys, co
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
     const float pA = phi[c], pB = phi[nc + c];
     const float ex = S.kappaN_N * (pA + pB - 1.f);
-    S.w[c] = fmaf(S.chiN_N, pB, ex);
-    S.w[nc + c] = fmaf(S.chiN_N, pA, ex);
+    float wA = fmaf(S.chiN_N, pB, ex), wB = fmaf(S.chiN_N, pA, ex);
+    if (S.umbrella) {
+      wA = fmaf(S.umbN_N, pA - S.phi_target[c], wA);
+      wB = fmaf(S.umbN_N, pB - S.phi_target[nc + c], wB);
+    }
+    S.w[c] = wA;
+    S.w[nc + c] = wB;
   }
 }
 
@@ -166,45 +188,96 @@ __global__ void k_set_step(unsigned long long* counters, int n_sys, unsigned lon
 // bond i a Gaussian with per-axis variance 1/(3(N-1)) by Box-Muller on the
 // word pairs (0,1) and (2,3).  Accumulated in FP64, then wrapped.
 // ---------------------------------------------------------------------------
+// Chain c (logical = storage slot) from bead 0 at (X, Y, Z): the bonds of
+// the initial configuration, accumulated in FP64, wrapped, written.
+__device__ void grow_chain(const SysDev& S, int c, double X, double Y, double Z) {
+  const int N = S.N;
+  const double sigma = N > 1 ? sqrt(1.0 / (3.0 * (N - 1))) : 0.0;
+  S.chain_id[c] = (uint32_t)c;
+  for (int i = 0; i < N; ++i) {
+    if (i > 0) {
+      const uint4 r = philox10(make_uint4((uint32_t)i, (uint32_t)c, kInitStep, (uint32_t)S.sys_index), S.rk);
+      const double m1 = sqrt(-2.0 * log(((double)(r.x >> 8) + 0.5) * 0x1p-24));
+      const double m2 = sqrt(-2.0 * log(((double)(r.z >> 8) + 0.5) * 0x1p-24));
+      double s1, c1, s2, c2;
+      sincospi(2.0 * ((double)(r.y >> 8) * 0x1p-24), &s1, &c1);
+      sincospi(2.0 * ((double)(r.w >> 8) * 0x1p-24), &s2, &c2);
+      X += sigma * m1 * c1;
+      Y += sigma * m1 * s1;
+      Z += sigma * m2 * c2;
+    }
+    const int64_t b = (int64_t)c * N + i;
+    const double P[3] = {X, Y, Z};
+    float* dst[3] = {S.x, S.y, S.z};
+    short im[3];
+    for (int a = 0; a < 3; ++a) {
+      const double L = (double)S.L[a];
+      double n = floor(P[a] / L);
+      float xw = (float)(P[a] - n * L);
+      if (xw >= S.L[a]) { xw = 0.f; n += 1.0; }
+      if (xw < 0.f) xw = 0.f;
+      dst[a][b] = xw;
+      im[a] = (short)n;
+    }
+    reinterpret_cast<short4*>(S.img)[b] = make_short4(im[0], im[1], im[2], 0);
+  }
+}
+
 __global__ void k_init(const SysDev* __restrict__ systems, int sys) {
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
-  const int N = S.N;
-  const double sigma = N > 1 ? sqrt(1.0 / (3.0 * (N - 1))) : 0.0;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += gridDim.x * blockDim.x) {
-    double X = 0, Y = 0, Z = 0;
-    S.chain_id[c] = (uint32_t)c;
-    for (int i = 0; i < N; ++i) {
-      const uint4 r = philox10(make_uint4((uint32_t)i, (uint32_t)c, kInitStep, (uint32_t)S.sys_index), S.rk);
-      if (i == 0) {
-        X = (double)S.L[0] * ((double)(r.x >> 8) * 0x1p-24);
-        Y = (double)S.L[1] * ((double)(r.y >> 8) * 0x1p-24);
-        Z = (double)S.L[2] * ((double)(r.z >> 8) * 0x1p-24);
-      } else {
-        const double m1 = sqrt(-2.0 * log(((double)(r.x >> 8) + 0.5) * 0x1p-24));
-        const double m2 = sqrt(-2.0 * log(((double)(r.z >> 8) + 0.5) * 0x1p-24));
-        double s1, c1, s2, c2;
-        sincospi(2.0 * ((double)(r.y >> 8) * 0x1p-24), &s1, &c1);
-        sincospi(2.0 * ((double)(r.w >> 8) * 0x1p-24), &s2, &c2);
-        X += sigma * m1 * c1;
-        Y += sigma * m1 * s1;
-        Z += sigma * m2 * c2;
-      }
-      const int64_t b = (int64_t)c * N + i;
-      const double P[3] = {X, Y, Z};
-      float* dst[3] = {S.x, S.y, S.z};
-      short im[3];
-      for (int a = 0; a < 3; ++a) {
-        const double L = (double)S.L[a];
-        double n = floor(P[a] / L);
-        float xw = (float)(P[a] - n * L);
-        if (xw >= S.L[a]) { xw = 0.f; n += 1.0; }
-        if (xw < 0.f) xw = 0.f;
-        dst[a][b] = xw;
-        im[a] = (short)n;
-      }
-      reinterpret_cast<short4*>(S.img)[b] = make_short4(im[0], im[1], im[2], 0);
+    const uint4 r = philox10(make_uint4(0u, (uint32_t)c, kInitStep, (uint32_t)S.sys_index), S.rk);
+    grow_chain(S, c, (double)S.L[0] * ((double)(r.x >> 8) * 0x1p-24),
+               (double)S.L[1] * ((double)(r.y >> 8) * 0x1p-24), (double)S.L[2] * ((double)(r.z >> 8) * 0x1p-24));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Placement from target volume fractions (coupling start-up, Sec. 3.2):
+// integer weights q(c) = floor(phi*(c) 2^16) of bead 0's type, their running
+// sums P (64-bit), then per chain: cell = first c with P(c) > floor(r Q/2^64),
+// r = (w1 << 32 | w0) of counter (0, c, kPlaceStep, s); bead 0 at a uniform
+// point of that cell (counter (1, c, ...)) plus an offset uniform in
+// [-h, h)^3, h = 1/(2 sqrt 3) (counter (2, c, ...)); the chain's bonds are
+// those of the initial configuration.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPlaceStep = 0xFFFFFFFEu;
+
+__global__ void k_place_weights(const float* __restrict__ phi, int64_t n, unsigned long long* __restrict__ q) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const float v = phi[c];
+    q[c] = v > 0.f ? (unsigned long long)(uint32_t)fminf(v * 65536.0f, 4294967040.0f) : 0ull;
+  }
+}
+
+__global__ void k_place(const SysDev* __restrict__ systems, int sys, const unsigned long long* __restrict__ prefix,
+                        unsigned long long Q) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  const double h = 0.5 / sqrt(3.0);  // correctly rounded, as on the host
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += gridDim.x * blockDim.x) {
+    const uint4 r0 = philox10(make_uint4(0u, (uint32_t)c, kPlaceStep, (uint32_t)S.sys_index), S.rk);
+    const uint4 r1 = philox10(make_uint4(1u, (uint32_t)c, kPlaceStep, (uint32_t)S.sys_index), S.rk);
+    const uint4 r2 = philox10(make_uint4(2u, (uint32_t)c, kPlaceStep, (uint32_t)S.sys_index), S.rk);
+    const unsigned long long r = ((unsigned long long)r0.y << 32) | r0.x;
+    const unsigned long long k = __umul64hi(r, Q);
+    int64_t lo = 0, hi = S.n_c - 1;  // first cell whose running sum exceeds k
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (prefix[mid] > k)
+        hi = mid;
+      else
+        lo = mid + 1;
     }
+    const int64_t ix = lo / ((int64_t)S.ny * S.nz), iy = (lo / S.nz) % S.ny, iz = lo % S.nz;
+    const double X = ((double)ix + (double)(r1.x >> 8) * 0x1p-24) * (double)S.L[0] / S.nx +
+                     h * fma((double)(r2.x >> 8), 0x1p-23, -1.0);
+    const double Y = ((double)iy + (double)(r1.y >> 8) * 0x1p-24) * (double)S.L[1] / S.ny +
+                     h * fma((double)(r2.y >> 8), 0x1p-23, -1.0);
+    const double Z = ((double)iz + (double)(r1.z >> 8) * 0x1p-24) * (double)S.L[2] / S.nz +
+                     h * fma((double)(r2.z >> 8), 0x1p-23, -1.0);
+    grow_chain(S, c, X, Y, Z);
   }
 }
 
@@ -463,6 +536,34 @@ cudaError_t launch_deinterleave(const uint32_t* counts, int64_t n_c, uint32_t* o
 cudaError_t launch_field_from_phi(const SysDev* systems, int sys, const float* phi, int sm_count, cudaStream_t s) {
   k_field_from_phi<<<sm_count * 4, 256, 0, s>>>(systems, sys, phi);
   return cudaGetLastError();
+}
+
+cudaError_t launch_place(const SysDev* systems, int sys, const SysDev& host, const float* phi,
+                         unsigned long long* q, unsigned long long* prefix, void* temp, size_t temp_bytes,
+                         unsigned long long* total, int sm_count, cudaStream_t s) {
+  const int64_t nc = host.n_c;
+  const float* w = phi + (host.n_A > 0 ? 0 : nc);  // weights of bead 0's type
+  k_place_weights<<<sm_count * 4, 256, 0, s>>>(w, nc, q);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  size_t bytes = temp_bytes;
+  e = cub::DeviceScan::InclusiveSum(temp, bytes, q, prefix, nc, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(total, prefix + nc - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  if (*total == 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((host.n_poly + 127) / 128, (int64_t)sm_count * 8);
+  k_place<<<grid, 128, 0, s>>>(systems, sys, prefix, *total);
+  return cudaGetLastError();
+}
+
+size_t place_temp_bytes(int64_t n_c) {
+  size_t bytes = 0;
+  cub::DeviceScan::InclusiveSum(nullptr, bytes, (const unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                n_c);
+  return bytes;
 }
 
 cudaError_t launch_advance(unsigned long long* counters, int n_sys, long long n, cudaStream_t s) {

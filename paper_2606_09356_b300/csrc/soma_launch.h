@@ -21,6 +21,13 @@ cudaError_t launch_field(const FieldArgs& f, StepRef r, int zero_next, cudaStrea
 cudaError_t launch_deinterleave(const uint32_t* counts, int64_t n_c, uint32_t* out, int sm_count, cudaStream_t s);
 cudaError_t launch_field_from_phi(const SysDev* systems, int sys, const float* phi, int sm_count, cudaStream_t s);
 cudaError_t launch_advance(unsigned long long* counters, int n_sys, long long n, cudaStream_t s);
+// Placement from target volume fractions phi [2][n_c] (device); q and prefix
+// hold n_c 64-bit words each; *total receives the weight sum (0: nothing
+// placed).  Synchronises the stream once.
+cudaError_t launch_place(const SysDev* systems, int sys, const SysDev& host, const float* phi,
+                         unsigned long long* q, unsigned long long* prefix, void* temp, size_t temp_bytes,
+                         unsigned long long* total, int sm_count, cudaStream_t s);
+size_t place_temp_bytes(int64_t n_c);
 cudaError_t launch_set_step(unsigned long long* counters, int n_sys, unsigned long long value, cudaStream_t s);
 cudaError_t launch_init(const SysDev* systems, int sys, int64_t n_poly, cudaStream_t s);
 cudaError_t launch_gather_state(const SysDev* systems, int sys, float* pos, int16_t* img, int sm_count,

@@ -38,8 +38,8 @@ SOMA_HIST_SEPARATE = 2
 EXPORTS = (
     "soma_options_default", "soma_create", "soma_destroy", "soma_strerror", "soma_last_error",
     "soma_mc_steps", "soma_sync", "soma_get_density", "soma_get_fields", "soma_set_density",
-    "soma_freeze_fields", "soma_get_state", "soma_set_state", "soma_get_state64", "soma_set_state64",
-    "soma_observables", "soma_get_accepted",
+    "soma_freeze_fields", "soma_set_umbrella", "soma_place", "soma_get_state", "soma_set_state",
+    "soma_get_state64", "soma_set_state64", "soma_observables", "soma_get_accepted",
     "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
     "soma_philox4x32", "soma_structure_factor_noalloc",
 )
@@ -116,6 +116,8 @@ def load_library(path=None):
     L.soma_get_fields.argtypes = [vp, i32, vp, sz, i32]
     L.soma_set_density.argtypes = [vp, i32, vp, sz, i32]
     L.soma_freeze_fields.argtypes = [vp, i32, vp, sz, i32]
+    L.soma_set_umbrella.argtypes = [vp, i32, vp, sz, ctypes.c_double, i32]
+    L.soma_place.argtypes = [vp, i32, vp, sz, i32]
     L.soma_get_state.argtypes = [vp, i32, vp, vp, ctypes.POINTER(u64), i32]
     L.soma_set_state.argtypes = [vp, i32, vp, vp, u64, i32]
     L.soma_get_state64.argtypes = [vp, i32, vp, vp, ctypes.POINTER(u64), i32]
@@ -311,6 +313,23 @@ class Handle:
         _check(self.lib.soma_freeze_fields(self.h, sys, _ptr(w), w.size, SOMA_HOST), "soma_freeze_fields")
 
     # -- state -----------------------------------------------------------
+    def set_umbrella(self, phi_target, lambdaN, sys=0):
+        """Restraint toward target volume fractions [2, n_c]; None or 0 turns it off."""
+        if phi_target is None or lambdaN == 0:
+            _check(self.lib.soma_set_umbrella(self.h, sys, None, 0, 0.0, SOMA_HOST), "soma_set_umbrella")
+            return
+        if not hasattr(phi_target, "data_ptr"):
+            phi_target = np.ascontiguousarray(phi_target, np.float32)
+        _check(self.lib.soma_set_umbrella(self.h, sys, _ptr(phi_target), phi_target.size, float(lambdaN),
+                                          _where(phi_target)), "soma_set_umbrella")
+
+    def place(self, phi_target, sys=0):
+        """New configuration of molecules placed from target volume fractions [2, n_c]."""
+        if not hasattr(phi_target, "data_ptr"):
+            phi_target = np.ascontiguousarray(phi_target, np.float32)
+        _check(self.lib.soma_place(self.h, sys, _ptr(phi_target), phi_target.size, _where(phi_target)),
+               "soma_place")
+
     def get_state(self, sys=0, pos=None, img=None):
         nb = self.systems[sys].n_beads
         pos = np.zeros((nb, 3), np.float32) if pos is None else pos
