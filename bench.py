@@ -401,10 +401,16 @@ def run_gpu(args):
 
     # the bond-force-biased (smart) move on the same workload, timed like the
     # headline (L2 flushed between steps, CUDA events around each step)
-    smart = None
+    smart = umbrella = None
     if not args.no_smart:
-        smart = bench_smart(soma, torch, args.workload, rank_system_kwargs(args.workload, rank), local, sptr, stream,
-                            flush, args.steps, args.warmup, hbm_peak, n_b, n_c)
+        kw = rank_system_kwargs(args.workload, rank)
+        smart = bench_variant(soma, torch, args.workload, kw, local, sptr, stream, flush, args.steps, args.warmup,
+                              hbm_peak, n_b, n_c, move=soma.SOMA_MOVE_SMART,
+                              note="SOMA_MOVE_SMART, same workload, L2 flushed between timed steps")
+        umbrella = bench_variant(soma, torch, args.workload, kw, local, sptr, stream, flush, args.steps,
+                                 args.warmup, hbm_peak, n_b, n_c, umbrella=50.0,
+                                 note="umbrella restraint (lambdaN = 50) toward a lamellar target: field "
+                                      "array from the counts, then the move kernel, per step; L2 flushed")
 
     # batched replicas vs sequential plain runs of the same 64 systems
     batched = None
@@ -422,7 +428,8 @@ def run_gpu(args):
                        "tuned": {k: info_after[k] for k in ("ctas_per_sm", "hist_mode")},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "steady_state": steady, "smart_moves": smart, "batched": batched,
+            "clocks": clk.summary(), "steady_state": steady, "smart_moves": smart, "umbrella": umbrella,
+            "batched": batched,
             "wall_s_timed": wall,
         }
         print(json.dumps(out))
@@ -431,12 +438,19 @@ def run_gpu(args):
         pg.destroy_process_group()
 
 
-def bench_smart(soma, torch, workload, kw, device, sptr, stream, flush, steps, warmup, hbm_peak, n_b, n_c):
-    """The workload with bond-force-biased trial moves: moves/s over flushed
-    steps and the move kernel's fraction of the HBM roofline (same
-    algorithmic bytes as the uniform move)."""
-    h = soma.Handle(soma.System(**{**kw, "move": soma.SOMA_MOVE_SMART}), device=device, kernel_timing=1,
-                    graph_steps=0, autotune=1)
+def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps, warmup, hbm_peak, n_b, n_c,
+                  move=0, umbrella=0.0, note=""):
+    """The workload with another trial move or with the umbrella restraint on:
+    moves/s over flushed steps and the move kernel's fraction of the HBM
+    roofline (same algorithmic bytes per step as the headline)."""
+    h = soma.Handle(soma.System(**{**kw, "move": move}), device=device, kernel_timing=1, graph_steps=0,
+                    autotune=1)
+    if umbrella:
+        import numpy as np
+        nx = kw["grid"][0]
+        x = (np.arange(nx) + 0.5) / nx
+        pA = np.repeat(0.5 + 0.4 * np.sin(4 * np.pi * x), kw["grid"][1] * kw["grid"][2])
+        h.set_umbrella(np.stack([pA, 1.0 - pA]).astype(np.float32), umbrella)
     for _ in range(warmup):
         h.mc_steps(1, stream=sptr)
     torch.cuda.synchronize()
@@ -456,12 +470,17 @@ def bench_smart(soma, torch, workload, kw, device, sptr, stream, flush, steps, w
     acc = (h.accepted() - a0) / (steps * n_b)
     h.close()
     mv_ms, mv_n = kt["move"]
+    fd_ms, fd_n = kt["field"]
     move_avg = mv_ms / max(1, mv_n)
     achieved = move_kernel_bytes(n_b, n_c) / (move_avg * 1e-3) / 1e9
-    return {"value": steps * n_b / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / steps,
-            "move_ms": move_avg, "achieved_gbs": achieved, "frac": achieved / hbm_peak, "acceptance": acc,
-            "traffic": _profiled_traffic(workload, "_smart"),
-            "note": "SOMA_MOVE_SMART, same workload, L2 flushed between timed steps"}
+    out = {"value": steps * n_b / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / steps,
+           "move_ms": move_avg, "achieved_gbs": achieved, "frac": achieved / hbm_peak, "acceptance": acc,
+           "note": note}
+    if fd_n:
+        out["field_ms"] = fd_ms / fd_n
+    if move:
+        out["traffic"] = _profiled_traffic(workload, "_smart")
+    return out
 
 
 def bench_batched(soma, workloads, torch, sptr, stream, steps=20):

@@ -151,6 +151,24 @@ __device__ __forceinline__ void apply_image_steps(int16_t* img, int64_t bead, fl
   }
 }
 
+// wrap_step of two coordinates of the same axis, the FMA packed.
+__device__ __forceinline__ float2 wrap_step2(float2 p, float L, float Lm, float2& fl) {
+  fl.x = p.x >= L ? 1.f : (p.x < 0.f ? -1.f : 0.f);
+  fl.y = p.y >= L ? 1.f : (p.y < 0.f ? -1.f : 0.f);
+  const float2 q = __ffma2_rn(make_float2(-L, -L), fl, p);
+  return make_float2(fminf(q.x, Lm), fminf(q.y, Lm));
+}
+
+// Cells of two positions, the scalings packed.
+__device__ __forceinline__ int2 cell_idx2(const MoveArgs& a, float2 x, float2 y, float2 z) {
+  const float2 sx = __fmul2_rn(x, make_float2(a.cps[0], a.cps[0]));
+  const float2 sy = __fmul2_rn(y, make_float2(a.cps[1], a.cps[1]));
+  const float2 sz = __fmul2_rn(z, make_float2(a.cps[2], a.cps[2]));
+  const int n0 = a.n[0] - 1, n1 = a.n[1] - 1, n2 = a.n[2] - 1;
+  return make_int2((min((int)sx.x, n0) * a.n[1] + min((int)sy.x, n1)) * a.n[2] + min((int)sz.x, n2),
+                   (min((int)sx.y, n0) * a.n[1] + min((int)sy.y, n1)) * a.n[2] + min((int)sz.y, n2));
+}
+
 __device__ __forceinline__ int cell_idx(const MoveArgs& a, float x, float y, float z) {
   return (cell_axis(x, a.cps[0], a.n[0]) * a.n[1] + cell_axis(y, a.cps[1], a.n[1])) * a.n[2] +
          cell_axis(z, a.cps[2], a.n[2]);
@@ -179,6 +197,18 @@ __device__ __forceinline__ float field_from_counts(const MoveArgs& a, int type, 
   return a.inv_rho * fmaf(a.chiN_N, (float)d_other, a.kappaN_N * (float)d_tot);
 }
 
+// field_from_counts of the lane's two beads, the arithmetic packed.
+__device__ __forceinline__ float2 fields_from_counts2(const MoveArgs& a, int te, int to, uint2 ne0, uint2 ne1,
+                                                      uint2 no0, uint2 no1) {
+  const int de_other = te ? (int)(ne1.x - ne0.x) : (int)(ne1.y - ne0.y);
+  const int do_other = to ? (int)(no1.x - no0.x) : (int)(no1.y - no0.y);
+  const int de_tot = (int)(ne1.x + ne1.y) - (int)(ne0.x + ne0.y);
+  const int do_tot = (int)(no1.x + no1.y) - (int)(no0.x + no0.y);
+  const float2 k = __fmul2_rn(make_float2(a.kappaN_N, a.kappaN_N), make_float2((float)de_tot, (float)do_tot));
+  const float2 f = __ffma2_rn(make_float2(a.chiN_N, a.chiN_N), make_float2((float)de_other, (float)do_other), k);
+  return __fmul2_rn(make_float2(a.inv_rho, a.inv_rho), f);
+}
+
 // Standard normal deviate of a Philox word: Phi^-1(((w >> 8) + 1/2) 2^-24).
 // The argument is formed exactly in FP32 by evaluating the lower tail of
 // whichever half of (0, 1) it falls in (Phi^-1(1 - v) = -Phi^-1(v)).
@@ -193,7 +223,8 @@ __device__ __forceinline__ float normal_of_word(uint32_t w) {
 // The bead pair of one lane: positions in, decisions, final cells and image
 // codes out.  Uniform proposals (Sec. 2.1, step (a)).
 template <bool kFromCounts>
-__device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, uint32_t cid, int k, int e, int o,
+__device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, const uint2* __restrict__ prev,
+                                             uint32_t cid, int k, int e, int o,
                                              int te, int to, bool he, bool ho, float& xe, float& ye, float& ze,
                                              float& xo, float& yo, float& zo, bool& acc, bool& acco, int& ce,
                                              int& co, float& wrap_e, float& wrap_o) {
@@ -205,30 +236,31 @@ __device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, ui
   // d = A (2 U - 1) = A ((w >> 8) 2^-23 - 1): the bracket is exact in FP32,
   // so one FMA with A 2^-23 and -A rounds the same exact value once
   const float A23 = a.A * 0x1p-23f;
-  const float dex = fmaf((float)(re.x >> 8), A23, -a.A);
-  const float dey = fmaf((float)(re.y >> 8), A23, -a.A);
-  const float dez = fmaf((float)(re.z >> 8), A23, -a.A);
-  const float dox = fmaf((float)(ro.x >> 8), A23, -a.A);
-  const float doy = fmaf((float)(ro.y >> 8), A23, -a.A);
-  const float doz = fmaf((float)(ro.z >> 8), A23, -a.A);
-  float fx, fy, fz;
-  const float pex = wrap_step(xe + dex, a.L[0], a.Lm[0], fx);
-  const float pey = wrap_step(ye + dey, a.L[1], a.Lm[1], fy);
-  const float pez = wrap_step(ze + dez, a.L[2], a.Lm[2], fz);
-  wrap_e = fmaf(9.f, fz, fmaf(3.f, fy, fx));
-  const float pox = wrap_step(xo + dox, a.L[0], a.Lm[0], fx);
-  const float poy = wrap_step(yo + doy, a.L[1], a.Lm[1], fy);
-  const float poz = wrap_step(zo + doz, a.L[2], a.Lm[2], fz);
-  wrap_o = fmaf(9.f, fz, fmaf(3.f, fy, fx));
-  const int ce0 = cell_idx(a, xe, ye, ze), ce1 = cell_idx(a, pex, pey, pez);
-  const int co0 = cell_idx(a, xo, yo, zo), co1 = cell_idx(a, pox, poy, poz);
+  // the two beads' arithmetic runs as packed pairs (Blackwell FP32x2 ops,
+  // each lane rounded exactly as the scalar operation)
+  const float2 A23v = make_float2(A23, A23), mA = make_float2(-a.A, -a.A);
+  const float2 dX = __ffma2_rn(make_float2((float)(re.x >> 8), (float)(ro.x >> 8)), A23v, mA);
+  const float2 dY = __ffma2_rn(make_float2((float)(re.y >> 8), (float)(ro.y >> 8)), A23v, mA);
+  const float2 dZ = __ffma2_rn(make_float2((float)(re.z >> 8), (float)(ro.z >> 8)), A23v, mA);
+  const float dex = dX.x, dey = dY.x, dez = dZ.x, dox = dX.y, doy = dY.y, doz = dZ.y;
+  float2 fX, fY, fZ;
+  const float2 pX = wrap_step2(__fadd2_rn(make_float2(xe, xo), dX), a.L[0], a.Lm[0], fX);
+  const float2 pY = wrap_step2(__fadd2_rn(make_float2(ye, yo), dY), a.L[1], a.Lm[1], fY);
+  const float2 pZ = wrap_step2(__fadd2_rn(make_float2(ze, zo), dZ), a.L[2], a.Lm[2], fZ);
+  const float2 wr = __ffma2_rn(make_float2(9.f, 9.f), fZ, __ffma2_rn(make_float2(3.f, 3.f), fY, fX));
+  wrap_e = wr.x;
+  wrap_o = wr.y;
+  const float pex = pX.x, pey = pY.x, pez = pZ.x, pox = pX.y, poy = pY.y, poz = pZ.y;
+  const int2 c_old = cell_idx2(a, make_float2(xe, xo), make_float2(ye, yo), make_float2(ze, zo));
+  const int2 c_new = cell_idx2(a, pX, pY, pZ);
+  const int ce0 = c_old.x, co0 = c_old.y, ce1 = c_new.x, co1 = c_new.y;
   float fe, fo;
   if (kFromCounts) {
-    const uint2* __restrict__ prev = reinterpret_cast<const uint2*>(count_buffer(a.counts, a.n_c, tl - 1));
     const uint2 ne0 = __ldg(prev + ce0), ne1 = __ldg(prev + ce1);
     const uint2 no0 = __ldg(prev + co0), no1 = __ldg(prev + co1);
-    fe = field_from_counts(a, te, ne0, ne1);
-    fo = field_from_counts(a, to, no0, no1);
+    const float2 f = fields_from_counts2(a, te, to, ne0, ne1, no0, no1);
+    fe = f.x;
+    fo = f.y;
   } else {
     const float* __restrict__ wte = a.w + (te ? a.n_c : 0);
     const float* __restrict__ wto = a.w + (to ? a.n_c : 0);
@@ -292,7 +324,8 @@ __device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, ui
 // the host enforces (drift <= k_b A^2/3 <= 1/2, 6 sig < L/2), a proposal
 // stays within one image of the box.
 template <bool kFromCounts>
-__device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, uint32_t cid, int k, int e, int o,
+__device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, const uint2* __restrict__ prev,
+                                           uint32_t cid, int k, int e, int o,
                                            int te, int to, bool he, bool ho, float& xe, float& ye, float& ze,
                                            float& xo, float& yo, float& zo, bool& acc, bool& acco, int& ce,
                                            int& co, float& wrap_e, float& wrap_o) {
@@ -328,7 +361,6 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, uint
   wrap_e = fmaf(9.f, fz, fmaf(3.f, fy, fx));
   const int ce0 = cell_idx(a, xe, ye, ze), ce1 = cell_idx(a, pex, pey, pez);
   const int co0 = cell_idx(a, xo, yo, zo);
-  const uint2* __restrict__ prev = reinterpret_cast<const uint2*>(count_buffer(a.counts, a.n_c, tl - 1));
   const float* __restrict__ wte = a.w + (te ? a.n_c : 0);
   const float* __restrict__ wto = a.w + (to ? a.n_c : 0);
   float fe;
@@ -404,9 +436,11 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, uint
 // Consumer warp: one tile of system a at step t.  Reads the stage, releases
 // it, moves the even then the odd beads of its chains, writes back, bins.
 // Returns the number of accepted moves of this lane.
+// prev: count buffer of step t-1 (fields), cur: count buffer of step t (histogram).
 template <bool kFromCounts, bool kSmart>
 __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, const MoveStage& st, uint64_t* empty,
-                                                 long long tl, int warp, int lane) {
+                                                 long long tl, const uint2* __restrict__ prev,
+                                                 uint32_t* __restrict__ cur, int warp, int lane) {
   const int P = a.P, N = a.N;
   const int k = lane & (P - 1);
   const int chain_in_tile = warp * (32 / P) + lane / P;
@@ -437,10 +471,10 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   int ce, co;
   float wrap_e, wrap_o;
   if (kSmart)
-    smart_pair<kFromCounts>(a, tl, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co, wrap_e,
+    smart_pair<kFromCounts>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co, wrap_e,
                             wrap_o);
   else
-    uniform_pair<kFromCounts>(a, tl, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co,
+    uniform_pair<kFromCounts>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co,
                               wrap_e, wrap_o);
 
   // ---- write back, images on wrap, fused histogram ----
@@ -458,9 +492,8 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   if (acc) apply_image_steps(a.img, gb, wrap_e);
   if (acco) apply_image_steps(a.img, gb + 1, wrap_o);
   if (a.bin) {
-    uint32_t* __restrict__ cnt = count_buffer(a.counts, a.n_c, tl);
-    if (he) atomicAdd(cnt + 2 * ce + te, 1u);
-    if (ho) atomicAdd(cnt + 2 * co + to, 1u);
+    if (he) atomicAdd(cur + 2 * ce + te, 1u);
+    if (ho) atomicAdd(cur + 2 * co + to, 1u);
   }
   return (acc ? 1u : 0u) + (acco ? 1u : 0u);
 }
@@ -514,12 +547,14 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __g
   }
 
   const long long tl = r.get();
+  const uint2* prev = reinterpret_cast<const uint2*>(count_buffer(a.counts, a.n_c, tl - 1));
+  uint32_t* cur = count_buffer(a.counts, a.n_c, tl);
   unsigned nacc = 0;
   int it = 0;
   for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
     const int s = it % kStages;
     if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, a.err)) break;
-    nacc += consume_tile<kFromCounts, kSmart>(a, tile, stage[s], &empty[s], tl, warp, lane);
+    nacc += consume_tile<kFromCounts, kSmart>(a, tile, stage[s], &empty[s], tl, prev, cur, warp, lane);
   }
   nacc = __reduce_add_sync(0xffffffffu, nacc);
   if (lane == 0 && nacc) atomicAdd(a.acc + blockIdx.x, (unsigned long long)nacc);
@@ -572,9 +607,12 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
     if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, err)) break;
     const int sys = batch_system(p, tile);
     const MoveArgs& a = p.sys[sys];
+    const uint2* prev = reinterpret_cast<const uint2*>(count_buffer(a.counts, a.n_c, tl - 1));
+    uint32_t* cur = count_buffer(a.counts, a.n_c, tl);
+    const int lt = tile - p.tile_start[sys];
     unsigned n = a.from_counts
-                     ? consume_tile<true, kSmart>(a, tile - p.tile_start[sys], stage[s], &empty[s], tl, warp, lane)
-                     : consume_tile<false, kSmart>(a, tile - p.tile_start[sys], stage[s], &empty[s], tl, warp, lane);
+                     ? consume_tile<true, kSmart>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
+                     : consume_tile<false, kSmart>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
     n = __reduce_add_sync(0xffffffffu, n);
     if (lane == 0 && n) atomicAdd(a.acc + blockIdx.x, (unsigned long long)n);
   }
