@@ -96,6 +96,13 @@ class _Nvml:
             raise RuntimeError("clock query failed")
         return v.value
 
+    def energy_mj(self):
+        """Total energy the GPU has consumed since the driver loaded, in mJ."""
+        v = self.ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.h, self.ct.byref(v)) != 0:
+            raise RuntimeError("energy query failed")
+        return v.value
+
     def reasons(self):
         v = self.ct.c_ulonglong()
         if self.reasons_fn(self.h, self.ct.byref(v)) != 0:
@@ -374,6 +381,12 @@ def run_gpu(args):
                           f"{hg.info()['sort_interval']} steps"}
         hg.close()
 
+    # energy per step (context: the paper reports energy per unit of work):
+    # NVML's energy counter across about two seconds of CUDA-graph replays
+    energy = None
+    if not args.no_energy:
+        energy = measure_energy(soma, torch, c, rank, local, sptr, stream, n_b)
+
     # end to end through the public API with pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -428,7 +441,7 @@ def run_gpu(args):
                        "tuned": {k: info_after[k] for k in ("ctas_per_sm", "hist_mode")},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "steady_state": steady, "smart_moves": smart, "umbrella": umbrella,
+            "clocks": clk.summary(), "steady_state": steady, "energy": energy, "smart_moves": smart, "umbrella": umbrella,
             "batched": batched,
             "wall_s_timed": wall,
         }
@@ -436,6 +449,31 @@ def run_gpu(args):
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def measure_energy(soma, torch, c, rank, local, sptr, stream, n_b, seconds=2.0):
+    try:
+        nv = _Nvml(local)
+        nv.energy_mj()
+    except Exception as e:
+        return {"error": repr(e)}
+    h = soma.Handle(soma.System(**{**c, "system_id": rank}), device=local)
+    h.mc_steps(64, stream=sptr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.mc_steps(256, stream=sptr)
+    torch.cuda.synchronize()
+    per = (time.perf_counter() - t0) / 256
+    n = max(256, int(seconds / per))
+    e0, t0 = nv.energy_mj(), time.perf_counter()
+    h.mc_steps(n, stream=sptr)
+    torch.cuda.synchronize()
+    e1, t1 = nv.energy_mj(), time.perf_counter()
+    h.close()
+    joules = (e1 - e0) * 1e-3
+    return {"steps": n, "seconds": t1 - t0, "joules_per_step": joules / n, "moves_per_joule": n * n_b / joules
+            if joules > 0 else None, "avg_power_w": joules / (t1 - t0),
+            "note": "NVML total-energy counter over CUDA-graph replays (L2 warm), whole GPU board"}
 
 
 def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps, warmup, hbm_peak, n_b, n_c,
@@ -534,6 +572,7 @@ def main():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-steady", action="store_true")
     p.add_argument("--no-smart", action="store_true")
+    p.add_argument("--no-energy", action="store_true")
     args = p.parse_args()
     if args.warmup < 3:
         p.error("--warmup must be at least 3")

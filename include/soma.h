@@ -253,6 +253,16 @@ int soma_autotune(soma_handle* h);
  * device function the move kernel uses).  Synchronous. */
 int soma_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n);
 
+/* Failure-path self-check (no counterpart in the paper, which names no
+ * fault mechanism): on `device` (-1 = current) one thread waits, with the
+ * move kernels' bounded mbarrier wait, on a barrier that nothing arrives
+ * on, for at most `cycles` SM clock cycles (1e3 .. 2e10, else SOMA_EINVAL).
+ * Returns SOMA_ETIMEOUT when the wait gave up, set the device error bit and
+ * returned as designed (the context stays usable); SOMA_OK would mean the
+ * wait completed, SOMA_ECUDA / SOMA_ENOMEM a CUDA failure.  Allocates and
+ * frees 4 bytes of device memory; synchronises the device. */
+int soma_selfcheck_timeout(int device, uint64_t cycles);
+
 /* S(q) of positions the caller already holds on the device, with no device
  * allocation: the paper has no counterpart; this entry point serves callers
  * that must not allocate GPU memory at the point of the call -- code whose

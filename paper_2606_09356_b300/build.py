@@ -7,6 +7,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsoma.so")
+# checked build (-DSOMA_DEBUG): bounds checks in the move kernel that set the
+# device error word, the stand-in for a memory checker on this platform
+OBJ_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libsoma_debug.so")
 SOURCES = ["soma_move.cu", "soma_kernels.cu", "soma_f64.cu", "soma_sort.cu", "soma_api.cu", "soma_noalloc.cu"]
 HEADERS = ["soma_internal.cuh", "soma_launch.h", "soma_device.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -22,8 +26,12 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile every CUDA source of the package and link libsoma.so; returns its path."""
+def build(force=False, verbose=False, extra_flags=(), debug=False):
+    """Compile every CUDA source of the package and link libsoma.so (or, with
+    debug=True, the checked libsoma_debug.so); returns its path."""
+    OBJ, LIB = (OBJ_DEBUG, LIB_DEBUG) if debug else (globals()["OBJ"], globals()["LIB"])
+    if debug:
+        extra_flags = list(extra_flags) + ["-DSOMA_DEBUG"]
     os.makedirs(OBJ, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(HERE, "..", "include", "soma.h")]
     objs = []
@@ -46,4 +54,4 @@ def build(force=False, verbose=False, extra_flags=()):
 
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True,
-          extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [])
+          extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else [], debug="--debug" in sys.argv)

@@ -17,9 +17,20 @@
 #include "soma_internal.cuh"
 #include "soma_launch.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace soma;
 
 namespace {
+
+// NVTX range around an API call (visible in Nsight timelines; a no-op
+// without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kDefaultSortInterval = 200;
 constexpr int kDefaultGraphSteps = 16;
@@ -532,6 +543,7 @@ void soma_destroy(soma_handle* h) {
 }
 
 int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt, soma_handle** out) {
+  NvtxRange nvtx_range("soma_create");
   if (!out) return SOMA_EINVAL;
   *out = nullptr;
   if (!sys || n_sys < 1 || n_sys > (1 << 16)) return SOMA_EINVAL;
@@ -733,6 +745,7 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
 }
 
 int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
+  NvtxRange nvtx_range("soma_mc_steps");
   int rc = check_live(h);
   if (rc) return rc;
   if (n_steps < 0) return SOMA_EINVAL;
@@ -790,6 +803,7 @@ int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
 }
 
 int soma_sync(soma_handle* h, void* stream) {
+  NvtxRange nvtx_range("soma_sync");
   int rc = check_live(h);
   if (rc) return rc;
   CK(cudaStreamSynchronize(pick(h, stream)));
@@ -798,6 +812,7 @@ int soma_sync(soma_handle* h, void* stream) {
 }
 
 int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where) {
+  NvtxRange nvtx_range("soma_get_density");
   int rc = check_live(h);
   if (rc) return rc;
   if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
@@ -813,6 +828,7 @@ int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where
 }
 
 int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where) {
+  NvtxRange nvtx_range("soma_get_fields");
   int rc = check_live(h);
   if (rc) return rc;
   if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
@@ -830,6 +846,7 @@ int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where) {
 }
 
 int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int where) {
+  NvtxRange nvtx_range("soma_set_density");
   int rc = check_live(h);
   if (rc) return rc;
   if (h->f64) return SOMA_ENOTSUP;
@@ -845,6 +862,7 @@ int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int wh
 }
 
 int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int where) {
+  NvtxRange nvtx_range("soma_freeze_fields");
   int rc = check_live(h);
   if (rc) return rc;
   if (h->f64) return SOMA_ENOTSUP;
@@ -866,6 +884,7 @@ int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int wh
 }
 
 int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* step, int where) {
+  NvtxRange nvtx_range("soma_get_state");
   int rc = check_live(h);
   if (rc) return rc;
   if (h->f64) return SOMA_ENOTSUP;
@@ -884,6 +903,7 @@ int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* 
 }
 
 int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img, uint64_t step, int where) {
+  NvtxRange nvtx_range("soma_set_state");
   int rc = check_live(h);
   if (rc) return rc;
   if (h->f64) return SOMA_ENOTSUP;
@@ -915,6 +935,7 @@ int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img
 }
 
 int soma_get_state64(soma_handle* h, int sys, double* pos, int16_t* img, uint64_t* step, int where) {
+  NvtxRange nvtx_range("soma_get_state64");
   int rc = check_live(h);
   if (rc) return rc;
   if (!h->f64) return SOMA_ENOTSUP;
@@ -933,6 +954,7 @@ int soma_get_state64(soma_handle* h, int sys, double* pos, int16_t* img, uint64_
 }
 
 int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* img, uint64_t step, int where) {
+  NvtxRange nvtx_range("soma_set_state64");
   int rc = check_live(h);
   if (rc) return rc;
   if (!h->f64) return SOMA_ENOTSUP;
@@ -976,6 +998,7 @@ int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted) {
 }
 
 int soma_observables(soma_handle* h, int sys, soma_obs* out) {
+  NvtxRange nvtx_range("soma_observables");
   int rc = check_live(h);
   if (rc) return rc;
   if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
@@ -1006,6 +1029,7 @@ int soma_observables(soma_handle* h, int sys, soma_obs* out) {
 }
 
 int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz, double* S_out) {
+  NvtxRange nvtx_range("soma_structure_factor");
   int rc = check_live(h);
   if (rc) return rc;
   if (sys < 0 || sys >= h->n_sys || nq < 0 || (nq > 0 && (!m_xyz || !S_out))) return SOMA_EINVAL;
@@ -1032,6 +1056,7 @@ int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz,
 }
 
 int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n, double lambdaN, int where) {
+  NvtxRange nvtx_range("soma_set_umbrella");
   int rc = check_live(h);
   if (rc) return rc;
   if (h->f64) return SOMA_ENOTSUP;
@@ -1067,6 +1092,7 @@ int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n
 }
 
 int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int where) {
+  NvtxRange nvtx_range("soma_place");
   int rc = check_live(h);
   if (rc) return rc;
   if (h->f64) return SOMA_ENOTSUP;
@@ -1101,7 +1127,26 @@ int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int w
   return sync_all(h);
 }
 
+int soma_selfcheck_timeout(int device, uint64_t cycles) {
+  if (cycles < 1000 || cycles > 20000000000ull) return SOMA_EINVAL;
+  if (device >= 0 && cudaSetDevice(device) != cudaSuccess) return SOMA_ECUDA;
+  int* err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return SOMA_ENOMEM;
+  }
+  int rc = SOMA_ECUDA, value = 0;
+  if (cudaMemset(err, 0, sizeof(int)) == cudaSuccess &&
+      launch_wait_selfcheck(err, (long long)cycles, nullptr) == cudaSuccess &&
+      cudaDeviceSynchronize() == cudaSuccess &&
+      cudaMemcpy(&value, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+    rc = (value & kErrTimeout) ? SOMA_ETIMEOUT : SOMA_OK;
+  cudaFree(err);
+  return rc;
+}
+
 int soma_reorder(soma_handle* h, void* stream) {
+  NvtxRange nvtx_range("soma_reorder");
   int rc = check_live(h);
   if (rc) return rc;
   if (h->f64) return SOMA_ENOTSUP;
@@ -1153,6 +1198,7 @@ int soma_kernel_times(soma_handle* h, double* ms, int64_t* launches, int reset) 
 // are counter-based, so the restored trajectory is the one that would have
 // run; the acceptance counters are restored as well.
 int soma_autotune(soma_handle* h) {
+  NvtxRange nvtx_range("soma_autotune");
   int rc = check_live(h);
   if (rc) return rc;
   h->tuned = true;

@@ -81,12 +81,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Wait for the phase of the given parity to complete, at most kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+// Wait for the phase of the given parity to complete, at most `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          long long limit = kWaitCycles) {
   if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_test(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicOr(err, kErrTimeout);
       return false;
     }
@@ -139,11 +140,16 @@ __device__ __forceinline__ float wrap_step(float p, float L, float Lm, float& fl
 
 // Image steps of the three axes packed as fx + 3 fy + 9 fz (balanced
 // ternary: zero only when nothing wrapped), applied in the rare case.
-__device__ __forceinline__ void apply_image_steps(int16_t* img, int64_t bead, float code) {
+__device__ __forceinline__ void apply_image_steps(int16_t* img, int64_t bead, float code, int* err) {
   if (code != 0.f) {
     const int c = __float2int_rn(code) + 13;  // 0 .. 26, digits fx+1, fy+1, fz+1
     short4* p = reinterpret_cast<short4*>(img) + bead;
     short4 v = *p;
+#ifdef SOMA_DEBUG
+    // checked build: an image counter about to leave the int16 range
+    if (v.x <= -32767 || v.x >= 32767 || v.y <= -32767 || v.y >= 32767 || v.z <= -32767 || v.z >= 32767)
+      atomicOr(err, kErrBounds);
+#endif
     v.x += (short)(c % 3 - 1);
     v.y += (short)((c / 3) % 3 - 1);
     v.z += (short)(c / 9 - 1);
@@ -477,6 +483,14 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
     uniform_pair<kFromCounts>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co,
                               wrap_e, wrap_o);
 
+#ifdef SOMA_DEBUG
+  // checked build: final cells inside the grid, positions finite in [0, L)
+  if ((he && (ce < 0 || ce >= a.n_c || !(xe >= 0.f && xe < a.L[0] && ye >= 0.f && ye < a.L[1] && ze >= 0.f &&
+                                          ze < a.L[2]))) ||
+      (ho && (co < 0 || co >= a.n_c || !(xo >= 0.f && xo < a.L[0] && yo >= 0.f && yo < a.L[1] && zo >= 0.f &&
+                                          zo < a.L[2]))))
+    atomicOr(a.err, kErrBounds);
+#endif
   // ---- write back, images on wrap, fused histogram ----
   const int64_t gb = (int64_t)c0 * N + lb;
   if ((N & 1) == 0) {
@@ -489,8 +503,8 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
     if (acc) { a.x[gb] = xe; a.y[gb] = ye; a.z[gb] = ze; }
     if (acco) { a.x[gb + 1] = xo; a.y[gb + 1] = yo; a.z[gb + 1] = zo; }
   }
-  if (acc) apply_image_steps(a.img, gb, wrap_e);
-  if (acco) apply_image_steps(a.img, gb + 1, wrap_o);
+  if (acc) apply_image_steps(a.img, gb, wrap_e, a.err);
+  if (acco) apply_image_steps(a.img, gb + 1, wrap_o, a.err);
   if (a.bin) {
     if (he) atomicAdd(cur + 2 * ce + te, 1u);
     if (ho) atomicAdd(cur + 2 * co + to, 1u);
@@ -617,6 +631,24 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
     if (lane == 0 && n) atomicAdd(a.acc + blockIdx.x, (unsigned long long)n);
   }
   for (int sys = 0; sys < p.n_sys; ++sys) clear_next(p.sys[sys], tl, threadIdx.x, kConsumerWarps * 32);
+}
+
+// Self-check of the bounded-wait failure path: one thread waits on an
+// mbarrier that nothing arrives on, for at most `cycles`; the wait gives up,
+// sets kErrTimeout and the kernel returns, as every wait of the move kernels
+// does when its copies or its consumers never come.
+__global__ void k_wait_selfcheck(int* err, long long cycles) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(&bar, 0u, err, cycles);
+  }
+}
+
+cudaError_t launch_wait_selfcheck(int* err, long long cycles, cudaStream_t s) {
+  k_wait_selfcheck<<<1, 32, 0, s>>>(err, cycles);
+  return cudaGetLastError();
 }
 
 // Resident CTAs per SM of the variant that runs every ordinary step (fields

@@ -15,6 +15,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIBRARY = os.path.join(_HERE, "libsoma.so")
+LIBRARY_DEBUG = os.path.join(_HERE, "libsoma_debug.so")  # checked build (device bounds checks)
 
 SOMA_OK = 0
 SOMA_EINVAL = -1
@@ -41,7 +42,7 @@ EXPORTS = (
     "soma_freeze_fields", "soma_set_umbrella", "soma_place", "soma_get_state", "soma_set_state",
     "soma_get_state64", "soma_set_state64", "soma_observables", "soma_get_accepted",
     "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
-    "soma_philox4x32", "soma_structure_factor_noalloc",
+    "soma_philox4x32", "soma_structure_factor_noalloc", "soma_selfcheck_timeout",
 )
 
 
@@ -117,6 +118,7 @@ def load_library(path=None):
     L.soma_set_density.argtypes = [vp, i32, vp, sz, i32]
     L.soma_freeze_fields.argtypes = [vp, i32, vp, sz, i32]
     L.soma_set_umbrella.argtypes = [vp, i32, vp, sz, ctypes.c_double, i32]
+    L.soma_selfcheck_timeout.argtypes = [i32, u64]
     L.soma_place.argtypes = [vp, i32, vp, sz, i32]
     L.soma_get_state.argtypes = [vp, i32, vp, vp, ctypes.POINTER(u64), i32]
     L.soma_set_state.argtypes = [vp, i32, vp, vp, u64, i32]
@@ -204,6 +206,12 @@ def soma_structure_factor_noalloc(pos, n_beads, N, n_A, box, m, S, stream=None):
     _check(load_library().soma_structure_factor_noalloc(ctypes.c_void_p(p), int(n_beads), int(N), int(n_A),
                                                          _ptr(box), len(m), _ptr(m), ctypes.c_void_p(q), stream),
            "soma_structure_factor_noalloc")
+
+
+def soma_selfcheck_timeout(device=-1, cycles=200_000_000):
+    """Return code of the bounded-wait self-check (SOMA_ETIMEOUT when the
+    failure path works as designed)."""
+    return int(load_library().soma_selfcheck_timeout(device, cycles))
 
 
 def soma_sync(h, stream=None):
