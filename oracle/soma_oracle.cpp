@@ -36,6 +36,8 @@
 //                         one-bead Boltzmann law and the dimer cell-pair law
 //                         (detailed balance makes them stationary).
 //   orc_fields_umbrella   pinned: central difference of H_nb + H_umb.
+//   wall confinement      pinned: the exact cell-pair law of an AB dimer
+//                         between walls (no periodic images in z).
 //   orc_place             pinned: the exact law of the bead-0 cell (target
 //                         weights convolved with the uniform offset) and the
 //                         Gaussian bond statistics of the placed chains.
@@ -63,6 +65,8 @@ typedef struct {
   double chiN, kappaN;
   double A;           // proposal half-width; A <= 0 means 0.5/sqrt(N-1)
   uint64_t seed;      // Philox key (lo, hi)
+  int32_t wall_z;     // 1: hard walls at z = 0 and z = L_z instead of periodic z
+  int32_t reserved;
 } orc_desc;
 
 typedef struct {
@@ -199,7 +203,31 @@ int64_t orc_cell_index(const orc_desc* d, const double* r) { return cell_of(d, r
 // Reading: bead 0 uses x_a = L_a * U(word a); bond i uses Box-Muller on word
 // pairs (0,1) and (2,3), keeping three of the four normals.
 // ---------------------------------------------------------------------------
+// Reading of the wall confinement of Sec. 3.2 (the particle subdomain is a
+// slab in z between walls): with wall_z the z axis is not periodic; a move
+// whose proposal leaves [0, L_z) is rejected, and chains built by the
+// initial configuration or the placement are folded into the slab by mirror
+// reflection at the walls, z -> t if t < L_z else 2 L_z - t, t = z mod 2 L_z.
+static double fold_z(double z, double L) {
+  const double t = z - 2.0 * L * std::floor(z / (2.0 * L));
+  double v = t < L ? t : 2.0 * L - t;
+  if (v >= L) v = std::nextafter(L, 0.0);
+  return v;
+}
+
+static void fold_chains(const orc_desc* d, double* pos) {
+  if (!d->wall_z) return;
+  for (int64_t b = 0; b < n_beads(d); ++b) pos[3 * b + 2] = fold_z(pos[3 * b + 2], d->box[2]);
+}
+
+static void init_chains(const orc_desc* d, double* pos);
+
 void orc_init(const orc_desc* d, double* pos) {
+  init_chains(d, pos);
+  fold_chains(d, pos);
+}
+
+static void init_chains(const orc_desc* d, double* pos) {
   const double sigma = d->N > 1 ? std::sqrt(1.0 / (3.0 * (double)(d->N - 1))) : 0.0;
   const double two_pi = 2.0 * M_PI;
   for (int c = 0; c < d->n_poly; ++c) {
@@ -344,7 +372,7 @@ int orc_place(const orc_desc* d, const float* target, double* pos) {
     P[c] = Q;
   }
   if (Q == 0) return -1;
-  orc_init(d, pos);  // conformations (bead 0 is replaced below)
+  init_chains(d, pos);  // conformations (bead 0 is replaced below; folded at the end)
   const double h = 0.5 / std::sqrt(3.0);
   for (int c = 0; c < d->n_poly; ++c) {
     uint32_t r0[4], r1[4], r2[4];
@@ -371,6 +399,7 @@ int orc_place(const orc_desc* d, const float* target, double* pos) {
     for (int i = 0; i < d->N; ++i)
       for (int a = 0; a < 3; ++a) p[3 * i + a] += shift[a];
   }
+  fold_chains(d, pos);
   return 0;
 }
 
@@ -458,8 +487,13 @@ static int64_t move_set(const orc_desc* d, double* pos, const double* w, uint32_
         bias = (rev - fwd) / (2.0 * s2);  // -ln[q(r'->r) / q(r->r')]
       }
       const double* wt = w + (int64_t)type_of(d, i) * nc;
-      double dE = k_b * dEb + wt[cell_of(d, rn)] - wt[cell_of(d, ri)];
-      double margin = dE + bias + std::log(unit_open(r[3]));
+      double margin;
+      if (d->wall_z && !(rn[2] >= 0.0 && rn[2] < d->box[2])) {
+        margin = HUGE_VAL;  // through a wall: rejected
+      } else {
+        double dE = k_b * dEb + wt[cell_of(d, rn)] - wt[cell_of(d, ri)];
+        margin = dE + bias + std::log(unit_open(r[3]));
+      }
       bool ok = margin < 0.0;
       int64_t b = c * N + i;
       if (acc_out) acc_out[b] = ok ? 1 : 0;

@@ -445,6 +445,40 @@ def pin_place_bond_statistics(O):
     return fails
 
 
+# ---------------------------------------------------------------------------
+def pin_wall_dimer_cell_pairs(O, blocks=16, per_block=15):
+    """AB dimer on a 2^3 grid with hard walls in z: the z kernel has no
+    periodic images (the restricted Boltzmann law is stationary)."""
+    fails = []
+    rng = np.random.default_rng(24)
+    box, grid = (1.0, 1.0, 0.8), (2, 2, 2)
+    for move in (0, 1):
+        o = O(4096, 2, 1, box, grid, 0.0, 0.0, seed=37 + move, move=move, wall_z=1)
+        kb, _, _ = o.params()
+        w = rng.normal(0.0, 0.7, size=(2, o.n_c))
+        Ks = [_bond_cell_kernel(box[0], grid[0], kb), _bond_cell_kernel(box[1], grid[1], kb),
+              _bond_cell_kernel(box[2], grid[2], kb, images=0)]
+        cells = [(ix, iy, iz) for ix in range(2) for iy in range(2) for iz in range(2)]
+        P = np.zeros((o.n_c, o.n_c))
+        for c1, (a1, b1, z1) in enumerate(cells):
+            for c2, (a2, b2, z2) in enumerate(cells):
+                P[c1, c2] = np.exp(-w[0, c1] - w[1, c2]) * Ks[0][a1, a2] * Ks[1][b1, b2] * Ks[2][z1, z2]
+        P /= P.sum()
+        pos = o.init()
+        if not (pos[:, 2].min() >= 0 and pos[:, 2].max() < box[2]):
+            fails.append("initial configuration outside the slab")
+        o.run(pos, 0, 20, w_frozen=w, n_threads=NTHREADS)
+        samples = []
+        for b in range(blocks):
+            r = o.run(pos, 20 + b * per_block, per_block, w_frozen=w, n_threads=NTHREADS, pair_hist=True)
+            h = r["pair_hist"].astype(np.float64)
+            samples.append(h / h.sum())
+        if not (pos[:, 2].min() >= 0 and pos[:, 2].max() < box[2]):
+            fails.append("a bead left the slab")
+        _block_test(fails, f"wall dimer cell-pair law (move {move})", np.array(samples), P.reshape(-1))
+    return fails
+
+
 ALL_PINS = {
     "philox_triton": pin_philox_triton,
     "init_statistics": pin_init_statistics,
@@ -461,4 +495,5 @@ ALL_PINS = {
     "umbrella_fields_derivative": pin_umbrella_fields_derivative,
     "place_bead0_law": pin_place_bead0_law,
     "place_bond_statistics": pin_place_bond_statistics,
+    "wall_dimer_cell_pairs": pin_wall_dimer_cell_pairs,
 }

@@ -60,6 +60,8 @@ MUTATIONS = [
      "                            cell % d->grid[2]};",
      "const int64_t idx[3] = {cell % d->grid[0], (cell / d->grid[0]) % d->grid[1],\n"
      "                            cell / ((int64_t)d->grid[0] * d->grid[1])};", "place_bead0_law"),
+    ("wall ignored: z stays periodic", "if (d->wall_z && !(rn[2] >= 0.0 && rn[2] < d->box[2])) {",
+     "if (false) {", "wall_dimer_cell_pairs"),
     ("placement weights of the other type", "const float* phi = target + (int64_t)type_of(d, 0) * nc;",
      "const float* phi = target + (int64_t)(1 - type_of(d, 0)) * nc;", "place_bead0_law"),
 ]
