@@ -95,6 +95,12 @@ typedef struct soma_system_desc {
   double kappaN;   /* Helfand compressibility kappa times N */
   double A;        /* proposal half-width; <= 0 selects 0.5 / sqrt(N - 1) */
   uint64_t seed;   /* Philox key */
+  int32_t wall_z;  /* 0: periodic in z; 1: hard walls at z = 0 and z = L_z (the
+                      particle subdomain as a slab between walls, Sec. 3.2):
+                      a move leaving [0, L_z) is rejected, initial and placed
+                      chains are folded into the slab by mirror reflection.
+                      SOMA_ENOTSUP with SOMA_PREC_FP64. */
+  int32_t reserved2; /* 0 */
 } soma_system_desc;
 
 typedef void* (*soma_alloc_fn)(size_t bytes, void* ctx);

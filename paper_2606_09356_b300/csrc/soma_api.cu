@@ -177,6 +177,7 @@ int validate_desc(const soma_system_desc& d) {
   for (int a = 0; a < 3; ++a)
     if (A >= d.box[a]) return SOMA_EINVAL;  // a proposal must wrap at most once
   if (d.move != SOMA_MOVE_UNIFORM && d.move != SOMA_MOVE_SMART) return SOMA_EINVAL;
+  if (d.wall_z != 0 && d.wall_z != 1) return SOMA_EINVAL;
   if (d.move == SOMA_MOVE_SMART) {
     // |drift s| <= (A^2 (N-1)/2) L and |sig xi| < 6 A/sqrt(3) with |xi| < 6:
     // both below L/2 keeps a proposal within one image of the box
@@ -254,6 +255,7 @@ void build_args(soma_handle* h) {
     a.acc = h->d_acc + S.acc_first;
     a.err = h->d_err;
     a.smart = h->desc[s].move == SOMA_MOVE_SMART ? 1 : 0;
+    a.wall_z = S.wall_z;
     {
       const double s2 = (double)S.A * (double)S.A / 3.0;
       a.sig = (float)std::sqrt(s2);
@@ -279,11 +281,12 @@ void build_args(soma_handle* h) {
   h->batches.clear();
   h->batch_members.clear();
   if (h->n_sys > 1) {
-    // a group holds one move kind (the batch kernel is specialised on it)
-    for (int kind = SOMA_MOVE_UNIFORM; kind <= SOMA_MOVE_SMART; ++kind) {
+    // a group holds one move kind and one z boundary (the batch kernel is
+    // specialised on both)
+    for (int kind = 0; kind < 4; ++kind) {
       std::vector<int> reg;
       for (int s = 0; s < h->n_sys; ++s)
-        if (h->host_sys[s].P && h->desc[s].move == kind) reg.push_back(s);
+        if (h->host_sys[s].P && h->desc[s].move == (kind & 1) && h->desc[s].wall_z == (kind >> 1)) reg.push_back(s);
       for (size_t g0 = 0; g0 < reg.size(); g0 += kMaxBatch) {
         BatchArgs b;
         std::memset(&b, 0, sizeof(b));
@@ -559,7 +562,7 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   if (o.precision == SOMA_PREC_FP64) {
     if (n_sys != 1) return SOMA_EINVAL;  // the FP64 form steps one system per handle
     for (int s = 0; s < n_sys; ++s)
-      if (sys[s].N > 64 || sys[s].move != SOMA_MOVE_UNIFORM) return SOMA_ENOTSUP;
+      if (sys[s].N > 64 || sys[s].move != SOMA_MOVE_UNIFORM || sys[s].wall_z) return SOMA_ENOTSUP;
   }
   for (int s = 0; s < n_sys; ++s)
     if (sys[s].move == SOMA_MOVE_SMART && sys[s].N > 64) return SOMA_ENOTSUP;
@@ -614,6 +617,7 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
     S.ny = d.grid[1];
     S.nz = d.grid[2];
     S.sys_index = d.system_id;
+    S.wall_z = d.wall_z;
     S.n_b = (int64_t)d.n_poly * d.N;
     S.n_c = (int64_t)d.grid[0] * d.grid[1] * d.grid[2];
     for (int a = 0; a < 3; ++a) {

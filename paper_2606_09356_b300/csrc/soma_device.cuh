@@ -82,13 +82,22 @@ __device__ __forceinline__ int try_move(const SysDev& S, const float* __restrict
   const float dz = S.A * fmaf((float)(r.z >> 8), 0x1p-23f, -1.0f);
   const float sx = wa * min_image(x - ax, S.L[0], S.invL[0]) + wb * min_image(x - bx, S.L[0], S.invL[0]);
   const float sy = wa * min_image(y - ay, S.L[1], S.invL[1]) + wb * min_image(y - by, S.L[1], S.invL[1]);
-  const float sz = wa * min_image(z - az, S.L[2], S.invL[2]) + wb * min_image(z - bz, S.L[2], S.invL[2]);
+  // z between hard walls (S.wall_z): plain differences, no wrap
+  const float sz = S.wall_z ? wa * (z - az) + wb * (z - bz)
+                            : wa * min_image(z - az, S.L[2], S.invL[2]) + wb * min_image(z - bz, S.L[2], S.invL[2]);
   const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float dEb = fmaf(2.f, fmaf(dx, sx, fmaf(dy, sy, dz * sz)), (wa + wb) * d2);
   int ex, ey, ez;
   const float px = wrap_coord(x + dx, S.L[0], ex);
   const float py = wrap_coord(y + dy, S.L[1], ey);
-  const float pz = wrap_coord(z + dz, S.L[2], ez);
+  float pz;
+  if (S.wall_z) {
+    pz = z + dz;
+    ez = 0;
+    if (!(pz >= 0.f && pz < S.L[2])) return 0;  // through a wall: rejected
+  } else {
+    pz = wrap_coord(z + dz, S.L[2], ez);
+  }
   const int cnew = cell_of(S, px, py, pz);
   const float dE = fmaf(S.kb, dEb, __ldg(wt + cnew) - __ldg(wt + cell));
   // Metropolis: accept iff dE + ln u < 0 with u = ((r_3 >> 9) + 1/2) 2^-23 in

@@ -47,6 +47,7 @@ struct alignas(16) SysDev {
   float* phi_target;            // [2 types][n_c], allocated on first use
   float umbN_N;
   int32_t umbrella;             // 1: the restraint is on
+  int32_t wall_z;               // 1: hard walls at z = 0 and z = L_z (z not periodic)
 };
 
 // Everything the move kernel needs for one system, passed by value as a
@@ -75,7 +76,7 @@ struct MoveArgs {
   // bond-force-biased proposal d = -drift s + sig xi, s the sum of the bead's
   // bond vectors, xi standard normal; s2 = A^2/3, drift = s2 k_b, sig = sqrt(s2)
   float sig, drift, inv2s2;  // inv2s2 = 1 / (2 s2)
-  float pad2;
+  int32_t wall_z;            // 1: hard walls at z = 0 and z = L_z (host-side flag; kernels are templated)
 };
 
 // Up to kMaxBatch systems stepped by one persistent launch: their constants

@@ -189,7 +189,8 @@ __global__ void k_set_step(unsigned long long* counters, int n_sys, unsigned lon
 // word pairs (0,1) and (2,3).  Accumulated in FP64, then wrapped.
 // ---------------------------------------------------------------------------
 // Chain c (logical = storage slot) from bead 0 at (X, Y, Z): the bonds of
-// the initial configuration, accumulated in FP64, wrapped, written.
+// the initial configuration, accumulated in FP64, wrapped (z folded between
+// walls), written.
 __device__ void grow_chain(const SysDev& S, int c, double X, double Y, double Z) {
   const int N = S.N;
   const double sigma = N > 1 ? sqrt(1.0 / (3.0 * (N - 1))) : 0.0;
@@ -212,6 +213,16 @@ __device__ void grow_chain(const SysDev& S, int c, double X, double Y, double Z)
     short im[3];
     for (int a = 0; a < 3; ++a) {
       const double L = (double)S.L[a];
+      if (a == 2 && S.wall_z) {
+        // between walls: folded into [0, L) by mirror reflection, no image
+        const double t = P[a] - 2.0 * L * floor(P[a] / (2.0 * L));
+        float zw = (float)(t < L ? t : 2.0 * L - t);
+        if (zw >= S.L[a]) zw = nextafterf(S.L[a], 0.f);
+        if (zw < 0.f) zw = 0.f;
+        dst[a][b] = zw;
+        im[a] = 0;
+        continue;
+      }
       double n = floor(P[a] / L);
       float xw = (float)(P[a] - n * L);
       if (xw >= S.L[a]) { xw = 0.f; n += 1.0; }

@@ -226,9 +226,33 @@ __device__ __forceinline__ float normal_of_word(uint32_t w) {
   return upper ? -v : v;
 }
 
+// z component of a bond vector: minimum image, or the plain difference
+// between hard walls (kWall: z is not periodic).
+template <bool kWall>
+__device__ __forceinline__ float bond_z(float d, const MoveArgs& a) {
+  return kWall ? d : min_image(d, a.L[2], a.invL[2]);
+}
+
+// Proposed z of the two beads: wrapped into [0, L) (periodic), or, between
+// walls, kept where it is when it would leave [0, L) (in_e / in_o false: the
+// move is rejected; the old z keeps the cell lookup inside the grid).
+template <bool kWall>
+__device__ __forceinline__ float2 propose_z(const MoveArgs& a, float ze, float zo, float2 dZ, float2& fZ, bool& in_e,
+                                            bool& in_o) {
+  const float2 q = __fadd2_rn(make_float2(ze, zo), dZ);
+  if (kWall) {
+    in_e = q.x >= 0.f && q.x < a.L[2];
+    in_o = q.y >= 0.f && q.y < a.L[2];
+    fZ = make_float2(0.f, 0.f);
+    return make_float2(in_e ? q.x : ze, in_o ? q.y : zo);
+  }
+  in_e = in_o = true;
+  return wrap_step2(q, a.L[2], a.Lm[2], fZ);
+}
+
 // The bead pair of one lane: positions in, decisions, final cells and image
 // codes out.  Uniform proposals (Sec. 2.1, step (a)).
-template <bool kFromCounts>
+template <bool kFromCounts, bool kWall>
 __device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, const uint2* __restrict__ prev,
                                              uint32_t cid, int k, int e, int o,
                                              int te, int to, bool he, bool ho, float& xe, float& ye, float& ze,
@@ -252,7 +276,8 @@ __device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, co
   float2 fX, fY, fZ;
   const float2 pX = wrap_step2(__fadd2_rn(make_float2(xe, xo), dX), a.L[0], a.Lm[0], fX);
   const float2 pY = wrap_step2(__fadd2_rn(make_float2(ye, yo), dY), a.L[1], a.Lm[1], fY);
-  const float2 pZ = wrap_step2(__fadd2_rn(make_float2(ze, zo), dZ), a.L[2], a.Lm[2], fZ);
+  bool in_e, in_o;
+  const float2 pZ = propose_z<kWall>(a, ze, zo, dZ, fZ, in_e, in_o);
   const float2 wr = __ffma2_rn(make_float2(9.f, 9.f), fZ, __ffma2_rn(make_float2(3.f, 3.f), fY, fX));
   wrap_e = wr.x;
   wrap_o = wr.y;
@@ -283,10 +308,10 @@ __device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, co
   const float lz = __shfl_up_sync(0xffffffffu, zo, 1, P);
   const float bLx = min_image(xe - lx, a.L[0], a.invL[0]);
   const float bLy = min_image(ye - ly, a.L[1], a.invL[1]);
-  const float bLz = min_image(ze - lz, a.L[2], a.invL[2]);
+  const float bLz = bond_z<kWall>(ze - lz, a);
   const float bRx = min_image(xe - xo, a.L[0], a.invL[0]);
   const float bRy = min_image(ye - yo, a.L[1], a.invL[1]);
-  const float bRz = min_image(ze - zo, a.L[2], a.invL[2]);
+  const float bRz = bond_z<kWall>(ze - zo, a);
   const float sx = fmaf(wL0, bLx, wR0 * bRx), sy = fmaf(wL0, bLy, wR0 * bRy), sz = fmaf(wL0, bLz, wR0 * bRz);
   const float d2 = fmaf(dex, dex, fmaf(dey, dey, dez * dez));
   const float dEb = fmaf(2.f, fmaf(dex, sx, fmaf(dey, sy, dez * sz)), (wL0 + wR0) * d2);
@@ -294,7 +319,7 @@ __device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, co
   // accept iff dE + ln u < 0, u = ((r3 >> 9) + 1/2) 2^-23 in (0, 1),
   // evaluated as dE log2(e) + log2(u) < 0
   const float u = fmaf((float)(re.w >> 9), 0x1p-23f, 0x1p-24f);
-  acc = he && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
+  acc = he && in_e && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
   // displacement actually applied to bead e (0 if rejected)
   const float ax = acc ? dex : 0.f, ay = acc ? dey : 0.f, az = acc ? dez : 0.f;
   if (acc) {
@@ -310,7 +335,7 @@ __device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, co
   const float dEbo = fmaf(2.f, fmaf(dox, ox, fmaf(doy, oy, doz * oz)), (1.f + wR1) * o2);
   const float dEo = fmaf(a.kb, dEbo, fo);
   const float uo = fmaf((float)(ro.w >> 9), 0x1p-23f, 0x1p-24f);
-  acco = ho && (fmaf(dEo, kLog2e, __log2f(uo)) < 0.f);
+  acco = ho && in_o && (fmaf(dEo, kLog2e, __log2f(uo)) < 0.f);
   if (acco) {
     xo = pox; yo = poy; zo = poz;
   }
@@ -329,7 +354,7 @@ __device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, co
 // bond vector is minimum-imaged, so |s| <= L per axis and, with the bounds
 // the host enforces (drift <= k_b A^2/3 <= 1/2, 6 sig < L/2), a proposal
 // stays within one image of the box.
-template <bool kFromCounts>
+template <bool kFromCounts, bool kWall>
 __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, const uint2* __restrict__ prev,
                                            uint32_t cid, int k, int e, int o,
                                            int te, int to, bool he, bool ho, float& xe, float& ye, float& ze,
@@ -348,10 +373,10 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, cons
   const float lz = __shfl_up_sync(0xffffffffu, zo, 1, P);
   const float bLx = min_image(xe - lx, a.L[0], a.invL[0]);
   const float bLy = min_image(ye - ly, a.L[1], a.invL[1]);
-  const float bLz = min_image(ze - lz, a.L[2], a.invL[2]);
+  const float bLz = bond_z<kWall>(ze - lz, a);
   const float bRx = min_image(xe - xo, a.L[0], a.invL[0]);
   const float bRy = min_image(ye - yo, a.L[1], a.invL[1]);
-  const float bRz = min_image(ze - zo, a.L[2], a.invL[2]);
+  const float bRz = bond_z<kWall>(ze - zo, a);
   const float sx = fmaf(wL0, bLx, wR0 * bRx), sy = fmaf(wL0, bLy, wR0 * bRy), sz = fmaf(wL0, bLz, wR0 * bRz);
   const float n0 = wL0 + wR0;
   const float fex = a.sig * normal_of_word(re.x);
@@ -363,7 +388,16 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, cons
   float fx, fy, fz;
   const float pex = wrap_step(xe + dex, a.L[0], a.Lm[0], fx);
   const float pey = wrap_step(ye + dey, a.L[1], a.Lm[1], fy);
-  const float pez = wrap_step(ze + dez, a.L[2], a.Lm[2], fz);
+  bool in_e = true, in_o = true;
+  float pez;
+  if (kWall) {
+    const float q = ze + dez;
+    in_e = q >= 0.f && q < a.L[2];
+    pez = in_e ? q : ze;
+    fz = 0.f;
+  } else {
+    pez = wrap_step(ze + dez, a.L[2], a.Lm[2], fz);
+  }
   wrap_e = fmaf(9.f, fz, fmaf(3.f, fy, fx));
   const int ce0 = cell_idx(a, xe, ye, ze), ce1 = cell_idx(a, pex, pey, pez);
   const int co0 = cell_idx(a, xo, yo, zo);
@@ -390,7 +424,7 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, cons
     const float fwd = fmaf(fex, fex, fmaf(fey, fey, fez * fez));
     const float dE = fmaf(a.kb, dEb, fe) + (rev - fwd) * a.inv2s2;
     const float u = fmaf((float)(re.w >> 9), 0x1p-23f, 0x1p-24f);
-    acc = he && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
+    acc = he && in_e && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
   }
   const float ax = acc ? dex : 0.f, ay = acc ? dey : 0.f, az = acc ? dez : 0.f;
   if (acc) {
@@ -402,7 +436,7 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, cons
   const float qz = __shfl_down_sync(0xffffffffu, bLz + az, 1, P);
   const float ox = fmaf(wR1, min_image(-qx, a.L[0], a.invL[0]), min_image(-(bRx + ax), a.L[0], a.invL[0]));
   const float oy = fmaf(wR1, min_image(-qy, a.L[1], a.invL[1]), min_image(-(bRy + ay), a.L[1], a.invL[1]));
-  const float oz = fmaf(wR1, min_image(-qz, a.L[2], a.invL[2]), min_image(-(bRz + az), a.L[2], a.invL[2]));
+  const float oz = fmaf(wR1, bond_z<kWall>(-qz, a), bond_z<kWall>(-(bRz + az), a));
   const float n1 = 1.f + wR1;
   const float fox = a.sig * normal_of_word(ro.x);
   const float foy = a.sig * normal_of_word(ro.y);
@@ -412,7 +446,15 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, cons
   const float doz = fmaf(-a.drift, oz, foz);
   const float pox = wrap_step(xo + dox, a.L[0], a.Lm[0], fx);
   const float poy = wrap_step(yo + doy, a.L[1], a.Lm[1], fy);
-  const float poz = wrap_step(zo + doz, a.L[2], a.Lm[2], fz);
+  float poz;
+  if (kWall) {
+    const float q = zo + doz;
+    in_o = q >= 0.f && q < a.L[2];
+    poz = in_o ? q : zo;
+    fz = 0.f;
+  } else {
+    poz = wrap_step(zo + doz, a.L[2], a.Lm[2], fz);
+  }
   wrap_o = fmaf(9.f, fz, fmaf(3.f, fy, fx));
   const int co1 = cell_idx(a, pox, poy, poz);
   float fo;
@@ -430,7 +472,7 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, cons
     const float fwd = fmaf(fox, fox, fmaf(foy, foy, foz * foz));
     const float dE = fmaf(a.kb, dEb, fo) + (rev - fwd) * a.inv2s2;
     const float u = fmaf((float)(ro.w >> 9), 0x1p-23f, 0x1p-24f);
-    acco = ho && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
+    acco = ho && in_o && (fmaf(dE, kLog2e, __log2f(u)) < 0.f);
   }
   if (acco) {
     xo = pox; yo = poy; zo = poz;
@@ -443,7 +485,7 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, cons
 // it, moves the even then the odd beads of its chains, writes back, bins.
 // Returns the number of accepted moves of this lane.
 // prev: count buffer of step t-1 (fields), cur: count buffer of step t (histogram).
-template <bool kFromCounts, bool kSmart>
+template <bool kFromCounts, bool kSmart, bool kWall>
 __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, const MoveStage& st, uint64_t* empty,
                                                  long long tl, const uint2* __restrict__ prev,
                                                  uint32_t* __restrict__ cur, int warp, int lane) {
@@ -477,10 +519,10 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   int ce, co;
   float wrap_e, wrap_o;
   if (kSmart)
-    smart_pair<kFromCounts>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co, wrap_e,
+    smart_pair<kFromCounts, kWall>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co, wrap_e,
                             wrap_o);
   else
-    uniform_pair<kFromCounts>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co,
+    uniform_pair<kFromCounts, kWall>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co,
                               wrap_e, wrap_o);
 
 #ifdef SOMA_DEBUG
@@ -539,7 +581,7 @@ __device__ __forceinline__ void drain(uint64_t* full, int issued, int* err) {
 }
 
 // Register budget for 3 resident CTAs per SM (72 registers, no spill).
-template <bool kFromCounts, bool kSmart>
+template <bool kFromCounts, bool kSmart, bool kWall>
 __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __grid_constant__ MoveArgs a, StepRef r) {
   __shared__ MoveStage stage[kStages];
   __shared__ __align__(8) uint64_t full[kStages];
@@ -568,7 +610,7 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __g
   for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
     const int s = it % kStages;
     if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, a.err)) break;
-    nacc += consume_tile<kFromCounts, kSmart>(a, tile, stage[s], &empty[s], tl, prev, cur, warp, lane);
+    nacc += consume_tile<kFromCounts, kSmart, kWall>(a, tile, stage[s], &empty[s], tl, prev, cur, warp, lane);
   }
   nacc = __reduce_add_sync(0xffffffffu, nacc);
   if (lane == 0 && nacc) atomicAdd(a.acc + blockIdx.x, (unsigned long long)nacc);
@@ -588,8 +630,8 @@ __device__ __forceinline__ int batch_system(const BatchArgs& p, int tile) {
   return lo;
 }
 
-// One move kind per launch (the host groups systems by kind).
-template <bool kSmart>
+// One move kind and one z boundary per launch (the host groups systems so).
+template <bool kSmart, bool kWall>
 __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
     k_move_batch(const __grid_constant__ BatchArgs p, StepRef r) {
   __shared__ MoveStage stage[kStages];
@@ -625,8 +667,8 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
     uint32_t* cur = count_buffer(a.counts, a.n_c, tl);
     const int lt = tile - p.tile_start[sys];
     unsigned n = a.from_counts
-                     ? consume_tile<true, kSmart>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
-                     : consume_tile<false, kSmart>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
+                     ? consume_tile<true, kSmart, kWall>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
+                     : consume_tile<false, kSmart, kWall>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
     n = __reduce_add_sync(0xffffffffu, n);
     if (lane == 0 && n) atomicAdd(a.acc + blockIdx.x, (unsigned long long)n);
   }
@@ -658,7 +700,7 @@ cudaError_t launch_wait_selfcheck(int* err, long long cycles, cudaStream_t s) {
 int move_kernel_max_ctas_per_sm() {
   int n = 0;
   const cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<true, false>, (kConsumerWarps + 1) * 32, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<true, false, false>, (kConsumerWarps + 1) * 32, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -670,31 +712,31 @@ int move_kernel_chains_per_tile(int P) { return kConsumerWarps * (32 / P); }
 
 cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s) {
   const int threads = (kConsumerWarps + 1) * 32;
-  if (a.smart) {
-    if (from_counts)
-      k_move<true, true><<<grid, threads, 0, s>>>(a, r);
-    else
-      k_move<false, true><<<grid, threads, 0, s>>>(a, r);
-  } else {
-    if (from_counts)
-      k_move<true, false><<<grid, threads, 0, s>>>(a, r);
-    else
-      k_move<false, false><<<grid, threads, 0, s>>>(a, r);
-  }
+  using Kernel = void (*)(MoveArgs, StepRef);
+  // [smart][wall][from_counts]
+  static const Kernel table[2][2][2] = {
+      {{k_move<false, false, false>, k_move<true, false, false>},
+       {k_move<false, false, true>, k_move<true, false, true>}},
+      {{k_move<false, true, false>, k_move<true, true, false>},
+       {k_move<false, true, true>, k_move<true, true, true>}}};
+  const Kernel k = table[a.smart ? 1 : 0][a.wall_z ? 1 : 0][from_counts ? 1 : 0];
+  k<<<grid, threads, 0, s>>>(a, r);
   return cudaGetLastError();
 }
 
 cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStream_t s) {
-  if (p.n_sys > 0 && p.sys[0].smart)
-    k_move_batch<true><<<grid, (kConsumerWarps + 1) * 32, 0, s>>>(p, r);
+  const bool smart = p.n_sys > 0 && p.sys[0].smart, wall = p.n_sys > 0 && p.sys[0].wall_z;
+  const int threads = (kConsumerWarps + 1) * 32;
+  if (smart)
+    wall ? k_move_batch<true, true><<<grid, threads, 0, s>>>(p, r) : k_move_batch<true, false><<<grid, threads, 0, s>>>(p, r);
   else
-    k_move_batch<false><<<grid, (kConsumerWarps + 1) * 32, 0, s>>>(p, r);
+    wall ? k_move_batch<false, true><<<grid, threads, 0, s>>>(p, r) : k_move_batch<false, false><<<grid, threads, 0, s>>>(p, r);
   return cudaGetLastError();
 }
 
 int move_batch_max_ctas_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move_batch<false>, (kConsumerWarps + 1) * 32, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move_batch<false, false>, (kConsumerWarps + 1) * 32, 0) !=
       cudaSuccess) {
     cudaGetLastError();
     return 1;

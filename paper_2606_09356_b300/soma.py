@@ -57,7 +57,8 @@ class soma_system_desc(ctypes.Structure):
         ("n_poly", ctypes.c_int32), ("N", ctypes.c_int32), ("n_A", ctypes.c_int32),
         ("system_id", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("move", ctypes.c_int32),
         ("box", ctypes.c_double * 3), ("chiN", ctypes.c_double), ("kappaN", ctypes.c_double),
-        ("A", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("A", ctypes.c_double), ("seed", ctypes.c_uint64), ("wall_z", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -223,10 +224,11 @@ class System:
     """One AB diblock melt (the fields of soma_system_desc)."""
 
     def __init__(self, n_poly, N, n_A, box, grid, chiN, kappaN, A=0.0, seed=1, system_id=0,
-                 move=SOMA_MOVE_UNIFORM):
+                 move=SOMA_MOVE_UNIFORM, wall_z=0):
         self.n_poly, self.N, self.n_A = int(n_poly), int(N), int(n_A)
         self.system_id = int(system_id)
         self.move = int(move)
+        self.wall_z = int(wall_z)
         self.box = tuple(float(b) for b in box)
         self.grid = tuple(int(g) for g in grid)
         self.chiN, self.kappaN, self.A, self.seed = float(chiN), float(kappaN), float(A), int(seed)
@@ -243,6 +245,7 @@ class System:
         d = soma_system_desc()
         d.n_poly, d.N, d.n_A, d.system_id = self.n_poly, self.N, self.n_A, self.system_id
         d.move = self.move
+        d.wall_z = self.wall_z
         for a in range(3):
             d.grid[a] = self.grid[a]
             d.box[a] = self.box[a]

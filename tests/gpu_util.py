@@ -18,7 +18,8 @@ def lib():
 
 def oracle_for(system):
     return Oracle(system.n_poly, system.N, system.n_A, system.box, system.grid, system.chiN, system.kappaN,
-                  A=system.A, seed=system.seed, sys_index=system.system_id, move=system.move)
+                  A=system.A, seed=system.seed, sys_index=system.system_id, move=system.move,
+                  wall_z=system.wall_z)
 
 
 def unwrapped(h, sys=0):

@@ -81,6 +81,7 @@ def test_strerror_and_defaults(lib):
     dict(A=5.0),                        # proposal wider than the box
     dict(chiN=float("nan")),
     dict(move=2),                       # unknown move kind
+    dict(wall_z=2),                     # unknown z boundary
     dict(move=1, A=0.2),                # smart: drift A^2 (N-1)/2 above 1/2
     dict(move=1, N=1, n_A=1, A=0.7, box=(4.5, 4.5, 4.5)),  # smart: Gaussian tail wider than half the box
 ])
@@ -97,6 +98,7 @@ def test_create_rejects_bad_descriptors_without_gpu(lib, bad):
 @pytest.mark.parametrize("kw,opts", [
     (dict(N=80, n_A=40, move=1), None),                          # smart moves: register path only
     (dict(N=32, n_A=16, move=1), dict(precision=1)),             # smart moves: FP32 form only
+    (dict(N=32, n_A=16, wall_z=1), dict(precision=1)),           # walls: FP32 form only
 ])
 def test_create_rejects_unsupported_smart_moves_without_gpu(lib, kw, opts):
     d = soma.System(n_poly=8, box=(4.0, 4.0, 4.0), grid=(4, 4, 4), chiN=1.0, kappaN=1.0, **kw).desc()
