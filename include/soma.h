@@ -108,7 +108,9 @@ typedef void (*soma_free_fn)(void* ptr, void* ctx);
 
 typedef struct soma_options {
   int32_t device;        /* CUDA device ordinal; -1 = the current device */
-  int32_t sort_interval; /* steps between chain reorders; 0 = never; -1 = tuned */
+  int32_t sort_interval; /* steps between chain reorders; 0 = never; -1 = tuned by the
+                            autotuner (reorder cost against the step-time drift
+                            after a reorder), 200 until it runs */
   int32_t ctas_per_sm;   /* resident CTAs per SM of the persistent move kernel; 0 = as many as fit */
   int32_t hist_mode;     /* SOMA_HIST_* */
   int32_t graph_steps;   /* steps per captured CUDA graph; 0 = plain launches */

@@ -1269,10 +1269,56 @@ int soma_autotune(soma_handle* h) {
       if ((rc = restore())) return rc;
     }
   }
+  apply_geometry(h, best_c, best_h);
+
+  // Sort interval (opt.sort_interval < 0): time one chain reorder, then the
+  // step time at growing distances j from it (chains drift out of cell
+  // order as they move); the interval K of least average cost per step,
+  // (t_sort + sum_{i<K} t(i)) / K with t linear between the marks, wins.
+  if (h->opt.sort_interval < 0 && !h->f64) {
+    float t_sort = 0.f;
+    CK(cudaEventRecord(a, h->stream));
+    if ((rc = enqueue_reorder(h, h->stream))) return rc;
+    CK(cudaEventRecord(b, h->stream));
+    CK(cudaEventSynchronize(b));
+    CK(cudaEventElapsedTime(&t_sort, a, b));
+    const int marks[] = {0, 32, 64, 128, 256, 512, 1024};
+    const int n_marks = (int)(sizeof(marks) / sizeof(marks[0]));
+    float t_at[n_marks];
+    long long done = 0;
+    for (int m = 0; m < n_marks; ++m) {
+      if (marks[m] > done) {
+        if ((rc = enqueue_steps(h, h->stream, (int)(marks[m] - done), false, (long long)step0 + done))) return rc;
+        done = marks[m];
+      }
+      CK(cudaEventRecord(a, h->stream));
+      if ((rc = enqueue_steps(h, h->stream, 8, false, (long long)step0 + done))) return rc;
+      CK(cudaEventRecord(b, h->stream));
+      CK(cudaEventSynchronize(b));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, a, b));
+      t_at[m] = ms / 8.f;
+      done += 8;
+    }
+    if ((rc = restore())) return rc;
+    double best_cost = 1e300;
+    int best_k = h->sort_interval;
+    for (int m = 1; m < n_marks; ++m) {
+      const int K = marks[m];
+      double sum = 0.0;  // trapezoids between the marks up to K
+      for (int j = 1; j <= m; ++j) sum += 0.5 * (t_at[j - 1] + t_at[j]) * (marks[j] - marks[j - 1]);
+      const double cost = (t_sort + sum) / K;
+      if (cost < best_cost) {
+        best_cost = cost;
+        best_k = K;
+      }
+    }
+    h->sort_interval = best_k;
+    if ((rc = enqueue_reorder(h, h->stream))) return rc;  // start the tuned interval sorted
+  }
   h->opt.kernel_timing = timing;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  apply_geometry(h, best_c, best_h);
   return sync_all(h);
 }
 

@@ -41,6 +41,18 @@ def test_launch_shape_histogram_graph_and_reorder_invariance():
         _same(ref, _run(s, 40, **{**dict(graph_steps=0, sort_interval=0), **opts}))
 
 
+def test_tuned_sort_interval_keeps_the_trajectory():
+    s = soma.System(**SMALL)
+    ref = _run(s, 40, graph_steps=0, sort_interval=0)
+    with soma.Handle(s, autotune=1, sort_interval=-1, graph_steps=0) as h:
+        h.mc_steps(40)
+        pos, img, step = h.get_state()
+        k = h.info()["sort_interval"]
+        got = (pos, img, h.get_density(), h.accepted(), step)
+    assert k in (32, 64, 128, 256, 512, 1024)
+    _same(ref, got)
+
+
 def test_batched_equals_plain():
     specs = workloads.batch64()[:5]
     systems = [soma.System(**{k: v for k, v in d.items() if k != "f_A"}) for d in specs]
