@@ -167,12 +167,17 @@ void orc_params(const orc_desc* d, double* k_b, double* A_eff, double* rho_bar) 
 }
 
 // Cell of a position: wrap into [0, L) per axis, scale by n/L, floor, clamp.
+// Reading (precision of the lookup): the wrapped coordinate and the scale
+// n/L are taken to FP32 and multiplied in FP32 before the floor, the
+// precision the positions are stored in; where the spacing L/n is a power
+// of two (every workload here) this equals the exact FP64 result.
 static int64_t cell_of(const orc_desc* d, const double r[3]) {
   int64_t idx[3];
   for (int a = 0; a < 3; ++a) {
     double L = d->box[a];
     double xw = r[a] - L * std::floor(r[a] / L);
-    int64_t i = (int64_t)std::floor(xw * ((double)d->grid[a] / L));
+    const float scaled = (float)xw * (float)((double)d->grid[a] / L);
+    int64_t i = (int64_t)std::floor((double)scaled);
     if (i > d->grid[a] - 1) i = d->grid[a] - 1;
     if (i < 0) i = 0;
     idx[a] = i;

@@ -71,6 +71,10 @@ def test_step_parity_config0_ten_steps():
     dict(n_poly=9, N=33, n_A=33, box=(2.0, 2.0, 2.0), grid=(4, 4, 4), chiN=0.0, kappaN=30.0),       # homopolymer
     dict(n_poly=1, N=2, n_A=1, box=(12.0, 12.0, 12.0), grid=(3, 3, 3), chiN=5.0, kappaN=5.0),       # a single dimer
     dict(n_poly=200, N=1, n_A=1, box=(2.0, 2.0, 2.0), grid=(4, 4, 4), chiN=5.0, kappaN=10.0, A=0.3),  # monomers
+    dict(n_poly=300, N=24, n_A=9, box=(3.0, 3.3, 2.9), grid=(7, 11, 9), chiN=18.0, kappaN=45.0),     # non-dyadic cells
+    dict(n_poly=64, N=16, n_A=8, box=(4.0, 4.0, 4.0), grid=(1, 1, 1), chiN=20.0, kappaN=50.0),      # a single cell
+    dict(n_poly=70, N=63, n_A=0, box=(2.0, 2.0, 2.0), grid=(8, 8, 8), chiN=20.0, kappaN=50.0),      # odd N, P = 32, all B
+    dict(n_poly=3, N=4096, n_A=1000, box=(1.0, 1.0, 1.0), grid=(8, 8, 8), chiN=20.0, kappaN=50.0),  # longest chains
 ])
 @pytest.mark.parametrize("ctas", [1, 3])
 def test_step_parity_shapes(kw, ctas):
