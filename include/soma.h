@@ -193,8 +193,11 @@ int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int wh
  * type-t bead in cell c from the next step on.  phi_target == NULL or
  * lambdaN == 0 turns it off.  lambdaN must be finite and >= 0
  * (SOMA_EINVAL); n must be 2 n_cells when on (SOMA_EINVAL); target values
- * are not checked.  While on, each step fills the field array from the
- * previous counts before the move kernel (one more launch per step).
+ * are not checked.  The restraint enters every field build after the call;
+ * fields already supplied for the next step by soma_set_density, or held by
+ * soma_freeze_fields, stay as given.  While on, each step fills the field
+ * array from the previous counts before the move kernel (one more launch per
+ * step).
  * soma_observables' Enb excludes the restraint.  SOMA_ENOTSUP on
  * SOMA_PREC_FP64 handles.  Synchronises. */
 int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n, double lambdaN, int where);
@@ -207,7 +210,9 @@ int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n
  * so within R_e/2 of it (Sec. 3.2); the chain keeps the Gaussian
  * conformation of the initial configuration.  Random numbers: Philox
  * counters (j, c, 0xFFFFFFFE, system_id), j = 0, 1, 2.  The step counter is
- * kept; counts, fields and acceptance counters restart from the new state.
+ * kept; counts and fields are rebuilt from the new state, and the
+ * acceptance counters of every system of the handle restart (as after
+ * soma_set_state).
  * SOMA_EINVAL (state kept) when the weights of bead 0's type sum to zero or
  * n != 2 n_cells; SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises. */
 int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int where);
@@ -220,7 +225,8 @@ int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int wh
  * [n_beads][3] int16, and the step counter, in logical chain order. */
 int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* step, int where);
 /* Restore: positions must lie in [0, L) per axis; resets the acceptance
- * counters and re-bins; the step counter is shared by all systems. */
+ * counters of every system of the handle and re-bins; the step counter is
+ * shared by all systems. */
 int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img, uint64_t step,
                    int where);
 

@@ -1087,10 +1087,9 @@ int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n
   build_args(h);
   drop_graph(h);
   // the field array (read by the generic move and by the next step when the
-  // restraint is on) follows the new functional at once
-  if (h->phi_pending[sys])
-    CK(launch_field_from_phi(h->d_sys, sys, h->d_stage_phi + 0, h->sm_count, h->stream));
-  else if (!S.frozen)
+  // restraint is on) follows the new functional at once; fields the caller
+  // supplied for the next step (soma_set_density) or holds stay as given
+  if (!h->phi_pending[sys] && !S.frozen)
     CK(launch_field(h->fargs[sys], fixed_step((long long)h->step - 1), 0, h->stream));
   return sync_all(h);
 }
