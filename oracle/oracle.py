@@ -41,7 +41,7 @@ class OrcDesc(ctypes.Structure):
         ("A", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("wall_z", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("pos64", ctypes.c_int32),
     ]
 
 
@@ -107,11 +107,13 @@ class Oracle:
             cls._lib = L
         return cls._lib
 
-    def __init__(self, n_poly, N, n_A, box, grid, chiN, kappaN, A=0.0, seed=1, sys_index=0, move=0, wall_z=0):
+    def __init__(self, n_poly, N, n_A, box, grid, chiN, kappaN, A=0.0, seed=1, sys_index=0, move=0, wall_z=0,
+                 pos64=0):
         self.d = OrcDesc()
         self.d.n_poly, self.d.N, self.d.n_A, self.d.sys_index = n_poly, N, n_A, sys_index
         self.d.move = int(move)
         self.d.wall_z = int(wall_z)
+        self.d.pos64 = int(pos64)
         for a in range(3):
             self.d.grid[a] = int(grid[a])
             self.d.box[a] = float(box[a])

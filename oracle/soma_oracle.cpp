@@ -66,7 +66,7 @@ typedef struct {
   double A;           // proposal half-width; A <= 0 means 0.5/sqrt(N-1)
   uint64_t seed;      // Philox key (lo, hi)
   int32_t wall_z;     // 1: hard walls at z = 0 and z = L_z instead of periodic z
-  int32_t reserved;
+  int32_t pos64;      // 1: positions are held in FP64 (cell lookup in FP64), 0: in FP32
 } orc_desc;
 
 typedef struct {
@@ -167,17 +167,19 @@ void orc_params(const orc_desc* d, double* k_b, double* A_eff, double* rho_bar) 
 }
 
 // Cell of a position: wrap into [0, L) per axis, scale by n/L, floor, clamp.
-// Reading (precision of the lookup): the wrapped coordinate and the scale
-// n/L are taken to FP32 and multiplied in FP32 before the floor, the
-// precision the positions are stored in; where the spacing L/n is a power
-// of two (every workload here) this equals the exact FP64 result.
+// Reading (precision of the lookup): the product is formed in the precision
+// the positions are stored in -- in FP32 from the FP32-rounded coordinate and
+// scale for the FP32 form, in FP64 for the FP64-position form.  For a
+// coordinate that is an FP32 value and a power-of-two spacing L/n (every
+// workload here) the two agree and equal the exact floor.
 static int64_t cell_of(const orc_desc* d, const double r[3]) {
   int64_t idx[3];
   for (int a = 0; a < 3; ++a) {
     double L = d->box[a];
     double xw = r[a] - L * std::floor(r[a] / L);
-    const float scaled = (float)xw * (float)((double)d->grid[a] / L);
-    int64_t i = (int64_t)std::floor((double)scaled);
+    const double scaled = d->pos64 ? xw * ((double)d->grid[a] / L)
+                                   : (double)((float)xw * (float)((double)d->grid[a] / L));
+    int64_t i = (int64_t)std::floor(scaled);
     if (i > d->grid[a] - 1) i = d->grid[a] - 1;
     if (i < 0) i = 0;
     idx[a] = i;

@@ -519,11 +519,11 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   int ce, co;
   float wrap_e, wrap_o;
   if (kSmart)
-    smart_pair<kFromCounts, kWall>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co, wrap_e,
-                            wrap_o);
+    smart_pair<kFromCounts, kWall>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce,
+                                   co, wrap_e, wrap_o);
   else
-    uniform_pair<kFromCounts, kWall>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco, ce, co,
-                              wrap_e, wrap_o);
+    uniform_pair<kFromCounts, kWall>(a, tl, prev, cid, k, e, o, te, to, he, ho, xe, ye, ze, xo, yo, zo, acc, acco,
+                                     ce, co, wrap_e, wrap_o);
 
 #ifdef SOMA_DEBUG
   // checked build: final cells inside the grid, positions finite in [0, L)
@@ -536,7 +536,7 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   // ---- write back, images on wrap, fused histogram ----
   const int64_t gb = (int64_t)c0 * N + lb;
   if ((N & 1) == 0) {
-    if (he && (acc || acco)) {
+    if (he) {  // unconditional: a rejected pair rewrites its own values, no branch on the outcome
       *reinterpret_cast<float2*>(a.x + gb) = make_float2(xe, xo);
       *reinterpret_cast<float2*>(a.y + gb) = make_float2(ye, yo);
       *reinterpret_cast<float2*>(a.z + gb) = make_float2(ze, zo);
@@ -545,8 +545,12 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
     if (acc) { a.x[gb] = xe; a.y[gb] = ye; a.z[gb] = ze; }
     if (acco) { a.x[gb + 1] = xo; a.y[gb + 1] = yo; a.z[gb + 1] = zo; }
   }
-  if (acc) apply_image_steps(a.img, gb, wrap_e, a.err);
-  if (acco) apply_image_steps(a.img, gb + 1, wrap_o, a.err);
+  // image counters change only when an accepted move crossed the box: one
+  // warp vote skips the update in the common case
+  if (__any_sync(0xffffffffu, (acc && wrap_e != 0.f) || (acco && wrap_o != 0.f))) {
+    if (acc) apply_image_steps(a.img, gb, wrap_e, a.err);
+    if (acco) apply_image_steps(a.img, gb + 1, wrap_o, a.err);
+  }
   if (a.bin) {
     if (he) atomicAdd(cur + 2 * ce + te, 1u);
     if (ho) atomicAdd(cur + 2 * co + to, 1u);

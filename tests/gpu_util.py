@@ -16,10 +16,12 @@ def lib():
     return soma.load_library()
 
 
-def oracle_for(system):
+def oracle_for(system, pos64=False):
+    """The oracle of a system; pos64 selects the FP64 cell lookup of the
+    FP64-position form."""
     return Oracle(system.n_poly, system.N, system.n_A, system.box, system.grid, system.chiN, system.kappaN,
                   A=system.A, seed=system.seed, sys_index=system.system_id, move=system.move,
-                  wall_z=system.wall_z)
+                  wall_z=system.wall_z, pos64=int(pos64))
 
 
 def unwrapped(h, sys=0):

@@ -27,7 +27,7 @@ def _unwrapped64(h):
 
 def test_f64_one_step_tight_parity():
     s = soma.System(**workloads.system_kwargs("config0"))
-    orc = G.oracle_for(s)
+    orc = G.oracle_for(s, pos64=True)
     with soma.Handle(s, **F64) as h:
         for _ in range(5):
             X0, step = _unwrapped64(h)
@@ -47,7 +47,7 @@ def test_f64_one_step_tight_parity():
 
 def test_f64_follows_oracle_for_1000_steps():
     s = soma.System(**workloads.system_kwargs("config0"))
-    orc = G.oracle_for(s)
+    orc = G.oracle_for(s, pos64=True)
     with soma.Handle(s, **F64) as h:
         X, step = _unwrapped64(h)
         res = orc.run(X, step, 1000, n_threads=G.NTHREADS)
