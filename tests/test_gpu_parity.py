@@ -122,12 +122,17 @@ def _sampled_parity(name, n_sample, steps=2, **opts):
         assert np.array_equal(h.get_density(), orc.density(X1))
 
 
+# the launch configuration bench.py times: autotuned shape, plain launches
+# with per-kernel timing events
+BENCH_OPTS = dict(autotune=1, graph_steps=0, kernel_timing=1)
+
+
 def test_step_parity_config1_full_size_sampled():
-    _sampled_parity("config1", 4096)
+    _sampled_parity("config1", 4096, **BENCH_OPTS)
 
 
 def test_step_parity_config2_full_size_sampled():
-    _sampled_parity("config2", 2048, steps=1)
+    _sampled_parity("config2", 2048, steps=1, **BENCH_OPTS)
 
 
 def test_observables_match_oracle():

@@ -74,7 +74,7 @@ def test_smart_step_parity_config1_full_size_sampled():
     ids = np.sort(rng.choice(sysm.n_poly, 2048, replace=False)).astype(np.uint32)
     N = sysm.N
     sel = (ids[:, None].astype(np.int64) * N + np.arange(N)[None, :]).reshape(-1)
-    with soma.Handle(sysm) as h:
+    with soma.Handle(sysm, autotune=1, graph_steps=0, kernel_timing=1) as h:  # as bench.py times it
         h.mc_steps(3)
         X0, step = G.unwrapped(h)
         w = orc.fields(h.get_density())
