@@ -100,10 +100,12 @@ def test_dimer_cell_pair_law_in_frozen_field():
     assert not fails, fails
 
 
-def test_long_run_statistics_agree_with_oracle():
+@pytest.mark.parametrize("move", [soma.SOMA_MOVE_UNIFORM, soma.SOMA_MOVE_SMART])
+def test_long_run_statistics_agree_with_oracle(move):
     """chiN = 20, kappaN = 50 (config 0 shape): <R_e^2>, acceptance and the
-    peak of S(q) from the GPU and the oracle agree within 3 sigma over seeds."""
-    kw = workloads.system_kwargs("config0")
+    peak of S(q) from the GPU and the oracle agree within 3 sigma over seeds,
+    for both trial-move kinds."""
+    kw = {**workloads.system_kwargs("config0"), "move": move}
     m = np.array([(x, y, z) for x in range(-4, 5) for y in range(-4, 5) for z in range(-4, 5)
                   if 0 < x * x + y * y + z * z <= 16], np.int32)
     shells = (m ** 2).sum(1)
