@@ -267,6 +267,12 @@ int soma_autotune(soma_handle* h);
  * device function the move kernel uses).  Synchronous. */
 int soma_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n);
 
+/* The standard normal deviates the smart move draws from n Philox words,
+ * xi = Phi^-1(((w >> 8) + 1/2) 2^-24) as the kernel evaluates it (FP32,
+ * the lower tail of either half through normcdfinvf); words and out are
+ * host buffers of n entries (a verification aid).  Synchronous. */
+int soma_normal_deviates(const uint32_t* words, float* out, size_t n);
+
 /* Failure-path self-check (no counterpart in the paper, which names no
  * fault mechanism): on `device` (-1 = current) one thread waits, with the
  * move kernels' bounded mbarrier wait, on a barrier that nothing arrives

@@ -1130,6 +1130,25 @@ int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int w
   return sync_all(h);
 }
 
+int soma_normal_deviates(const uint32_t* words, float* out, size_t n) {
+  if (n == 0) return SOMA_OK;
+  if (!words || !out) return SOMA_EINVAL;
+  uint32_t* dw = nullptr;
+  float* dout = nullptr;
+  int rc = SOMA_ECUDA;
+  if (cudaMalloc(&dw, n * 4) != cudaSuccess || cudaMalloc(&dout, n * 4) != cudaSuccess) {
+    cudaGetLastError();
+    rc = SOMA_ENOMEM;
+  } else if (cudaMemcpy(dw, words, n * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             launch_normal_words(dw, dout, (int64_t)n, nullptr) == cudaSuccess &&
+             cudaMemcpy(out, dout, n * 4, cudaMemcpyDeviceToHost) == cudaSuccess) {
+    rc = SOMA_OK;
+  }
+  cudaFree(dw);
+  cudaFree(dout);
+  return rc;
+}
+
 int soma_selfcheck_timeout(int device, uint64_t cycles) {
   if (cycles < 1000 || cycles > 20000000000ull) return SOMA_EINVAL;
   if (device >= 0 && cudaSetDevice(device) != cudaSuccess) return SOMA_ECUDA;

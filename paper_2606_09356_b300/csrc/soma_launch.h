@@ -14,6 +14,8 @@ cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStrea
 int move_batch_max_ctas_per_sm();
 int move_kernel_max_ctas_per_sm();
 int move_kernel_chains_per_tile(int P);
+// The smart move's standard normal deviates of n words (verification aid).
+cudaError_t launch_normal_words(const uint32_t* w, float* out, int64_t n, cudaStream_t s);
 // One mbarrier wait that nothing satisfies, bounded by `cycles` (sets kErrTimeout in *err).
 cudaError_t launch_wait_selfcheck(int* err, long long cycles, cudaStream_t s);
 cudaError_t launch_move_generic(const SysDev* systems, int sys, int64_t n_poly, int N, StepRef r, int sm_count,

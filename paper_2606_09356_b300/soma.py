@@ -43,6 +43,7 @@ EXPORTS = (
     "soma_get_state64", "soma_set_state64", "soma_observables", "soma_get_accepted",
     "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
     "soma_philox4x32", "soma_structure_factor_noalloc", "soma_selfcheck_timeout",
+    "soma_normal_deviates",
 )
 
 
@@ -120,6 +121,7 @@ def load_library(path=None):
     L.soma_freeze_fields.argtypes = [vp, i32, vp, sz, i32]
     L.soma_set_umbrella.argtypes = [vp, i32, vp, sz, ctypes.c_double, i32]
     L.soma_selfcheck_timeout.argtypes = [i32, u64]
+    L.soma_normal_deviates.argtypes = [vp, vp, sz]
     L.soma_place.argtypes = [vp, i32, vp, sz, i32]
     L.soma_get_state.argtypes = [vp, i32, vp, vp, ctypes.POINTER(u64), i32]
     L.soma_set_state.argtypes = [vp, i32, vp, vp, u64, i32]
@@ -207,6 +209,14 @@ def soma_structure_factor_noalloc(pos, n_beads, N, n_A, box, m, S, stream=None):
     _check(load_library().soma_structure_factor_noalloc(ctypes.c_void_p(p), int(n_beads), int(N), int(n_A),
                                                          _ptr(box), len(m), _ptr(m), ctypes.c_void_p(q), stream),
            "soma_structure_factor_noalloc")
+
+
+def soma_normal_deviates(words):
+    """The smart move's normal deviates of uint32 words (as the kernel computes them)."""
+    words = np.ascontiguousarray(words, np.uint32)
+    out = np.zeros(words.shape, np.float32)
+    _check(load_library().soma_normal_deviates(_ptr(words), _ptr(out), words.size), "soma_normal_deviates")
+    return out
 
 
 def soma_selfcheck_timeout(device=-1, cycles=200_000_000):

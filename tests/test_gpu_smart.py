@@ -143,3 +143,18 @@ def test_smart_ideal_chains_keep_gaussian_statistics():
     b2 = (np.diff(X, axis=1) ** 2).sum(-1).mean() * (s.N - 1)
     assert abs(b2 - 1.0) < 5 * np.sqrt(2.0 / 3.0 / (s.n_poly * (s.N - 1)))
     assert abs(np.mean(re2) - 1.0) < 5 * np.sqrt(2.0 / 3.0 / s.n_poly)
+
+
+def test_normal_deviates_match_the_exact_quantile():
+    """Every one of the 2^24 arguments: the kernel's FP32 Phi^-1 against the
+    exact quantile, and the mirror symmetry Phi^-1(1 - u) = -Phi^-1(u) bit
+    for bit."""
+    from scipy.special import ndtri
+    m = np.arange(1 << 24, dtype=np.uint32)
+    words = (m << 8) | (m & 0xFF)  # the low 8 bits of a word are not used
+    xi = soma.soma_normal_deviates(words).astype(np.float64)
+    ref = ndtri((m.astype(np.float64) + 0.5) * 2.0 ** -24)
+    err = np.abs(xi - ref)
+    print("max |xi - Phi^-1| =", err.max())
+    assert err.max() <= 2e-6
+    assert np.array_equal(xi[::-1], -xi)
