@@ -238,7 +238,8 @@ int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* 
 
 /* FP64 observables of the current configuration. */
 int soma_observables(soma_handle* h, int sys, soma_obs* out);
-/* Accepted-move counter only (one small device-to-host read). */
+/* Accepted-move counter only (one small device-to-host read, ordered after
+ * the latest soma_mc_steps on whichever stream it was given; waits for it). */
 int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted);
 
 /* S(q) = (1/n_beads) |sum_j s_j exp(i q.r_j)|^2, s_j = +1 (A) / -1 (B), for

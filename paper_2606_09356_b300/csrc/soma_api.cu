@@ -53,6 +53,7 @@ struct soma_handle {
   int device = 0, sm_count = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // dedicated stream for graph capture
+  cudaEvent_t order_ev = nullptr;  // recorded after every soma_mc_steps, on its stream
   soma_options opt{};
   int n_sys = 0;
   std::vector<soma_system_desc> desc;
@@ -533,6 +534,7 @@ int soma_last_error(const soma_handle* h) { return h ? h->sticky : SOMA_EINVAL; 
 
 void soma_destroy(soma_handle* h) {
   if (!h) return;
+  if (h->order_ev) cudaEventSynchronize(h->order_ev);  // steps enqueued on a caller's stream
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& te : h->pending) {
     cudaEventDestroy(te.a);
@@ -542,6 +544,7 @@ void soma_destroy(soma_handle* h) {
   dev_free_all(h);
   if (h->stream) cudaStreamDestroy(h->stream);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->order_ev) cudaEventDestroy(h->order_ev);
   delete h;
 }
 
@@ -591,7 +594,8 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return bail(SOMA_ECUDA);
   h->sm_count = prop.multiProcessorCount;
   if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming) != cudaSuccess)
     return bail(SOMA_ECUDA);
   h->max_ctas_per_sm = move_kernel_max_ctas_per_sm();
   h->max_ctas_batch = move_batch_max_ctas_per_sm();
@@ -803,6 +807,7 @@ int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
     h->step += (uint64_t)chunk;
     h->steps_since_sort += (uint64_t)chunk;
   }
+  CK(cudaEventRecord(h->order_ev, s));
   return SOMA_OK;
 }
 
@@ -993,6 +998,8 @@ int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted) {
   int rc = check_live(h);
   if (rc) return rc;
   if (sys < 0 || sys >= h->n_sys || !accepted) return SOMA_EINVAL;
+  // the steps may have gone to a caller's stream: read after them
+  CK(cudaStreamWaitEvent(h->stream, h->order_ev, 0));
   CK(launch_sum_acc(h->d_sys, sys, h->d_acc_sum, h->stream));
   unsigned long long a = 0;
   CK(cudaMemcpyAsync(&a, h->d_acc_sum, 8, cudaMemcpyDeviceToHost, h->stream));

@@ -91,3 +91,17 @@ def test_many_handles_and_destroy():
     assert not np.array_equal(st[0], st[1])
     for h in hs:
         h.close()
+
+
+def test_accepted_count_is_read_after_steps_on_a_caller_stream():
+    import torch
+    s = soma.System(**workloads.system_kwargs("config1"))
+    st = torch.cuda.Stream()
+    with soma.Handle(s, graph_steps=0) as h:
+        h.mc_steps(1)
+        h.sync()
+        a0 = h.accepted()
+        h.mc_steps(20, stream=st.cuda_stream)
+        a1 = h.accepted()  # ordered after the 20 steps on the caller's stream
+        torch.cuda.synchronize()
+        assert a1 == h.accepted() and a1 > a0
