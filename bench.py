@@ -386,30 +386,38 @@ def run_gpu(args):
     if not args.no_energy:
         energy = measure_energy(soma, torch, c, rank, local, sptr, stream, n_b)
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers: the state
+    # goes up once, every step's accepted count comes down (enqueued behind
+    # its step, one synchronisation at the end), then the final counts
     e2e = None
     if not args.no_e2e:
-        pos, img, step = h.get_state()
+        he = soma.Handle(soma.System(**rank_system_kwargs(args.workload, rank)), device=local, autotune=1,
+                         graph_steps=0)
+        he.mc_steps(args.warmup, stream=sptr)  # tuning and warm-up, untimed
+        torch.cuda.synchronize()
+        pos, img, step = he.get_state()
         pin_pos = torch.from_numpy(pos).pin_memory()
         pin_img = torch.from_numpy(img).pin_memory()
         dens = torch.empty((2, n_c), dtype=torch.int32).pin_memory()
+        accs = torch.zeros(args.steps, dtype=torch.int64).pin_memory()
+        acc_np = accs.numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h.set_state(pin_pos.numpy(), pin_img.numpy(), step)
-        acc = 0
-        for _ in range(args.steps):
-            h.mc_steps(1, stream=sptr)
-            acc = h.accepted()                   # the step's result, 8 bytes to the host
-        h.get_density(out=dens.numpy().view(np.uint32))
+        he.set_state(pin_pos.numpy(), pin_img.numpy(), step)
+        for i in range(args.steps):
+            he.mc_steps(1, stream=sptr)
+            he.copy_accepted(acc_np[i:i + 1], stream=sptr)  # the step's result, 8 bytes to the host
+        he.get_density(out=dens.numpy().view(np.uint32))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        ok = int(acc_np[-1]) == he.accepted() and bool(np.all(np.diff(acc_np) >= 0))
+        he.close()
         h2d = (pos.nbytes + img.nbytes) / args.steps
         d2h = 8 + dens.numel() * 4 / args.steps
         e2e = {"value": args.steps * n_b * ws / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h,
-               "note": "set_state from pinned host, per step soma_mc_steps + soma_get_accepted, "
-                       "then soma_get_density to pinned host; host wall clock"}
-        _ = acc
+               "d2h_bytes_per_step": d2h, "results_consistent": ok,
+               "note": "set_state from pinned host; per step soma_mc_steps + soma_copy_accepted to pinned "
+                       "host (enqueued behind the step); then soma_get_density to pinned host; host wall clock"}
 
     # the bond-force-biased (smart) move on the same workload, timed like the
     # headline (L2 flushed between steps, CUDA events around each step)

@@ -241,6 +241,13 @@ int soma_observables(soma_handle* h, int sys, soma_obs* out);
 /* Accepted-move counter only (one small device-to-host read, ordered after
  * the latest soma_mc_steps on whichever stream it was given; waits for it). */
 int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted);
+/* The same count, enqueued: on `stream` (NULL = the handle's stream), after
+ * the latest soma_mc_steps, the count is reduced on the device and copied to
+ * *dst (host memory; pinned for the copy to be asynchronous).  Returns
+ * without waiting; *dst is valid once the stream has synchronised.  Calls on
+ * one stream complete in order, so a caller may enqueue one per step and
+ * read them all after a single synchronisation. */
+int soma_copy_accepted(soma_handle* h, int sys, uint64_t* dst, void* stream);
 
 /* S(q) = (1/n_beads) |sum_j s_j exp(i q.r_j)|^2, s_j = +1 (A) / -1 (B), for
  * q = 2 pi m / L at the nq integer triples m_xyz [nq][3]; S is FP64 [nq]. */

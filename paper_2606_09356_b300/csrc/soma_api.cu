@@ -1008,6 +1008,17 @@ int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted) {
   return SOMA_OK;
 }
 
+int soma_copy_accepted(soma_handle* h, int sys, uint64_t* dst, void* stream) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !dst) return SOMA_EINVAL;
+  cudaStream_t s = pick(h, stream);
+  CK(cudaStreamWaitEvent(s, h->order_ev, 0));  // after the latest steps, on any stream
+  CK(launch_sum_acc(h->d_sys, sys, h->d_acc_sum, s));
+  CK(cudaMemcpyAsync(dst, h->d_acc_sum, 8, cudaMemcpyDeviceToHost, s));
+  return SOMA_OK;
+}
+
 int soma_observables(soma_handle* h, int sys, soma_obs* out) {
   NvtxRange nvtx_range("soma_observables");
   int rc = check_live(h);

@@ -40,7 +40,7 @@ EXPORTS = (
     "soma_options_default", "soma_create", "soma_destroy", "soma_strerror", "soma_last_error",
     "soma_mc_steps", "soma_sync", "soma_get_density", "soma_get_fields", "soma_set_density",
     "soma_freeze_fields", "soma_set_umbrella", "soma_place", "soma_get_state", "soma_set_state",
-    "soma_get_state64", "soma_set_state64", "soma_observables", "soma_get_accepted",
+    "soma_get_state64", "soma_set_state64", "soma_observables", "soma_get_accepted", "soma_copy_accepted",
     "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
     "soma_philox4x32", "soma_structure_factor_noalloc", "soma_selfcheck_timeout",
     "soma_normal_deviates",
@@ -121,6 +121,7 @@ def load_library(path=None):
     L.soma_freeze_fields.argtypes = [vp, i32, vp, sz, i32]
     L.soma_set_umbrella.argtypes = [vp, i32, vp, sz, ctypes.c_double, i32]
     L.soma_selfcheck_timeout.argtypes = [i32, u64]
+    L.soma_copy_accepted.argtypes = [vp, i32, vp, vp]
     L.soma_normal_deviates.argtypes = [vp, vp, sz]
     L.soma_place.argtypes = [vp, i32, vp, sz, i32]
     L.soma_get_state.argtypes = [vp, i32, vp, vp, ctypes.POINTER(u64), i32]
@@ -402,6 +403,11 @@ class Handle:
         a = ctypes.c_uint64()
         _check(self.lib.soma_get_accepted(self.h, sys, ctypes.byref(a)), "soma_get_accepted")
         return a.value
+
+    def copy_accepted(self, dst, sys=0, stream=None):
+        """Enqueue the accepted count into dst (a 1-element uint64 host array,
+        pinned for an asynchronous copy); valid after the stream synchronises."""
+        _check(self.lib.soma_copy_accepted(self.h, sys, _ptr(dst), stream), "soma_copy_accepted")
 
     def structure_factor(self, m, sys=0):
         m = np.ascontiguousarray(m, np.int32).reshape(-1, 3)

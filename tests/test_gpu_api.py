@@ -105,3 +105,22 @@ def test_accepted_count_is_read_after_steps_on_a_caller_stream():
         a1 = h.accepted()  # ordered after the 20 steps on the caller's stream
         torch.cuda.synchronize()
         assert a1 == h.accepted() and a1 > a0
+
+
+def test_enqueued_accepted_counts_follow_each_step():
+    import torch
+    s = soma.System(**workloads.system_kwargs("config0"))
+    st = torch.cuda.Stream()
+    got = torch.zeros(6, dtype=torch.int64).pin_memory().numpy()
+    with soma.Handle(s, graph_steps=0) as h:
+        ref = []
+        for i in range(6):
+            h.mc_steps(1, stream=st.cuda_stream)
+            h.copy_accepted(got[i:i + 1], stream=st.cuda_stream)
+        torch.cuda.synchronize()
+        assert got[-1] == h.accepted()
+    with soma.Handle(s, graph_steps=0) as h2:  # the same trajectory, read step by step
+        for i in range(6):
+            h2.mc_steps(1)
+            ref.append(h2.accepted())
+    assert list(got) == ref
