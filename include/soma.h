@@ -28,7 +28,11 @@
  *     owned by the caller; `where` says whether a pointer is host memory
  *     (SOMA_HOST) or device memory on the handle's GPU (SOMA_DEVICE).
  *   - Work is enqueued on the caller's CUDA stream (NULL = the handle's own
- *     stream).  Calls that return data to the host synchronise that stream.
+ *     stream).  Calls that return data to the host wait for all work on the
+ *     device (soma_get_accepted and soma_copy_accepted order themselves
+ *     after the latest soma_mc_steps only).  A handle is not thread-safe:
+ *     the caller serialises the calls on one handle; distinct handles are
+ *     independent.
  *   - Layouts: positions [bead][xyz] with bead = chain * N + i in LOGICAL
  *     chain order; counts and fields [type][cell], type 0 = A, 1 = B;
  *     cell = (ix * ny + iy) * nz + iz.
