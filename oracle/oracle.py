@@ -102,6 +102,7 @@ class Oracle:
             L.orc_energy_umbrella.restype = ctypes.c_double
             L.orc_fields_umbrella.argtypes = [dp, u32p, f64p, ctypes.c_double, f64p]
             L.orc_place.argtypes = [dp, ctypes.POINTER(ctypes.c_float), f64p]
+            L.orc_density_profile.argtypes = [dp, u32p, ctypes.c_int, f64p]
             L.orc_place.restype = ctypes.c_int
             L.orc_run.restype = ctypes.c_int64
             cls._lib = L
@@ -168,6 +169,14 @@ class Oracle:
         self.lib().orc_fields_umbrella(ctypes.byref(self.d), _p(counts, ctypes.c_uint32),
                                        _p(target, ctypes.c_double), float(lambdaN), _p(w, ctypes.c_double))
         return w
+
+    def density_profile(self, counts, axis):
+        """Laterally averaged volume fractions [2, grid[axis]] along one axis."""
+        counts = np.ascontiguousarray(counts, np.uint32)
+        out = np.zeros((2, int(self.d.grid[axis])), np.float64)
+        self.lib().orc_density_profile(ctypes.byref(self.d), _p(counts, ctypes.c_uint32), int(axis),
+                                       _p(out, ctypes.c_double))
+        return out
 
     def place(self, target):
         """Positions [n_b, 3] of molecules placed from float32 target volume

@@ -36,6 +36,8 @@
 //                         one-bead Boltzmann law and the dimer cell-pair law
 //                         (detailed balance makes them stationary).
 //   orc_fields_umbrella   pinned: central difference of H_nb + H_umb.
+//   orc_density_profile   pinned: closed form on constructed counts and the
+//                         mean over layers = the global composition.
 //   wall confinement      pinned: the exact cell-pair law of an AB dimer
 //                         between walls (no periodic images in z).
 //   orc_place             pinned: the exact law of the bead-0 cell (target
@@ -291,6 +293,23 @@ void orc_fields(const orc_desc* d, const uint32_t* counts, double* w) {
   const double rho_bar = (double)n_beads(d) / (double)nc;
   for (int64_t c = 0; c < nc; ++c)
     cell_fields(d, counts[c] / rho_bar, counts[nc + c] / rho_bar, &w[c], &w[nc + c]);
+}
+
+// Laterally averaged volume fractions along one axis (the layer profiles
+// phi_t(z) that Sec. 4 compares between the particle, continuum and coupled
+// runs): phi_t(k) = (1/m) sum over the m cells of layer k of n_t(c)/rho_bar,
+// layer k = the cells whose index along `axis` is k.  out is [type][layer].
+void orc_density_profile(const orc_desc* d, const uint32_t* counts, int axis, double* out) {
+  const int64_t nc = n_cells(d);
+  const double rho_bar = (double)n_beads(d) / (double)nc;
+  const int n = d->grid[axis];
+  const int64_t m = nc / n;
+  for (int i = 0; i < 2 * n; ++i) out[i] = 0.0;
+  for (int64_t c = 0; c < nc; ++c) {
+    const int64_t idx[3] = {c / ((int64_t)d->grid[1] * d->grid[2]), (c / d->grid[2]) % d->grid[1], c % d->grid[2]};
+    for (int t = 0; t < 2; ++t) out[t * n + idx[axis]] += counts[t * nc + c] / rho_bar;
+  }
+  for (int i = 0; i < 2 * n; ++i) out[i] /= (double)m;
 }
 
 // The non-bonded energy functional itself, H_nb from the counts.

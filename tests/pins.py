@@ -479,6 +479,31 @@ def pin_wall_dimer_cell_pairs(O, blocks=16, per_block=15):
     return fails
 
 
+# ---------------------------------------------------------------------------
+def pin_density_profile(O):
+    """Counts built as (layer index + 1)(type + 1) give the profile
+    (k + 1)(t + 1)/rho_bar exactly; random counts average, over the layers,
+    to the global composition."""
+    fails = []
+    o = O(40, 8, 3, (2.0, 3.0, 4.0), (3, 4, 5), 10.0, 20.0, seed=1)
+    _, _, rho = o.params()
+    grid = (3, 4, 5)
+    ix, iy, iz = np.meshgrid(*[np.arange(g) for g in grid], indexing="ij")
+    idx = [ix.reshape(-1), iy.reshape(-1), iz.reshape(-1)]
+    for axis in range(3):
+        counts = np.stack([(idx[axis] + 1) * (t + 1) for t in range(2)]).astype(np.uint32)
+        prof = o.density_profile(counts, axis)
+        exact = np.stack([(np.arange(grid[axis]) + 1) * (t + 1) / rho for t in range(2)])
+        _check(fails, f"profile axis {axis}", float(np.abs(prof - exact).max()), 0.0, 1e-12)
+    rng = np.random.default_rng(5)
+    counts = rng.integers(0, 9, size=(2, o.n_c)).astype(np.uint32)
+    for axis in range(3):
+        prof = o.density_profile(counts, axis)
+        _check(fails, f"profile mean axis {axis}", float(np.abs(prof.mean(1) - counts.sum(1) / (o.n_c * rho)).max()),
+               0.0, 1e-12)
+    return fails
+
+
 ALL_PINS = {
     "philox_triton": pin_philox_triton,
     "init_statistics": pin_init_statistics,
@@ -496,4 +521,5 @@ ALL_PINS = {
     "place_bead0_law": pin_place_bead0_law,
     "place_bond_statistics": pin_place_bond_statistics,
     "wall_dimer_cell_pairs": pin_wall_dimer_cell_pairs,
+    "density_profile": pin_density_profile,
 }

@@ -62,6 +62,8 @@ MUTATIONS = [
      "                            cell / ((int64_t)d->grid[0] * d->grid[1])};", "place_bead0_law"),
     ("wall ignored: z stays periodic", "if (d->wall_z && !(rn[2] >= 0.0 && rn[2] < d->box[2])) {",
      "if (false) {", "wall_dimer_cell_pairs"),
+    ("profile averaged over the wrong cell count", "for (int i = 0; i < 2 * n; ++i) out[i] /= (double)m;",
+     "for (int i = 0; i < 2 * n; ++i) out[i] /= (double)nc;", "density_profile"),
     ("placement weights of the other type", "const float* phi = target + (int64_t)type_of(d, 0) * nc;",
      "const float* phi = target + (int64_t)(1 - type_of(d, 0)) * nc;", "place_bead0_law"),
 ]
