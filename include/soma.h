@@ -180,6 +180,13 @@ int soma_sync(soma_handle* h, void* stream);
 /* Density counts of the current configuration, [2][n_cells] uint32. */
 int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where);
 
+/* Laterally averaged volume fractions of the current configuration along
+ * one axis (0 = x, 1 = y, 2 = z): out[t * n_layers + k] = the mean over the
+ * cells of layer k of n_t(c) / rho_bar, in FP64 from exact integer layer
+ * sums (the profiles phi_t(z) Sec. 4 compares); n must be 2 * grid[axis]
+ * (host buffer).  Synchronises. */
+int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t n);
+
 /* Fields used by the next step, [2][n_cells] FP32. */
 int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where);
 

@@ -91,6 +91,7 @@ struct soma_handle {
   float* d_stage_pos = nullptr;
   int16_t* d_stage_img = nullptr;
   float* d_stage_phi = nullptr;
+  unsigned long long* d_profile = nullptr;  // layer sums of soma_density_profile (first use)
   void* place_temp = nullptr;  // CUB scan scratch of soma_place (allocated on first use)
   size_t place_temp_bytes = 0;
   int64_t max_nb = 0, max_nc = 0;
@@ -833,6 +834,36 @@ int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where
   CK(launch_deinterleave(src, S.n_c, dst, h->sm_count, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (where != SOMA_DEVICE) CK(cudaMemcpy(out, dst, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+  return SOMA_OK;
+}
+
+int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t n) {
+  NvtxRange nvtx_range("soma_density_profile");
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !out || axis < 0 || axis > 2) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  const int dims[3] = {S.nx, S.ny, S.nz};
+  const int layers = dims[axis];
+  if (n != (size_t)(2 * layers)) return SOMA_EINVAL;
+  if ((rc = sync_all(h))) return rc;
+  if (!h->d_profile) {  // per-layer sums of the largest grid dimension, allocated on first use
+    int most = 1;
+    for (const SysDev& T : h->host_sys) most = std::max(most, std::max(T.nx, std::max(T.ny, T.nz)));
+    h->d_profile = (unsigned long long*)dev_alloc(h, 16 * (size_t)most);
+    if (!h->d_profile) return SOMA_ENOMEM;
+  }
+  unsigned long long* d_sum = h->d_profile;
+  const uint32_t* src = count_buffer(S.counts, S.n_c, (long long)h->step - 1);
+  CK(launch_profile(src, S.nx, S.ny, S.nz, axis, d_sum, h->stream));
+  std::vector<unsigned long long> sums(2 * (size_t)layers);
+  CK(cudaMemcpyAsync(sums.data(), d_sum, sizeof(unsigned long long) * sums.size(), cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const double rho_bar = (double)S.n_b / (double)S.n_c;
+  const double per_layer = (double)(S.n_c / layers);
+  for (int k = 0; k < layers; ++k)
+    for (int t = 0; t < 2; ++t) out[(size_t)t * layers + k] = (double)sums[2 * (size_t)k + t] / rho_bar / per_layer;
   return SOMA_OK;
 }
 

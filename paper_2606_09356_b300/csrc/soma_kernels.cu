@@ -174,6 +174,45 @@ __global__ void k_field_from_phi(const SysDev* __restrict__ systems, int sys, co
   }
 }
 
+// Layer sums of the counts along one axis: block k adds the (nA, nB) of the
+// m cells of layer k (interleaved count buffer) into out[2k], out[2k+1].
+__global__ void k_profile(const uint32_t* __restrict__ counts, int nx, int ny, int nz, int axis,
+                          unsigned long long* __restrict__ out) {
+  const int k = blockIdx.x;
+  const int64_t m = (int64_t)nx * ny * nz / (axis == 0 ? nx : axis == 1 ? ny : nz);
+  unsigned long long a = 0, b = 0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    int64_t c;
+    if (axis == 0)
+      c = (int64_t)k * ny * nz + i;
+    else if (axis == 1)
+      c = ((i / nz) * ny + k) * nz + i % nz;
+    else
+      c = i * nz + k;
+    a += counts[2 * c];
+    b += counts[2 * c + 1];
+  }
+  __shared__ unsigned long long sa[32], sb[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sa[threadIdx.x >> 5] = a;
+    sb[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long ta = 0, tb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      ta += sa[w];
+      tb += sb[w];
+    }
+    out[2 * k] = ta;
+    out[2 * k + 1] = tb;
+  }
+}
+
 // Step counters of graph replays: advance n_sys counters by n, or set them.
 __global__ void k_advance_step(unsigned long long* counters, int n_sys, long long n) {
   for (int i = threadIdx.x; i < n_sys; i += blockDim.x) counters[i] += (unsigned long long)n;
@@ -575,6 +614,13 @@ size_t place_temp_bytes(int64_t n_c) {
   cub::DeviceScan::InclusiveSum(nullptr, bytes, (const unsigned long long*)nullptr, (unsigned long long*)nullptr,
                                 n_c);
   return bytes;
+}
+
+cudaError_t launch_profile(const uint32_t* counts, int nx, int ny, int nz, int axis, unsigned long long* out,
+                           cudaStream_t s) {
+  const int layers = axis == 0 ? nx : axis == 1 ? ny : nz;
+  k_profile<<<layers, 256, 0, s>>>(counts, nx, ny, nz, axis, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_advance(unsigned long long* counters, int n_sys, long long n, cudaStream_t s) {

@@ -25,6 +25,10 @@ cudaError_t launch_field(const FieldArgs& f, StepRef r, int zero_next, cudaStrea
 cudaError_t launch_deinterleave(const uint32_t* counts, int64_t n_c, uint32_t* out, int sm_count, cudaStream_t s);
 cudaError_t launch_field_from_phi(const SysDev* systems, int sys, const float* phi, int sm_count, cudaStream_t s);
 cudaError_t launch_advance(unsigned long long* counters, int n_sys, long long n, cudaStream_t s);
+// Per-layer sums (nA, nB) of an interleaved count buffer along one axis:
+// out [layers][2] (layers = the grid size along `axis`).
+cudaError_t launch_profile(const uint32_t* counts, int nx, int ny, int nz, int axis, unsigned long long* out,
+                           cudaStream_t s);
 // Placement from target volume fractions phi [2][n_c] (device); q and prefix
 // hold n_c 64-bit words each; *total receives the weight sum (0: nothing
 // placed).  Synchronises the stream once.
