@@ -164,3 +164,23 @@ def test_place_then_umbrella_reproduces_target():
         return float(np.corrcoef(a, b)[0, 1])
     assert corr(placed) > 0.5
     assert corr(held) > 0.9
+
+
+def test_place_in_a_multi_system_handle_equals_single():
+    base = dict(n_poly=300, N=16, n_A=8, box=(4.0, 4.0, 4.0), grid=(16, 16, 16), chiN=20.0, kappaN=50.0)
+    systems = [soma.System(**base, seed=70 + i, system_id=i) for i in range(3)]
+    tg = _target(systems[1], seed=12)
+    with soma.Handle(systems) as hb:
+        hb.mc_steps(4)
+        others = [hb.get_state(i)[0] for i in (0, 2)]
+        hb.place(tg, sys=1)
+        placed = hb.get_state(1)[0]
+        assert all(np.array_equal(a, hb.get_state(i)[0]) for a, i in zip(others, (0, 2)))
+        hb.mc_steps(5)
+        after = [hb.get_state(i)[0] for i in range(3)]
+    with soma.Handle(systems[1]) as h:
+        h.mc_steps(4)
+        h.place(tg)
+        assert np.array_equal(h.get_state()[0], placed)
+        h.mc_steps(5)
+        assert np.array_equal(h.get_state()[0], after[1])
