@@ -5,7 +5,8 @@ a mutated copy of its source) and returns a list of failure strings; an empty
 list means the pin holds.  The facts used:
 
 * Philox4x32-10: an independent implementation (Triton's, on its CPU
-  interpreter) of the generator of Salmon et al. (SC'11).
+  interpreter) of the generator of Salmon et al. (SC'11); chi-square
+  uniformity of the top and low bytes of 2^20 words.
 * Gaussian-chain statistics of the initial configuration and of the
   chiN = kappaN = 0 dynamics: per-axis bond variance 1/(3(N-1)), <R_e^2> = 1,
   <R_g^2> = (N+1)/(6N); the harmonic chain's Boltzmann law is stationary.
@@ -67,6 +68,27 @@ def pin_philox_triton(O, n=512, seed=12345):
     got = O.philox(ctr, key)
     bad = np.nonzero((got != ref).any(axis=1))[0]
     return [f"philox differs from Triton's at {len(bad)} of {n} counters"] if len(bad) else []
+
+
+def pin_philox_uniformity(O, n=1 << 18):
+    """Chi-square of the top byte and of the low byte of 4n words from
+    consecutive counters (256 bins each): within the 1e-4 tails of the
+    chi-square law with 255 degrees of freedom."""
+    from scipy.stats import chi2
+    fails = []
+    ctr = np.zeros((n, 4), np.uint32)
+    ctr[:, 0] = np.arange(n, dtype=np.uint32)
+    ctr[:, 2] = 7
+    key = np.tile(np.array([[0x12345678, 0x9ABCDEF0]], np.uint32), (n, 1))
+    w = O.philox(ctr, key).reshape(-1)
+    lo, hi = chi2.ppf(1e-4, 255), chi2.ppf(1 - 1e-4, 255)
+    for name, b in (("top byte", w >> 24), ("low byte", w & 0xFF)):
+        cnt = np.bincount(b.astype(np.int64), minlength=256)
+        e = w.size / 256
+        x2 = float(((cnt - e) ** 2 / e).sum())
+        if not (lo < x2 < hi):
+            fails.append(f"philox {name} chi-square {x2:.1f} outside ({lo:.1f}, {hi:.1f})")
+    return fails
 
 
 # ---------------------------------------------------------------------------
@@ -505,6 +527,7 @@ def pin_density_profile(O):
 
 
 ALL_PINS = {
+    "philox_uniformity": pin_philox_uniformity,
     "philox_triton": pin_philox_triton,
     "init_statistics": pin_init_statistics,
     "ideal_dynamics": pin_ideal_dynamics,
