@@ -1,7 +1,8 @@
 """Throughput benchmark of the SCMF Monte Carlo step (bead moves per second).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config1]
-                    [--impl reference] [--no-batched] [--no-e2e]
+                    [--impl reference] [--no-batched] [--no-e2e] [--no-cpu]
+                    [--no-steady] [--no-smart] [--no-energy]
 
 One JSON line on rank 0.  A step is one whole Monte Carlo step of every bead
 (one move kernel: moves against the fields of the previous step's counts,
@@ -10,6 +11,13 @@ reorder when it falls due).  Inputs are resident in HBM; between timed steps
 a 256 MiB buffer (twice the L2) is written so every step starts from a cold
 L2; each step is bracketed by CUDA events on the library's stream and the
 move and field kernels by the library's own per-kernel events.
+
+Beside the headline the line carries: the move kernel's roofline fraction
+(with the DRAM traffic of the committed ncu summary when it was taken from
+the current kernel source), the CPU oracle on a bounded sample, the end to
+end rate through the C ABI with host buffers, CUDA-graph steady state,
+energy per step from NVML, the smart-move and umbrella variants of the
+same workload, and the 64-system batch against its systems run one by one.
 
 ``--impl reference`` times the plain FP64 CPU oracle on the same workload
 shape (a bounded sample of it) on the host cores instead.
