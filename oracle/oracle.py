@@ -103,6 +103,7 @@ class Oracle:
             L.orc_fields_umbrella.argtypes = [dp, u32p, f64p, ctypes.c_double, f64p]
             L.orc_place.argtypes = [dp, ctypes.POINTER(ctypes.c_float), f64p]
             L.orc_density_profile.argtypes = [dp, u32p, ctypes.c_int, f64p]
+            L.orc_vertical_correlation.argtypes = [dp, u32p, ctypes.c_int, f64p]
             L.orc_place.restype = ctypes.c_int
             L.orc_run.restype = ctypes.c_int64
             cls._lib = L
@@ -176,6 +177,14 @@ class Oracle:
         out = np.zeros((2, int(self.d.grid[axis])), np.float64)
         self.lib().orc_density_profile(ctypes.byref(self.d), _p(counts, ctypes.c_uint32), int(axis),
                                        _p(out, ctypes.c_double))
+        return out
+
+    def vertical_correlation(self, counts, type_):
+        """C(dz) of the type counts, dz = 0 .. nz-1."""
+        counts = np.ascontiguousarray(counts, np.uint32)
+        out = np.zeros(int(self.d.grid[2]), np.float64)
+        self.lib().orc_vertical_correlation(ctypes.byref(self.d), _p(counts, ctypes.c_uint32), int(type_),
+                                            _p(out, ctypes.c_double))
         return out
 
     def place(self, target):

@@ -36,6 +36,8 @@
 //                         one-bead Boltzmann law and the dimer cell-pair law
 //                         (detailed balance makes them stationary).
 //   orc_fields_umbrella   pinned: central difference of H_nb + H_umb.
+//   orc_vertical_correlation pinned: a cosine layer pattern (periodic), a
+//                         linear ramp between walls (closed forms), C(0) = 1.
 //   orc_density_profile   pinned: closed form on constructed counts and the
 //                         mean over layers = the global composition.
 //   wall confinement      pinned: the exact cell-pair law of an AB dimer
@@ -310,6 +312,42 @@ void orc_density_profile(const orc_desc* d, const uint32_t* counts, int axis, do
     for (int t = 0; t < 2; ++t) out[t * n + idx[axis]] += counts[t * nc + c] / rho_bar;
   }
   for (int i = 0; i < 2 * n; ++i) out[i] /= (double)m;
+}
+
+// Vertical correlation of the type-t counts (Sec. 4 compares a vertical
+// correlation C(dz) of the concentration between runs; it gives no formula).
+// Reading: the correlation coefficient of n_t(c) and n_t(c + dz e_z) over all
+// cell pairs at vertical distance dz -- periodic in z, or, with walls, only
+// the pairs inside the slab --, each pair set with its own means,
+//   C(dz) = [<a b> - <a><b>] / [<n^2> - <n>^2],  a = n_t(c), b = n_t(c + dz e_z),
+// the variance taken over all cells.  out[dz], dz = 0 .. nz-1.
+void orc_vertical_correlation(const orc_desc* d, const uint32_t* counts, int type, double* out) {
+  const int64_t nc = n_cells(d);
+  const int nz = d->grid[2];
+  const uint32_t* n = counts + (int64_t)type * nc;
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t c = 0; c < nc; ++c) {
+    s1 += n[c];
+    s2 += (double)n[c] * n[c];
+  }
+  const double var = s2 / nc - (s1 / nc) * (s1 / nc);
+  for (int dz = 0; dz < nz; ++dz) {
+    double sab = 0.0, sa = 0.0, sb = 0.0, pairs = 0.0;
+    for (int64_t c = 0; c < nc; ++c) {
+      const int iz = (int)(c % nz);
+      int jz = iz + dz;
+      if (jz >= nz) {
+        if (d->wall_z) continue;
+        jz -= nz;
+      }
+      const double a = n[c], b = n[c - iz + jz];
+      sab += a * b;
+      sa += a;
+      sb += b;
+      pairs += 1.0;
+    }
+    out[dz] = var > 0.0 ? (sab / pairs - (sa / pairs) * (sb / pairs)) / var : 0.0;
+  }
 }
 
 // The non-bonded energy functional itself, H_nb from the counts.

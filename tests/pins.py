@@ -526,6 +526,37 @@ def pin_density_profile(O):
     return fails
 
 
+def pin_vertical_correlation(O):
+    """Layers of counts proportional to 1 + cos(2 pi k z / nz) give
+    C(dz) = cos(2 pi k dz / nz) when z is periodic; between walls a linear
+    ramp n(z) = z pairs perfectly along z, so C(dz) is the ratio of the
+    ramp's variance over the nz - dz layers that have a partner to its
+    variance over all layers, ((nz - dz)^2 - 1) / (nz^2 - 1); C(0) = 1 for
+    any field."""
+    fails = []
+    nz = 8
+    o = O(10, 4, 2, (2.0, 2.0, 4.0), (2, 3, nz), 0.0, 0.0, seed=1)
+    for k in (1, 2, 3):
+        layer = np.rint(2 * (1 + np.cos(2 * np.pi * k * np.arange(nz) / nz)) * 1000).astype(np.int64)
+        counts = np.zeros((2, o.n_c), np.uint32)
+        counts[0] = np.tile(layer, o.n_c // nz)
+        C = o.vertical_correlation(counts, 0)
+        exact = np.cos(2 * np.pi * k * np.arange(nz) / nz)
+        _check(fails, f"periodic cosine k={k}", float(np.abs(C - exact).max()), 0.0, 2e-3)
+    nzw = 6
+    ow = O(10, 4, 2, (2.0, 2.0, 4.0), (2, 3, nzw), 0.0, 0.0, seed=1, wall_z=1)
+    counts = np.zeros((2, ow.n_c), np.uint32)
+    counts[1] = np.tile(np.arange(nzw), ow.n_c // nzw).astype(np.uint32)
+    C = ow.vertical_correlation(counts, 1)
+    for dz in range(nzw):
+        exact = ((nzw - dz) ** 2 - 1) / (nzw ** 2 - 1)
+        _check(fails, f"walls ramp dz={dz}", C[dz], exact, 1e-12)
+    rng = np.random.default_rng(9)
+    counts = rng.integers(0, 7, size=(2, o.n_c)).astype(np.uint32)
+    _check(fails, "C(0) of a random field", o.vertical_correlation(counts, 1)[0], 1.0, 1e-12)
+    return fails
+
+
 ALL_PINS = {
     "philox_uniformity": pin_philox_uniformity,
     "philox_triton": pin_philox_triton,
@@ -545,4 +576,5 @@ ALL_PINS = {
     "place_bond_statistics": pin_place_bond_statistics,
     "wall_dimer_cell_pairs": pin_wall_dimer_cell_pairs,
     "density_profile": pin_density_profile,
+    "vertical_correlation": pin_vertical_correlation,
 }

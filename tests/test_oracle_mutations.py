@@ -64,6 +64,7 @@ MUTATIONS = [
      "if (false) {", "wall_dimer_cell_pairs"),
     ("profile averaged over the wrong cell count", "for (int i = 0; i < 2 * n; ++i) out[i] /= (double)m;",
      "for (int i = 0; i < 2 * n; ++i) out[i] /= (double)nc;", "density_profile"),
+    ("correlation pairs wrap between walls", "        if (d->wall_z) continue;\n", "", "vertical_correlation"),
     ("placement weights of the other type", "const float* phi = target + (int64_t)type_of(d, 0) * nc;",
      "const float* phi = target + (int64_t)(1 - type_of(d, 0)) * nc;", "place_bead0_law"),
 ]
