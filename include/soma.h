@@ -187,6 +187,15 @@ int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where
  * (host buffer).  Synchronises. */
 int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t n);
 
+/* Vertical correlation of the type-`type` counts of the current
+ * configuration (the vertical correlation Sec. 4 compares):
+ *   C(dz) = [<a b> - <a><b>] / [<n^2> - <n>^2],  a = n(c), b = n(c + dz e_z),
+ * over all cell pairs at vertical distance dz (periodic in z, or only those
+ * inside the slab with wall_z), the variance over all cells; from exact
+ * integer sums, in FP64.  out has n = grid[2] entries, dz = 0 .. nz-1 (host
+ * buffer); 0 where the field has no variance.  Synchronises. */
+int soma_vertical_correlation(soma_handle* h, int sys, int type, double* out, size_t n);
+
 /* Fields used by the next step, [2][n_cells] FP32. */
 int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where);
 

@@ -92,6 +92,8 @@ struct soma_handle {
   int16_t* d_stage_img = nullptr;
   float* d_stage_phi = nullptr;
   unsigned long long* d_profile = nullptr;  // layer sums of soma_density_profile (first use)
+  unsigned long long* d_vcorr = nullptr;    // pair sums of soma_vertical_correlation (first use)
+  size_t vcorr_words = 0;
   void* place_temp = nullptr;  // CUB scan scratch of soma_place (allocated on first use)
   size_t place_temp_bytes = 0;
   int64_t max_nb = 0, max_nc = 0;
@@ -864,6 +866,39 @@ int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t 
   const double per_layer = (double)(S.n_c / layers);
   for (int k = 0; k < layers; ++k)
     for (int t = 0; t < 2; ++t) out[(size_t)t * layers + k] = (double)sums[2 * (size_t)k + t] / rho_bar / per_layer;
+  return SOMA_OK;
+}
+
+int soma_vertical_correlation(soma_handle* h, int sys, int type, double* out, size_t n) {
+  NvtxRange nvtx_range("soma_vertical_correlation");
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !out || type < 0 || type > 1) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if (n != (size_t)S.nz) return SOMA_EINVAL;
+  if ((rc = sync_all(h))) return rc;
+  const size_t words = 4 * ((size_t)S.nz + 1);
+  if (h->vcorr_words < words) {  // sums buffer, grown on demand (kept for the handle's life)
+    int most = 1;
+    for (const SysDev& T : h->host_sys) most = std::max(most, T.nz);
+    h->vcorr_words = 4 * ((size_t)most + 1);
+    h->d_vcorr = (unsigned long long*)dev_alloc(h, 8 * h->vcorr_words);
+    if (!h->d_vcorr) return SOMA_ENOMEM;
+  }
+  const uint32_t* src = count_buffer(S.counts, S.n_c, (long long)h->step - 1);
+  CK(launch_vcorr(src, S.n_c, S.nz, type, S.wall_z, h->d_vcorr, h->stream));
+  std::vector<unsigned long long> v(words);
+  CK(cudaMemcpyAsync(v.data(), h->d_vcorr, 8 * words, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const size_t all = 4 * (size_t)S.nz;
+  const double cells = (double)v[all + 3];
+  const double mean = (double)v[all + 1] / cells;
+  const double var = (double)v[all + 0] / cells - mean * mean;
+  for (int dz = 0; dz < S.nz; ++dz) {
+    const double p = (double)v[4 * dz + 3];
+    const double cov = (double)v[4 * dz] / p - ((double)v[4 * dz + 1] / p) * ((double)v[4 * dz + 2] / p);
+    out[dz] = var > 0.0 ? cov / var : 0.0;
+  }
   return SOMA_OK;
 }
 

@@ -213,6 +213,55 @@ __global__ void k_profile(const uint32_t* __restrict__ counts, int nx, int ny, i
   }
 }
 
+// Vertical pair sums of the type-t counts: block dz adds, over the cells c
+// whose partner c + dz e_z exists (periodic, or inside the slab between
+// walls), a b, a and b with a = n_t(c), b = n_t(c + dz e_z); block nz adds
+// n and n^2 over all cells.  Integer sums, exact.  out [nz + 1][4].
+__global__ void k_vcorr(const uint32_t* __restrict__ counts, int64_t n_c, int nz, int type, int wall,
+                        unsigned long long* __restrict__ out) {
+  const int dz = blockIdx.x;
+  unsigned long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  for (int64_t c = threadIdx.x; c < n_c; c += blockDim.x) {
+    const unsigned long long a = counts[2 * c + type];
+    if (dz == nz) {
+      s0 += a * a;
+      s1 += a;
+      s3 += 1;
+      continue;
+    }
+    const int iz = (int)(c % nz);
+    int jz = iz + dz;
+    if (jz >= nz) {
+      if (wall) continue;
+      jz -= nz;
+    }
+    const unsigned long long b = counts[2 * (c - iz + jz) + type];
+    s0 += a * b;
+    s1 += a;
+    s2 += b;
+    s3 += 1;
+  }
+  __shared__ unsigned long long sh[4][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_down_sync(0xffffffffu, s0, o);
+    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    s3 += __shfl_down_sync(0xffffffffu, s3, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = s0;
+    sh[1][threadIdx.x >> 5] = s1;
+    sh[2][threadIdx.x >> 5] = s2;
+    sh[3][threadIdx.x >> 5] = s3;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    unsigned long long t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[threadIdx.x][w];
+    out[4 * dz + threadIdx.x] = t;
+  }
+}
+
 // Step counters of graph replays: advance n_sys counters by n, or set them.
 __global__ void k_advance_step(unsigned long long* counters, int n_sys, long long n) {
   for (int i = threadIdx.x; i < n_sys; i += blockDim.x) counters[i] += (unsigned long long)n;
@@ -620,6 +669,12 @@ cudaError_t launch_profile(const uint32_t* counts, int nx, int ny, int nz, int a
                            cudaStream_t s) {
   const int layers = axis == 0 ? nx : axis == 1 ? ny : nz;
   k_profile<<<layers, 256, 0, s>>>(counts, nx, ny, nz, axis, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vcorr(const uint32_t* counts, int64_t n_c, int nz, int type, int wall, unsigned long long* out,
+                         cudaStream_t s) {
+  k_vcorr<<<nz + 1, 256, 0, s>>>(counts, n_c, nz, type, wall, out);
   return cudaGetLastError();
 }
 

@@ -36,6 +36,11 @@ cudaError_t launch_place(const SysDev* systems, int sys, const SysDev& host, con
                          unsigned long long* q, unsigned long long* prefix, void* temp, size_t temp_bytes,
                          unsigned long long* total, int sm_count, cudaStream_t s);
 size_t place_temp_bytes(int64_t n_c);
+// Vertical pair sums of an interleaved count buffer (type `type`): out
+// [nz + 1][4] = (sum a b, sum a, sum b, pairs) per dz, then (sum n^2,
+// sum n, -, cells).
+cudaError_t launch_vcorr(const uint32_t* counts, int64_t n_c, int nz, int type, int wall, unsigned long long* out,
+                         cudaStream_t s);
 cudaError_t launch_set_step(unsigned long long* counters, int n_sys, unsigned long long value, cudaStream_t s);
 cudaError_t launch_init(const SysDev* systems, int sys, int64_t n_poly, cudaStream_t s);
 cudaError_t launch_gather_state(const SysDev* systems, int sys, float* pos, int16_t* img, int sm_count,

@@ -38,7 +38,8 @@ SOMA_HIST_SEPARATE = 2
 # every entry point declared in include/soma.h
 EXPORTS = (
     "soma_options_default", "soma_create", "soma_destroy", "soma_strerror", "soma_last_error",
-    "soma_mc_steps", "soma_sync", "soma_get_density", "soma_density_profile", "soma_get_fields",
+    "soma_mc_steps", "soma_sync", "soma_get_density", "soma_density_profile", "soma_vertical_correlation",
+    "soma_get_fields",
     "soma_set_density",
     "soma_freeze_fields", "soma_set_umbrella", "soma_place", "soma_get_state", "soma_set_state",
     "soma_get_state64", "soma_set_state64", "soma_observables", "soma_get_accepted", "soma_copy_accepted",
@@ -124,6 +125,7 @@ def load_library(path=None):
     L.soma_selfcheck_timeout.argtypes = [i32, u64]
     L.soma_copy_accepted.argtypes = [vp, i32, vp, vp]
     L.soma_density_profile.argtypes = [vp, i32, i32, vp, sz]
+    L.soma_vertical_correlation.argtypes = [vp, i32, i32, vp, sz]
     L.soma_normal_deviates.argtypes = [vp, vp, sz]
     L.soma_place.argtypes = [vp, i32, vp, sz, i32]
     L.soma_get_state.argtypes = [vp, i32, vp, vp, ctypes.POINTER(u64), i32]
@@ -323,6 +325,13 @@ class Handle:
         """Laterally averaged volume fractions [2, grid[axis]] along one axis."""
         out = np.zeros((2, self.systems[sys].grid[axis]), np.float64)
         _check(self.lib.soma_density_profile(self.h, sys, int(axis), _ptr(out), out.size), "soma_density_profile")
+        return out
+
+    def vertical_correlation(self, type_, sys=0):
+        """C(dz) of the type counts (0 = A, 1 = B), dz = 0 .. grid[2]-1."""
+        out = np.zeros(self.systems[sys].grid[2], np.float64)
+        _check(self.lib.soma_vertical_correlation(self.h, sys, int(type_), _ptr(out), out.size),
+               "soma_vertical_correlation")
         return out
 
     def get_fields(self, sys=0):

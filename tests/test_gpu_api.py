@@ -130,7 +130,7 @@ def test_enqueued_accepted_counts_follow_each_step():
     dict(workloads.system_kwargs("config0")),
     dict(n_poly=300, N=24, n_A=9, box=(3.0, 3.3, 2.9), grid=(7, 11, 9), chiN=18.0, kappaN=45.0, wall_z=1),
 ])
-def test_density_profiles_match_oracle(kw):
+def test_density_profiles_and_vertical_correlation_match_oracle(kw):
     s = soma.System(**kw)
     orc = G.oracle_for(s)
     with soma.Handle(s) as h:
@@ -138,3 +138,5 @@ def test_density_profiles_match_oracle(kw):
         counts = h.get_density()
         for axis in range(3):
             assert np.allclose(h.density_profile(axis), orc.density_profile(counts, axis), rtol=1e-13, atol=1e-13)
+        for t in range(2):
+            assert np.allclose(h.vertical_correlation(t), orc.vertical_correlation(counts, t), rtol=1e-9, atol=1e-9)
