@@ -20,12 +20,16 @@
 //
 // Parity status of each exported function (what pins it in tests/):
 //   orc_philox4x32        pinned: an independent third-party Philox4x32-10
-//                         (Triton's, run by its CPU interpreter) bit for bit.
+//                         (Triton's, run by its CPU interpreter) bit for bit;
+//                         chi-square uniformity of its words.
+//   orc_normal_quantile   pinned: scipy's ndtri and the mirror symmetry.
 //   orc_init              pinned: bond statistics of a Gaussian chain
 //                         (<b^2> = 1/(N-1), <R_e^2> = 1, <R_g^2> = (N+1)/6N).
 //   orc_density           pinned: count invariants and brute-force binning.
 //   orc_fields            pinned: central difference of the energy functional
 //                         and the incompressible exchange-field special case.
+//   orc_energy_nb         pinned with the fields: its central differences are
+//                         the fields, which the special case pins on their own.
 //   orc_mc_step/orc_run   pinned: <R_e^2> = 1 and the acceptance quadrature at
 //                         chiN = kappaN = 0; Boltzmann occupancy of one bead in
 //                         a frozen field; exact 64-state cell-pair law of an AB
