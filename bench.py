@@ -10,7 +10,9 @@ fused histogram, clearing of the next count buffer; plus the periodic chain
 reorder when it falls due).  Inputs are resident in HBM; between timed steps
 a 256 MiB buffer (twice the L2) is written so every step starts from a cold
 L2; each step is bracketed by CUDA events on the library's stream and the
-move and field kernels by the library's own per-kernel events.
+move and field kernels by the library's own per-kernel events.  The steps
+are queued while a spin kernel holds the stream, so the event windows hold
+GPU work only (no host launch latency).
 
 Beside the headline the line carries: the move kernel's roofline fraction
 (with the DRAM traffic of the committed ncu summary when it was taken from
@@ -165,6 +167,14 @@ class Clocks:
         if self.error and not self.sm:
             out["error"] = self.error
         return out
+
+
+def hold_stream(torch, stream, steps, per_step_s=1.5e-3, clock_hz=2.0e9):
+    """Keep the stream busy (a bounded spin kernel, outside every timed
+    window) while the host queues the timed steps, so the per-step CUDA-event
+    windows measure the GPU's work and not the host's launch latency."""
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(int(min(2.0, (steps + 2) * per_step_s) * clock_hz))
 
 
 def rank_system_kwargs(workload, rank):
@@ -338,6 +348,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
     with Clocks(local) as clk:
+        hold_stream(torch, stream, args.steps)
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(float(i))          # evict the L2 between timed steps
@@ -511,6 +522,7 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
     h.kernel_times(reset=True)
     a0 = h.accepted()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    hold_stream(torch, stream, steps)
     for i in range(steps):
         with torch.cuda.stream(stream):
             flush.fill_(float(i))

@@ -11,7 +11,8 @@
 //  * a consumer lane k of a chain holds beads 2k (even set) and 2k+1 (odd
 //    set); neighbours come from the adjacent lane by width-P shuffles;
 //  * both beads' proposals are formed first, so the four gathers of the lane
-//    (old and proposed cell of each bead) go out together;
+//    (old and proposed cell of each bead) go out together; their arithmetic
+//    runs as packed FP32x2 pairs (each lane rounded as the scalar operation);
 //  * set 0 (even beads) is decided first; set 1 reuses set 0's bond vectors
 //    plus the accepted displacement, so no second minimum image is needed;
 //  * the field term of a move comes straight from the integer counts of the
@@ -24,7 +25,10 @@
 //    added to count buffer t mod 3 by fire-and-forget atomics (kernel (b)),
 //    and the CTAs clear count buffer t+1 mod 3 for the next step.
 // k_move steps one system; k_move_batch steps up to kMaxBatch systems in one
-// persistent launch (tiles of all systems in one sequence).
+// persistent launch (tiles of all systems in one sequence).  Both are
+// specialised on the proposal (uniform, or bond-force-biased: smart_pair)
+// and on the z boundary (periodic, or hard walls: a proposal leaving the
+// slab is rejected, z bonds are plain differences).
 // Every mbarrier wait is bounded: on expiry the kernel sets kErrTimeout in the
 // device error word, drains its own copies (again bounded) and returns.
 #include <cuda_runtime.h>
