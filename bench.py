@@ -552,7 +552,8 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
 def bench_batched(soma, workloads, torch, sptr, stream, steps=20):
     """Aggregate moves/s of the 64-system batch in one handle (one launch per
     kernel per step for all systems, CUDA graphs) against the same systems run
-    one after another, each in its own handle (create excluded)."""
+    one after another, each in its own handle with plain launches (one
+    soma_mc_steps call per system; create excluded)."""
     specs = workloads.batch64()
     systems = [soma.System(**{k: v for k, v in d.items() if k != "f_A"}) for d in specs]
     moves = sum(s.n_beads for s in systems) * steps
@@ -575,8 +576,7 @@ def bench_batched(soma, workloads, torch, sptr, stream, steps=20):
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             a.record(stream)
-        for _ in range(steps):
-            h.mc_steps(1, stream=sptr)
+        h.mc_steps(steps, stream=sptr)  # one call: the library enqueues one plain launch per step
         with torch.cuda.stream(stream):
             b.record(stream)
         torch.cuda.synchronize()
