@@ -38,7 +38,7 @@ def random_system(rng, i):
                        move=move, wall_z=int(rng.integers(0, 2)))
 
 
-@pytest.mark.parametrize("seed", range(40))
+@pytest.mark.parametrize("seed", range(80))
 def test_random_shape_steps_match_oracle(seed):
     rng = np.random.default_rng(1000 + seed)
     s = random_system(rng, 0)
@@ -66,7 +66,7 @@ def test_random_shape_steps_match_oracle(seed):
             assert abs(st["acc_gpu"] - st["acc_orc"]) <= st["suspect"]
 
 
-@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("seed", range(20))
 def test_random_mixed_handles_equal_solo_runs(seed):
     rng = np.random.default_rng(2000 + seed)
     systems = [random_system(rng, i) for i in range(int(rng.integers(2, 7)))]
