@@ -177,7 +177,9 @@ int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream);
 /* Wait for the handle's work and check the device error word. */
 int soma_sync(soma_handle* h, void* stream);
 
-/* Density counts of the current configuration, [2][n_cells] uint32. */
+/* Density counts of the current configuration, [2][n_cells] uint32, to host
+ * or device memory per `where`.  SOMA_EINVAL for a bad sys index, a NULL out
+ * or n != 2 n_cells.  Synchronises. */
 int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where);
 
 /* Laterally averaged volume fractions of the current configuration along
@@ -196,12 +198,17 @@ int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t 
  * buffer); 0 where the field has no variance.  Synchronises. */
 int soma_vertical_correlation(soma_handle* h, int sys, int type, double* out, size_t n);
 
-/* Fields used by the next step, [2][n_cells] FP32. */
+/* Fields used by the next step, [2][n_cells] FP32 (built from the current
+ * counts unless held or supplied).  SOMA_EINVAL as for soma_get_density.
+ * Synchronises. */
 int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where);
 
 /* Coupling write: replace the fields of the next step by those of the given
- * volume fractions phi [2][n_cells] (FP32); later steps rebuild from counts.
- * (Sec. 3.2: the particle run is handed the continuum's concentrations.) */
+ * volume fractions phi [2][n_cells] (FP32, host or device per `where`;
+ * copied); later steps rebuild from counts.  (Sec. 3.2: the particle run is
+ * handed the continuum's concentrations.)  SOMA_EINVAL for a bad sys, NULL
+ * phi or n != 2 n_cells; SOMA_ENOTSUP on SOMA_PREC_FP64 handles.
+ * Synchronises. */
 int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int where);
 
 /* Coupling start-up (Sec. 3.2: molecules placed from the supplied
@@ -237,16 +244,21 @@ int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n
  * n != 2 n_cells; SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises. */
 int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int where);
 
-/* Test mode: hold the fields at w [2][n_cells] (FP32) for every later step
- * (w == NULL releases them and rebuilds from the current counts). */
+/* Test mode: hold the fields at w [2][n_cells] (FP32, copied) for every
+ * later step (w == NULL releases them and rebuilds from the current counts).
+ * SOMA_EINVAL for a bad sys or n != 2 n_cells; SOMA_ENOTSUP on
+ * SOMA_PREC_FP64 handles.  Synchronises. */
 int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int where);
 
 /* Checkpoint: positions [n_beads][3] FP32 wrapped into [0, L), images
- * [n_beads][3] int16, and the step counter, in logical chain order. */
+ * [n_beads][3] int16, and the step counter, in logical chain order (host or
+ * device buffers per `where`; any of pos, img, step may be NULL).
+ * SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises. */
 int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* step, int where);
-/* Restore: positions must lie in [0, L) per axis; resets the acceptance
- * counters of every system of the handle and re-bins; the step counter is
- * shared by all systems. */
+/* Restore: positions must lie in [0, L) per axis (else SOMA_EINVAL and the
+ * state is kept); resets the acceptance counters of every system of the
+ * handle and re-bins; the step counter is shared by all systems and must be
+ * below 2^32 - 1.  Synchronises. */
 int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img, uint64_t step,
                    int where);
 
@@ -256,7 +268,9 @@ int soma_get_state64(soma_handle* h, int sys, double* pos, int16_t* img, uint64_
 int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* img, uint64_t step,
                      int where);
 
-/* FP64 observables of the current configuration. */
+/* FP64 observables of the current configuration (R_e^2, R_g^2 from
+ * unwrapped positions, E_bond, E_nb from the counts, acceptance since the
+ * last restore).  SOMA_EINVAL for a bad sys or NULL out.  Synchronises. */
 int soma_observables(soma_handle* h, int sys, soma_obs* out);
 /* Accepted-move counter only (one small device-to-host read, ordered after
  * the latest soma_mc_steps on whichever stream it was given; waits for it). */
@@ -270,7 +284,10 @@ int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted);
 int soma_copy_accepted(soma_handle* h, int sys, uint64_t* dst, void* stream);
 
 /* S(q) = (1/n_beads) |sum_j s_j exp(i q.r_j)|^2, s_j = +1 (A) / -1 (B), for
- * q = 2 pi m / L at the nq integer triples m_xyz [nq][3]; S is FP64 [nq]. */
+ * q = 2 pi m / L at the nq integer triples m_xyz [nq][3] (host); S is FP64
+ * [nq] (host).  SOMA_EINVAL for a bad sys, nq < 0 or NULL buffers (nq = 0
+ * does nothing).
+ * Synchronises. */
 int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz, double* S);
 
 /* Reorder the chains of every system now (storage order only; the
