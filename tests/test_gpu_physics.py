@@ -151,3 +151,47 @@ def test_long_run_statistics_agree_with_oracle(move):
     kstar = int(np.argmax(ra.mean(0)))
     se = np.sqrt(ga[:, kstar].var(ddof=1) / 8 + ra[:, kstar].var(ddof=1) / 8)
     assert abs(ga[:, kstar].mean() - ra[:, kstar].mean()) <= 3 * se
+
+
+def test_long_run_slab_statistics_agree_with_oracle():
+    """Between hard walls in z (config 0 shape): <R_e^2>, acceptance and the
+    total-density profile of the two wall layers from the GPU and the oracle
+    agree within 3 sigma over 8 seeds (the depletion at the walls is a
+    property of the confined melt that neither side is told)."""
+    kw = {**workloads.system_kwargs("config0"), "wall_z": 1}
+    burn, steps, every = 300, 1200, 100
+
+    def stats(seed, gpu):
+        s = soma.System(**{**kw, "seed": seed})
+        o = G.oracle_for(s)
+        re2, prof, acc = [], [], 0
+        if gpu:
+            h = soma.Handle(s)
+            h.mc_steps(burn)
+            a0 = h.accepted()
+            for _ in range(steps // every):
+                h.mc_steps(every)
+                re2.append(h.observables()["Re2"])
+                p = h.density_profile(2)
+                prof.append(p.sum(0))
+            acc = (h.accepted() - a0) / (steps * s.n_beads)
+            h.close()
+        else:
+            X = o.init()
+            o.run(X, 0, burn, n_threads=G.NTHREADS)
+            for k in range(steps // every):
+                r = o.run(X, burn + k * every, every, n_threads=G.NTHREADS)
+                acc += r["accepted"]
+                re2.append(o.observables(X)["Re2"])
+                prof.append(o.density_profile(o.density(X), 2).sum(0))
+            acc /= steps * o.n_b
+        prof = np.mean(prof, axis=0)
+        return np.mean(re2), acc, 0.5 * (prof[0] + prof[-1])
+
+    g = np.array([stats(sd, True) for sd in range(1, 9)])
+    r = np.array([stats(sd, False) for sd in range(1, 9)])
+    for k, name in ((0, "Re2"), (1, "acc"), (2, "wall-layer density")):
+        se = np.sqrt(g[:, k].var(ddof=1) / 8 + r[:, k].var(ddof=1) / 8)
+        assert abs(g[:, k].mean() - r[:, k].mean()) <= 3 * se + 1e-12, (name, g[:, k].mean(), r[:, k].mean(), se)
+    # the walls deplete the layers next to them
+    assert g[:, 2].mean() < 0.95
