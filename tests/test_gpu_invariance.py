@@ -110,3 +110,18 @@ def test_persistent_grid_invariance_full_size():
             ref = st
         else:
             _same(ref, st)
+
+
+def test_batch64_full_size_equals_solo_runs():
+    """The 64-system batch at full size, launched as bench.py times it (one
+    handle, CUDA graphs): after 5 steps every system is bit-identical to the
+    same system stepped alone."""
+    specs = workloads.batch64()
+    systems = [soma.System(**{k: v for k, v in d.items() if k != "f_A"}) for d in specs]
+    with soma.Handle(systems, graph_steps=5) as hb:
+        hb.mc_steps(5)
+        batched = [(hb.get_state(i)[0], hb.get_density(i), hb.accepted(i)) for i in range(len(systems))]
+    for i, s in enumerate(systems):
+        with soma.Handle(s, graph_steps=0) as h:
+            h.mc_steps(5)
+            _same(batched[i], (h.get_state()[0], h.get_density(), h.accepted()))
