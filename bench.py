@@ -420,6 +420,12 @@ def run_gpu(args):
         dens = torch.empty((2, n_c), dtype=torch.int32).pin_memory()
         accs = torch.zeros(args.steps, dtype=torch.int64).pin_memory()
         acc_np = accs.numpy()
+        # one untimed pass of the same calls (first-call costs: staging, pinned paths)
+        he.set_state(pin_pos.numpy(), pin_img.numpy(), step)
+        for i in range(min(3, args.steps)):
+            he.mc_steps(1, stream=sptr)
+            he.copy_accepted(acc_np[i:i + 1], stream=sptr)
+        he.get_density(out=dens.numpy().view(np.uint32))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         he.set_state(pin_pos.numpy(), pin_img.numpy(), step)
