@@ -184,3 +184,24 @@ def test_place_in_a_multi_system_handle_equals_single():
         assert np.array_equal(h.get_state()[0], placed)
         h.mc_steps(5)
         assert np.array_equal(h.get_state()[0], after[1])
+
+
+def test_umbrella_switched_on_keeps_supplied_fields_for_the_next_step():
+    """Fields supplied by soma_set_density for the next step stay as supplied
+    when the restraint is switched on afterwards; the restraint enters the
+    fields built after that step."""
+    s = soma.System(**workloads.system_kwargs("config0"))
+    orc = G.oracle_for(s)
+    tg = _target(s, seed=14)
+    rng = np.random.default_rng(2)
+    phi = rng.uniform(0.0, 1.0, size=(2, s.n_cells)).astype(np.float32)
+    with soma.Handle(s, graph_steps=0) as h:
+        h.mc_steps(2)
+        h.set_density(phi)
+        supplied = h.get_fields()
+        h.set_umbrella(tg, LAMBDA)
+        assert np.array_equal(h.get_fields(), supplied)
+        h.mc_steps(1)  # moves against the supplied fields
+        counts = h.get_density()
+        ref = orc.fields_umbrella(counts, tg.astype(np.float64), LAMBDA)
+        assert np.all(np.abs(h.get_fields() - ref) <= _fields_bound(orc, counts, tg, LAMBDA))
