@@ -112,6 +112,46 @@ def test_persistent_grid_invariance_full_size():
             _same(ref, st)
 
 
+@pytest.mark.parametrize("variant", ["uniform", "smart", "walls"])
+def test_long_run_grid_invariance_full_size(variant):
+    """A stage-ring race would show up only now and then: config1 at full
+    size for many steps, CUDA graphs and chain reorders on, with 3 and 1
+    resident CTAs per SM, must stay bit-identical throughout."""
+    kw = dict(workloads.system_kwargs("config1"))
+    if variant == "smart":
+        kw["move"] = soma.SOMA_MOVE_SMART
+    if variant == "walls":
+        kw["wall_z"] = 1
+    s = soma.System(**kw)
+    steps = 1000 if variant == "uniform" else 300
+    ref = None
+    for c in (3, 1):
+        with soma.Handle(s, ctas_per_sm=c, graph_steps=50, sort_interval=97) as h:
+            h.mc_steps(steps)
+            st = (h.get_state()[0], h.get_density(), h.accepted())
+        if ref is None:
+            ref = st
+        else:
+            _same(ref, st)
+
+
+def test_long_run_batch64_grid_invariance():
+    """The batch kernel's stage ring over 200 steps of the 64-system batch:
+    default and one resident CTA per SM give the same trajectories."""
+    specs = workloads.batch64()
+    systems = [soma.System(**{k: v for k, v in d.items() if k != "f_A"}) for d in specs]
+    ref = None
+    for c in (0, 1):
+        with soma.Handle(systems, ctas_per_sm=c, graph_steps=50) as hb:
+            hb.mc_steps(200)
+            st = [(hb.get_state(i)[0], hb.get_density(i), hb.accepted(i)) for i in range(len(systems))]
+        if ref is None:
+            ref = st
+        else:
+            for a, b in zip(ref, st):
+                _same(a, b)
+
+
 def test_batch64_full_size_equals_solo_runs():
     """The 64-system batch at full size, launched as bench.py times it (one
     handle, CUDA graphs): after 5 steps every system is bit-identical to the
