@@ -276,11 +276,14 @@ int soma_observables(soma_handle* h, int sys, soma_obs* out);
  * the latest soma_mc_steps on whichever stream it was given; waits for it). */
 int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted);
 /* The same count, enqueued: on `stream` (NULL = the handle's stream), after
- * the latest soma_mc_steps, the count is reduced on the device and copied to
- * *dst (host memory; pinned for the copy to be asynchronous).  Returns
- * without waiting; *dst is valid once the stream has synchronised.  Calls on
- * one stream complete in order, so a caller may enqueue one per step and
- * read them all after a single synchronisation. */
+ * the latest soma_mc_steps, the count is reduced on the device and lands in
+ * *dst (host memory).  Pinned host memory that the handle's device can
+ * address, 8-byte aligned, is written by the reduction kernel itself (no
+ * copy); other host memory gets an asynchronous copy (asynchronous only if
+ * pinned).  Returns without waiting; *dst is valid once the stream has
+ * synchronised.  Calls on one stream complete in order, so a caller may
+ * enqueue one per step and read them all after a single synchronisation.
+ * SOMA_EINVAL for a bad sys or NULL dst. */
 int soma_copy_accepted(soma_handle* h, int sys, uint64_t* dst, void* stream);
 
 /* S(q) = (1/n_beads) |sum_j s_j exp(i q.r_j)|^2, s_j = +1 (A) / -1 (B), for

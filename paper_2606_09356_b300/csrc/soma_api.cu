@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1080,6 +1081,17 @@ int soma_copy_accepted(soma_handle* h, int sys, uint64_t* dst, void* stream) {
   if (sys < 0 || sys >= h->n_sys || !dst) return SOMA_EINVAL;
   cudaStream_t s = pick(h, stream);
   CK(cudaStreamWaitEvent(s, h->order_ev, 0));  // after the latest steps, on any stream
+  // Pinned host memory that this device can address (8-byte aligned): the
+  // reduction stores the count there itself, with no copy-engine round trip
+  // behind the step.  Any other host memory: reduce, then copy.
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer != nullptr && at.device == h->device &&
+      (reinterpret_cast<uintptr_t>(at.devicePointer) & 7u) == 0) {
+    CK(launch_sum_acc(h->d_sys, sys, static_cast<unsigned long long*>(at.devicePointer), s));
+    return SOMA_OK;
+  }
+  (void)cudaGetLastError();  // an unregistered pointer is not an error here
   CK(launch_sum_acc(h->d_sys, sys, h->d_acc_sum, s));
   CK(cudaMemcpyAsync(dst, h->d_acc_sum, 8, cudaMemcpyDeviceToHost, s));
   return SOMA_OK;

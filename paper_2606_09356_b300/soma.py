@@ -422,8 +422,9 @@ class Handle:
         return a.value
 
     def copy_accepted(self, dst, sys=0, stream=None):
-        """Enqueue the accepted count into dst (a 1-element uint64 host array,
-        pinned for an asynchronous copy); valid after the stream synchronises."""
+        """Enqueue the accepted count into dst (a 1-element uint64 host array;
+        pinned and 8-byte aligned, the reduction kernel writes it directly,
+        otherwise it is copied); valid after the stream synchronises."""
         _check(self.lib.soma_copy_accepted(self.h, sys, _ptr(dst), stream), "soma_copy_accepted")
 
     def structure_factor(self, m, sys=0):

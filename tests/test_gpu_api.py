@@ -107,23 +107,39 @@ def test_accepted_count_is_read_after_steps_on_a_caller_stream():
         assert a1 == h.accepted() and a1 > a0
 
 
-def test_enqueued_accepted_counts_follow_each_step():
+def _count_buffers(kind, n):
+    """n one-count destinations: pinned and 8-byte aligned (written by the
+    reduction kernel itself), pinned at an odd 4-byte offset, or pageable
+    (both copied)."""
+    import torch
+    if kind == "pageable":
+        a = np.zeros(n, np.uint64)
+        return [a[i:i + 1] for i in range(n)], lambda: [int(v) for v in a]
+    raw = torch.zeros(8 * n + 8, dtype=torch.uint8).pin_memory().numpy()
+    off = 0 if kind == "pinned" else 4
+    views = [raw[off + 8 * i: off + 8 * i + 8].view(np.uint64) for i in range(n)]
+    return views, lambda: [int(v[0]) for v in views]
+
+
+@pytest.mark.parametrize("kind", ["pinned", "pinned_unaligned", "pageable"])
+def test_enqueued_accepted_counts_follow_each_step(kind):
     import torch
     s = soma.System(**workloads.system_kwargs("config0"))
     st = torch.cuda.Stream()
-    got = torch.zeros(6, dtype=torch.int64).pin_memory().numpy()
+    dst, read = _count_buffers(kind, 6)
     with soma.Handle(s, graph_steps=0) as h:
-        ref = []
         for i in range(6):
             h.mc_steps(1, stream=st.cuda_stream)
-            h.copy_accepted(got[i:i + 1], stream=st.cuda_stream)
+            h.copy_accepted(dst[i], stream=st.cuda_stream)
         torch.cuda.synchronize()
+        got = read()
         assert got[-1] == h.accepted()
+    ref = []
     with soma.Handle(s, graph_steps=0) as h2:  # the same trajectory, read step by step
         for i in range(6):
             h2.mc_steps(1)
             ref.append(h2.accepted())
-    assert list(got) == ref
+    assert got == ref
 
 
 @pytest.mark.parametrize("kw", [
