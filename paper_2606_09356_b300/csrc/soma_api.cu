@@ -243,7 +243,7 @@ void build_args(soma_handle* h) {
     a.sys_index = S.sys_index;
     a.n_poly = S.n_poly;
     a.chains_per_tile = S.P ? move_kernel_chains_per_tile(S.P) : 0;
-    a.n_tiles = S.P ? (S.n_poly + a.chains_per_tile - 1) / a.chains_per_tile : 0;
+    a.n_tiles = S.P ? (int)(((int64_t)S.n_poly + a.chains_per_tile - 1) / a.chains_per_tile) : 0;
     a.bin = h->hist_mode == SOMA_HIST_FUSED ? 1 : 0;
     a.n_c = S.n_c;
     a.x = S.x;
@@ -430,7 +430,32 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
   return SOMA_OK;
 }
 
+// Key, value and CUB buffers of the chain reorder (about 40 bytes per chain),
+// allocated once, on first need.
+int ensure_sort_work(soma_handle* h) {
+  SortWork& w = h->sort;
+  if (w.temp) return SOMA_OK;
+  const size_t n = (size_t)w.n_chains;
+  w.keys_in = (unsigned long long*)dev_alloc(h, 8 * n);
+  w.keys_out = (unsigned long long*)dev_alloc(h, 8 * n);
+  w.vals_in = (uint32_t*)dev_alloc(h, 4 * n);
+  w.vals_out = (uint32_t*)dev_alloc(h, 4 * n);
+  w.chain_sys = (int32_t*)dev_alloc(h, 4 * n);
+  w.temp_bytes = sort_temp_bytes(w.n_chains, w.end_bit);
+  void* temp = dev_alloc(h, w.temp_bytes);
+  if (!w.keys_in || !w.keys_out || !w.vals_in || !w.vals_out || !w.chain_sys || !temp) return SOMA_ENOMEM;
+  std::vector<int32_t> cs(n);
+  for (int s = 0; s < h->n_sys; ++s)
+    std::fill(cs.begin() + h->host_sys[s].chain_base, cs.begin() + h->host_sys[s].chain_base + h->host_sys[s].n_poly,
+              s);
+  CK(cudaMemcpy(w.chain_sys, cs.data(), 4 * n, cudaMemcpyHostToDevice));
+  w.temp = temp;  // set last: a failed attempt is retried in full
+  return SOMA_OK;
+}
+
 int enqueue_reorder(soma_handle* h, cudaStream_t s) {
+  int rc = ensure_sort_work(h);
+  if (rc) return rc;
   TimedEvent te;
   if (h->opt.kernel_timing) begin_timed(h, s, te, T_SORT);
   CK(launch_reorder(h->d_sys, h->n_sys, h->sort, h->sm_count, s));
@@ -557,8 +582,12 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   if (!out) return SOMA_EINVAL;
   *out = nullptr;
   if (!sys || n_sys < 1 || n_sys > (1 << 16)) return SOMA_EINVAL;
-  for (int s = 0; s < n_sys; ++s)
+  int64_t total_chains = 0;
+  for (int s = 0; s < n_sys; ++s) {
     if (validate_desc(sys[s]) != SOMA_OK) return SOMA_EINVAL;
+    total_chains += sys[s].n_poly;
+  }
+  if (total_chains > (int64_t)UINT32_MAX) return SOMA_EINVAL;  // the reorder numbers chains in 32 bits
   soma_options o;
   if (opt)
     o = *opt;
@@ -707,27 +736,14 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   if (!h->d_acc || !h->d_sys || !h->d_step || !h->d_err || !h->d_obs || !h->d_acc_sum || !h->d_stage_pos ||
       !h->d_stage_img || !h->d_stage_phi)
     return bail(SOMA_ENOMEM);
-  // sort work
+  // sort work: allocated here when chains may be reordered (a sort interval
+  // or the autotuner), else on the first soma_reorder
   {
     int bits = 0;
     while ((1 << bits) < n_sys) ++bits;
     h->sort.n_chains = chain_base;
     h->sort.end_bit = 40 + bits;
-    h->sort.keys_in = (unsigned long long*)dev_alloc(h, 8 * (size_t)chain_base);
-    h->sort.keys_out = (unsigned long long*)dev_alloc(h, 8 * (size_t)chain_base);
-    h->sort.vals_in = (uint32_t*)dev_alloc(h, 4 * (size_t)chain_base);
-    h->sort.vals_out = (uint32_t*)dev_alloc(h, 4 * (size_t)chain_base);
-    h->sort.chain_sys = (int32_t*)dev_alloc(h, 4 * (size_t)chain_base);
-    h->sort.temp_bytes = sort_temp_bytes(chain_base, h->sort.end_bit);
-    h->sort.temp = dev_alloc(h, h->sort.temp_bytes);
-    if (!h->sort.keys_in || !h->sort.keys_out || !h->sort.vals_in || !h->sort.vals_out || !h->sort.chain_sys ||
-        !h->sort.temp)
-      return bail(SOMA_ENOMEM);
-    std::vector<int32_t> cs((size_t)chain_base);
-    for (int s = 0; s < n_sys; ++s)
-      std::fill(cs.begin() + h->host_sys[s].chain_base, cs.begin() + h->host_sys[s].chain_base + sys[s].n_poly, s);
-    if (cudaMemcpy(h->sort.chain_sys, cs.data(), 4 * cs.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-      return bail(SOMA_ECUDA);
+    if ((h->sort_interval != 0 || o.autotune) && (rc = ensure_sort_work(h)) != SOMA_OK) return bail(rc);
   }
   if (cudaMemcpy(h->d_sys, h->host_sys.data(), sizeof(SysDev) * n_sys, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(h->d_step, 0, 8 * (size_t)n_sys) != cudaSuccess || cudaMemset(h->d_err, 0, 4) != cudaSuccess ||
@@ -1331,7 +1347,7 @@ int soma_autotune(soma_handle* h) {
     CK(cudaMemcpy(p, S.y, S.n_b * 4, cudaMemcpyDeviceToHost)); p += S.n_b * 4;
     CK(cudaMemcpy(p, S.z, S.n_b * 4, cudaMemcpyDeviceToHost)); p += S.n_b * 4;
     CK(cudaMemcpy(p, S.img, S.n_b * 8, cudaMemcpyDeviceToHost)); p += S.n_b * 8;
-    CK(cudaMemcpy(p, S.chain_id, S.n_poly * 4, cudaMemcpyDeviceToHost)); p += S.n_poly * 4;
+    CK(cudaMemcpy(p, S.chain_id, (size_t)S.n_poly * 4, cudaMemcpyDeviceToHost)); p += (size_t)S.n_poly * 4;
     CK(cudaMemcpy(p, S.counts, S.n_c * 24, cudaMemcpyDeviceToHost)); p += S.n_c * 24;
     CK(cudaMemcpy(p, S.w, S.n_c * 8, cudaMemcpyDeviceToHost));
   }
@@ -1346,7 +1362,7 @@ int soma_autotune(soma_handle* h) {
       CK(cudaMemcpy(S.y, p, S.n_b * 4, cudaMemcpyHostToDevice)); p += S.n_b * 4;
       CK(cudaMemcpy(S.z, p, S.n_b * 4, cudaMemcpyHostToDevice)); p += S.n_b * 4;
       CK(cudaMemcpy(S.img, p, S.n_b * 8, cudaMemcpyHostToDevice)); p += S.n_b * 8;
-      CK(cudaMemcpy(S.chain_id, p, S.n_poly * 4, cudaMemcpyHostToDevice)); p += S.n_poly * 4;
+      CK(cudaMemcpy(S.chain_id, p, (size_t)S.n_poly * 4, cudaMemcpyHostToDevice)); p += (size_t)S.n_poly * 4;
       CK(cudaMemcpy(S.counts, p, S.n_c * 24, cudaMemcpyHostToDevice)); p += S.n_c * 24;
       CK(cudaMemcpy(S.w, p, S.n_c * 8, cudaMemcpyHostToDevice));
     }

@@ -153,7 +153,7 @@ __global__ void k_init64(const SysDev* __restrict__ systems, int sys) {
   load_sys(&S, systems + sys);
   const int N = S.N;
   const double sigma = N > 1 ? sqrt(1.0 / (3.0 * (N - 1))) : 0.0;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += gridDim.x * blockDim.x) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
     double X = 0, Y = 0, Z = 0;
     S.chain_id[c] = (uint32_t)c;
     for (int i = 0; i < N; ++i) {
@@ -248,7 +248,7 @@ __global__ void k_obs_chains64(const SysDev* __restrict__ systems, int sys, doub
   load_sys(&S, systems + sys);
   const int N = S.N;
   double re2 = 0, rg2 = 0, bb = 0;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += gridDim.x * blockDim.x) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b0 = (int64_t)c * N;
     double first[3] = {0, 0, 0}, prev[3] = {0, 0, 0}, sum[3] = {0, 0, 0}, sq = 0;
     for (int i = 0; i < N; ++i) {

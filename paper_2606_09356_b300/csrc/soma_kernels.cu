@@ -279,7 +279,7 @@ __global__ void k_set_step(unsigned long long* counters, int n_sys, unsigned lon
 // Chain c (logical = storage slot) from bead 0 at (X, Y, Z): the bonds of
 // the initial configuration, accumulated in FP64, wrapped (z folded between
 // walls), written.
-__device__ void grow_chain(const SysDev& S, int c, double X, double Y, double Z) {
+__device__ void grow_chain(const SysDev& S, int64_t c, double X, double Y, double Z) {
   const int N = S.N;
   const double sigma = N > 1 ? sqrt(1.0 / (3.0 * (N - 1))) : 0.0;
   S.chain_id[c] = (uint32_t)c;
@@ -325,7 +325,7 @@ __device__ void grow_chain(const SysDev& S, int c, double X, double Y, double Z)
 __global__ void k_init(const SysDev* __restrict__ systems, int sys) {
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += gridDim.x * blockDim.x) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
     const uint4 r = philox10(make_uint4(0u, (uint32_t)c, kInitStep, (uint32_t)S.sys_index), S.rk);
     grow_chain(S, c, (double)S.L[0] * ((double)(r.x >> 8) * 0x1p-24),
                (double)S.L[1] * ((double)(r.y >> 8) * 0x1p-24), (double)S.L[2] * ((double)(r.z >> 8) * 0x1p-24));
@@ -355,7 +355,7 @@ __global__ void k_place(const SysDev* __restrict__ systems, int sys, const unsig
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
   const double h = 0.5 / sqrt(3.0);  // correctly rounded, as on the host
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += gridDim.x * blockDim.x) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
     const uint4 r0 = philox10(make_uint4(0u, (uint32_t)c, kPlaceStep, (uint32_t)S.sys_index), S.rk);
     const uint4 r1 = philox10(make_uint4(1u, (uint32_t)c, kPlaceStep, (uint32_t)S.sys_index), S.rk);
     const uint4 r2 = philox10(make_uint4(2u, (uint32_t)c, kPlaceStep, (uint32_t)S.sys_index), S.rk);
@@ -472,7 +472,7 @@ __global__ void k_obs_chains(const SysDev* __restrict__ systems, int sys, double
   load_sys(&S, systems + sys);
   const int N = S.N;
   double re2 = 0, rg2 = 0, bb = 0;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += gridDim.x * blockDim.x) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b0 = (int64_t)c * N;
     // unwrapped positions relative to bead 0 (keeps the sums well conditioned)
     double first[3] = {0, 0, 0}, prev[3] = {0, 0, 0}, sum[3] = {0, 0, 0}, sq = 0;
@@ -653,7 +653,7 @@ cudaError_t launch_place(const SysDev* systems, int sys, const SysDev& host, con
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
   if (*total == 0) return cudaSuccess;
-  const int grid = (int)std::min<int64_t>((host.n_poly + 127) / 128, (int64_t)sm_count * 8);
+  const int grid = (int)std::min<int64_t>(((int64_t)host.n_poly + 127) / 128, (int64_t)sm_count * 8);
   k_place<<<grid, 128, 0, s>>>(systems, sys, prefix, *total);
   return cudaGetLastError();
 }

@@ -84,6 +84,8 @@ def test_strerror_and_defaults(lib):
     dict(wall_z=2),                     # unknown z boundary
     dict(move=1, A=0.2),                # smart: drift A^2 (N-1)/2 above 1/2
     dict(move=1, N=1, n_A=1, A=0.7, box=(4.5, 4.5, 4.5)),  # smart: Gaussian tail wider than half the box
+    dict(n_poly=(2**31 - 64) // 32 + 1),  # one chain past 2^31 - 65 beads
+    dict(grid=(1024, 1024, 512)),         # 2^29 cells: past the cell limit
 ])
 def test_create_rejects_bad_descriptors_without_gpu(lib, bad):
     kw = dict(n_poly=8, N=32, n_A=16, box=(4.0, 4.0, 4.0), grid=(4, 4, 4), chiN=1.0, kappaN=1.0)
@@ -92,6 +94,17 @@ def test_create_rejects_bad_descriptors_without_gpu(lib, bad):
     arr = (soma.soma_system_desc * 1)(d)
     h = ctypes.c_void_p()
     assert lib.soma_create(arr, 1, None, ctypes.byref(h)) == soma.SOMA_EINVAL
+    assert not h.value
+
+
+def test_create_rejects_more_than_2_32_chains_in_one_handle_without_gpu(lib):
+    """Each system is within its own limits, but the chain reorder numbers
+    the chains of all systems of a handle in 32 bits."""
+    n = 2**31 - 65
+    ds = [soma.System(n_poly=n, N=1, n_A=1, box=(4.0, 4.0, 4.0), grid=(4, 4, 4), chiN=0.0, kappaN=1.0, A=0.1,
+                      system_id=i).desc() for i in range(3)]
+    h = ctypes.c_void_p()
+    assert lib.soma_create((soma.soma_system_desc * 3)(*ds), 3, None, ctypes.byref(h)) == soma.SOMA_EINVAL
     assert not h.value
 
 
