@@ -156,3 +156,40 @@ def test_density_profiles_and_vertical_correlation_match_oracle(kw):
             assert np.allclose(h.density_profile(axis), orc.density_profile(counts, axis), rtol=1e-13, atol=1e-13)
         for t in range(2):
             assert np.allclose(h.vertical_correlation(t), orc.vertical_correlation(counts, t), rtol=1e-9, atol=1e-9)
+
+
+def test_empty_and_zero_work_calls():
+    """Zero steps change nothing (state, step, counts, accepted count);
+    negative step counts are rejected with the state kept; empty S(q),
+    Philox and normal-deviate requests return empty results."""
+    s = soma.System(**workloads.system_kwargs("config0"))
+    with soma.Handle(s, graph_steps=4) as h:
+        h.mc_steps(3)
+        before = h.get_state(), h.get_density(), h.accepted()
+        h.mc_steps(0)
+        with pytest.raises(soma.SomaError) as e:
+            h.mc_steps(-1)
+        assert e.value.code == soma.SOMA_EINVAL
+        after = h.get_state(), h.get_density(), h.accepted()
+        assert after[0][2] == before[0][2] == 3
+        assert np.array_equal(after[0][0], before[0][0]) and np.array_equal(after[1], before[1])
+        assert after[2] == before[2]
+        assert h.structure_factor(np.zeros((0, 3), np.int32)).shape == (0,)
+    assert soma.soma_philox4x32(np.zeros((0, 4), np.uint32), np.zeros((0, 2), np.uint32)).shape == (0, 4)
+    assert soma.soma_normal_deviates(np.zeros(0, np.uint32)).shape == (0,)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n_poly=1, N=1, n_A=1, box=(1.0, 1.0, 1.0), grid=(1, 1, 1), chiN=0.0, kappaN=50.0, A=0.3),
+    dict(n_poly=1, N=2, n_A=1, box=(12.0, 12.0, 12.0), grid=(1, 1, 1), chiN=20.0, kappaN=50.0),
+    dict(n_poly=1, N=64, n_A=32, box=(3.0, 3.0, 3.0), grid=(1, 2, 3), chiN=20.0, kappaN=50.0),
+])
+def test_smallest_systems_step_like_the_oracle(kw):
+    """One chain: a single bead in a single cell, a dimer in one cell, one
+    64-bead chain (a full warp) on six cells; five steps against the oracle."""
+    s = soma.System(**kw)
+    with soma.Handle(s, graph_steps=0) as h:
+        for _ in range(5):
+            G.compare_step(h)
+        counts = h.get_density()
+        assert counts[0].sum() == s.n_A and counts[1].sum() == s.N - s.n_A
