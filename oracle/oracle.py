@@ -42,6 +42,12 @@ class OrcDesc(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("wall_z", ctypes.c_int32),
         ("pos64", ctypes.c_int32),
+        ("conv", ctypes.c_int32),
+        ("n_A_alt", ctypes.c_int32),
+        ("zone_lo", ctypes.c_double),
+        ("zone_hi", ctypes.c_double),
+        ("thr", ctypes.c_uint64 * 4),
+        ("mol", ctypes.POINTER(ctypes.c_uint8)),
     ]
 
 
@@ -106,6 +112,9 @@ class Oracle:
             L.orc_vertical_correlation.argtypes = [dp, u32p, ctypes.c_int, f64p]
             L.orc_place.restype = ctypes.c_int
             L.orc_run.restype = ctypes.c_int64
+            L.orc_conversion_threshold.argtypes = [ctypes.c_double]
+            L.orc_conversion_threshold.restype = ctypes.c_uint64
+            L.orc_convert.argtypes = [dp, f64p, ctypes.c_uint32, i64p]
             cls._lib = L
         return cls._lib
 
@@ -122,6 +131,35 @@ class Oracle:
         self.d.chiN, self.d.kappaN, self.d.A, self.d.seed = float(chiN), float(kappaN), float(A), int(seed)
         self.n_b = n_poly * N
         self.n_c = int(grid[0]) * int(grid[1]) * int(grid[2])
+        self.types = None
+
+    # -- molecule types and boundary-zone conversion ---------------------
+    def set_conversion(self, n_A_alt, zone_lo, zone_hi, p):
+        """Chains carry molecule types (all 0 at first) and convert in the
+        zones; p = per-step probabilities (bottom 0->1, bottom 1->0, top 0->1,
+        top 1->0), turned into thresholds by the oracle."""
+        self.d.conv = 1
+        self.d.n_A_alt = int(n_A_alt)
+        self.d.zone_lo, self.d.zone_hi = float(zone_lo), float(zone_hi)
+        for k in range(4):
+            self.d.thr[k] = int(self.lib().orc_conversion_threshold(float(p[k])))
+        if self.types is None:
+            self.types = np.zeros(self.d.n_poly, np.uint8)
+            self.d.mol = self.types.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+    def set_types(self, types):
+        """Molecule type of every logical chain (copied in; conversion must be on)."""
+        assert self.types is not None
+        self.types[:] = np.asarray(types, np.uint8)
+
+    def convert(self, pos, t):
+        """The boundary-zone conversions that open step t (types change in
+        place); returns the counts (bottom 0->1, bottom 1->0, top 0->1, top 1->0)."""
+        pos = np.ascontiguousarray(pos, np.float64)
+        c4 = np.zeros(4, np.int64)
+        self.lib().orc_convert(ctypes.byref(self.d), _p(pos, ctypes.c_double), ctypes.c_uint32(t & 0xFFFFFFFF),
+                               _p(c4, ctypes.c_int64))
+        return c4
 
     # -- constants -------------------------------------------------------
     def params(self):

@@ -49,6 +49,12 @@
 //   orc_place             pinned: the exact law of the bead-0 cell (target
 //                         weights convolved with the uniform offset) and the
 //                         Gaussian bond statistics of the placed chains.
+//   orc_convert           pinned: the two-state Markov law of a molecule's
+//                         type inside a zone (binomial counts after t steps),
+//                         the zone occupancy law of bead 0 (uniform, so the
+//                         fraction converted by certain flips is the zone's
+//                         share of the box), and the one-bead Boltzmann law
+//                         of a converted molecule's bead type.
 //   The chiN, kappaN > 0 statistics of a dense melt have no closed form:
 //   parity unpinned there except against this oracle itself.
 #include <cmath>
@@ -75,6 +81,13 @@ typedef struct {
   uint64_t seed;      // Philox key (lo, hi)
   int32_t wall_z;     // 1: hard walls at z = 0 and z = L_z instead of periodic z
   int32_t pos64;      // 1: positions are held in FP64 (cell lookup in FP64), 0: in FP32
+  // molecule types and boundary-zone conversion (Sec. 3.2), conv = 1:
+  int32_t conv;       // 1: chains carry a molecule type and convert in the zones
+  int32_t n_A_alt;    // beads 0..n_A_alt-1 of a converted (type-1) molecule are A
+  double zone_lo;     // width of the bottom conversion zone, z in [0, zone_lo)
+  double zone_hi;     // width of the top conversion zone, z in [L_z - zone_hi, L_z)
+  uint64_t thr[4];    // thresholds {bottom 0->1, bottom 1->0, top 0->1, top 1->0}
+  uint8_t* mol;       // molecule type per logical chain (0 own, 1 converted)
 } orc_desc;
 
 typedef struct {
@@ -166,7 +179,12 @@ static int64_t n_beads(const orc_desc* d) { return (int64_t)d->n_poly * d->N; }
 static int64_t n_cells(const orc_desc* d) {
   return (int64_t)d->grid[0] * d->grid[1] * d->grid[2];
 }
-static int type_of(const orc_desc* d, int i) { return i < d->n_A ? 0 : 1; }
+// Bead i of logical chain c is type A (0) if i is below the A-block length
+// of the chain's molecule type, else B (1).
+static int type_of(const orc_desc* d, int64_t c, int i) {
+  const int nA = (d->conv && d->mol && d->mol[c]) ? d->n_A_alt : d->n_A;
+  return i < nA ? 0 : 1;
+}
 
 void orc_params(const orc_desc* d, double* k_b, double* A_eff, double* rho_bar) {
   *k_b = bond_k(d);
@@ -276,7 +294,7 @@ void orc_density(const orc_desc* d, const double* pos, uint32_t* counts) {
   for (int c = 0; c < d->n_poly; ++c)
     for (int i = 0; i < d->N; ++i) {
       const double* r = pos + ((int64_t)c * d->N + i) * 3;
-      counts[type_of(d, i) * nc + cell_of(d, r)] += 1;
+      counts[type_of(d, c, i) * nc + cell_of(d, r)] += 1;
     }
 }
 
@@ -432,7 +450,10 @@ static uint32_t place_weight(float phi) {
 
 int orc_place(const orc_desc* d, const float* target, double* pos) {
   const int64_t nc = n_cells(d);
-  const float* phi = target + (int64_t)type_of(d, 0) * nc;
+  // every chain is built as the system's own molecule (type 0): its bead 0
+  // has type A if n_A > 0
+  if (d->conv && d->mol) std::memset(d->mol, 0, (size_t)d->n_poly);
+  const float* phi = target + (int64_t)(d->n_A > 0 ? 0 : 1) * nc;
   std::vector<uint64_t> P(nc);
   uint64_t Q = 0;
   for (int64_t c = 0; c < nc; ++c) {
@@ -554,7 +575,7 @@ static int64_t move_set(const orc_desc* d, double* pos, const double* w, uint32_
         }
         bias = (rev - fwd) / (2.0 * s2);  // -ln[q(r'->r) / q(r->r')]
       }
-      const double* wt = w + (int64_t)type_of(d, i) * nc;
+      const double* wt = w + (int64_t)type_of(d, chain, i) * nc;
       double margin;
       if (d->wall_z && !(rn[2] >= 0.0 && rn[2] < d->box[2])) {
         margin = HUGE_VAL;  // through a wall: rejected
@@ -648,7 +669,7 @@ void orc_structure_factor(const orc_desc* d, const double* pos, int nq, const in
       for (int i = 0; i < d->N; ++i) {
         const double* r = pos + ((int64_t)c * d->N + i) * 3;
         double ph = q[0] * r[0] + q[1] * r[1] + q[2] * r[2];
-        double s = type_of(d, i) == 0 ? 1.0 : -1.0;
+        double s = type_of(d, c, i) == 0 ? 1.0 : -1.0;
         re += s * std::cos(ph);
         im += s * std::sin(ph);
       }
@@ -657,9 +678,58 @@ void orc_structure_factor(const orc_desc* d, const double* pos, int nq, const in
 }
 
 // ---------------------------------------------------------------------------
+// Boundary zones (Sec. 3.2): transition layers at the bottom and top of the
+// box in z where molecules are converted to and from the continuum model's
+// units, at conversion rates the continuum model supplies.
+// Reading: each chain carries a molecule type m (0: the system's own
+// architecture, n_A A-beads; 1: a converted molecule, n_A_alt A-beads).  At
+// the start of step t, before set 0, a chain whose bead 0 lies in a zone --
+// its wrapped z, as the FP32 number the positions are stored in, below
+// (float)zone_lo (bottom), else at or above (float)(L_z - zone_hi) (top) --
+// draws word 0 of the Philox counter (0xFFFFFFFF, c, t, s) (a bead word no
+// bead has) and changes its type iff that word is below the threshold of
+// its zone and current type, thr = floor(p 2^32 + 1/2) for the per-step
+// probability p.  Positions are untouched; the step's moves and counts see
+// the new types, the fields entering the step come from the previous counts.
+// Returns the conversions, per zone and direction, in counts4 (if given).
+// ---------------------------------------------------------------------------
+uint64_t orc_conversion_threshold(double p) {
+  if (!(p > 0.0)) return 0;
+  if (p >= 1.0) return 4294967296ull;
+  return (uint64_t)std::floor(p * 4294967296.0 + 0.5);
+}
+
+void orc_convert(const orc_desc* d, const double* pos, uint32_t t, int64_t* counts4) {
+  if (!d->conv || !d->mol) return;
+  const double L = d->box[2];
+  const float zlo = (float)d->zone_lo;
+  const float zhi = (float)(L - d->zone_hi);
+  for (int c = 0; c < d->n_poly; ++c) {
+    const double z = pos[(int64_t)c * d->N * 3 + 2];
+    const float zw = d->wall_z ? (float)z : (float)(z - L * std::floor(z / L));
+    int zone;
+    if (zw < zlo)
+      zone = 0;
+    else if (zw >= zhi)
+      zone = 1;
+    else
+      continue;
+    uint32_t r[4];
+    draw(d, 0xFFFFFFFFu, (uint32_t)c, t, r);
+    const int m = d->mol[c];
+    if ((uint64_t)r[0] < d->thr[2 * zone + m]) {
+      d->mol[c] = (uint8_t)(1 - m);
+      if (counts4) counts4[2 * zone + m] += 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // A run of n_steps steps starting at step t0.  Unless w_frozen is given, the
 // fields entering step t come from the counts after step t-1 (or after the
-// initial configuration), with the umbrella term when target is given.  Optional accumulators per step: occupancy counts
+// initial configuration), with the umbrella term when target is given; with
+// conversion on, each step starts with the boundary-zone conversions.
+// Optional accumulators per step: occupancy counts
 // summed over steps, the joint cell histogram of two-bead chains, R_e^2 and
 // the accepted count.  Returns the total accepted count.
 // ---------------------------------------------------------------------------
@@ -677,6 +747,7 @@ int64_t orc_run(const orc_desc* d, double* pos, uint32_t t0, int64_t n_steps,
   }
   int64_t total = 0;
   for (int64_t s = 0; s < n_steps; ++s) {
+    orc_convert(d, pos, (uint32_t)(t0 + s), nullptr);
     int64_t a = orc_mc_step(d, pos, w.data(), (uint32_t)(t0 + s), nullptr, nullptr, nullptr,
                             n_threads);
     total += a;

@@ -26,6 +26,10 @@ list means the pin holds.  The facts used:
   quantised target weights convolved with the uniform offset (piecewise-
   linear integrals, integrated exactly between their kinks), and Gaussian
   bond statistics of the placed chains.
+* Boundary-zone conversion: the two-state Markov law of a molecule's type
+  in a zone (binomial type counts after t steps), the binomial zone
+  occupancy of the uniform bead 0 under certain flips, the Boltzmann law of
+  a converted bead's type, and the ideal-chain S(q) of a two-type mixture.
 """
 import os
 import subprocess
@@ -557,6 +561,122 @@ def pin_vertical_correlation(O):
     return fails
 
 
+# ---------------------------------------------------------------------------
+# Molecule types and boundary-zone conversion (Sec. 3.2).
+def _binomial_z(k, n, p):
+    return (k - n * p) / np.sqrt(max(n * p * (1.0 - p), 1e-12))
+
+
+def pin_conversion_markov(O, n=20000, steps=8):
+    """With one zone covering the whole box, every chain's type is an
+    independent two-state Markov chain with per-step probabilities a (0->1)
+    and b (1->0): from type 0, P(type 1 after t steps) = pi (1 - (1-a-b)^t),
+    pi = a/(a+b); the number of type-1 chains is binomial.  Each zone is
+    tried on its own with unequal rates in the two directions."""
+    fails = []
+    L = 4.0
+    for zone, rates in (("bottom", (0.30, 0.10)), ("top", (0.15, 0.45))):
+        o = O(n, 2, 1, (L, L, L), (4, 4, 4), 0.0, 0.0, A=0.2, seed=31, wall_z=1)
+        p = (rates[0], rates[1], 0.0, 0.0) if zone == "bottom" else (0.0, 0.0, rates[0], rates[1])
+        o.set_conversion(0, L if zone == "bottom" else 0.0, L if zone == "top" else 0.0, p)
+        k0 = 0 if zone == "bottom" else 2
+        a, b = o.d.thr[k0] / 2.0**32, o.d.thr[k0 + 1] / 2.0**32
+        pos = o.init()
+        n1_prev = 0
+        for t in range(steps):
+            c4 = o.convert(pos, t)
+            n1 = int(o.types.sum())
+            if c4[k0] - c4[k0 + 1] != n1 - n1_prev or c4[2 - k0] or c4[3 - k0]:
+                fails.append(f"{zone} zone: conversion counts {c4.tolist()} do not account for {n1 - n1_prev}")
+            n1_prev = n1
+            pt = a / (a + b) * (1.0 - (1.0 - a - b) ** (t + 1))
+            z = _binomial_z(n1, n, pt)
+            if abs(z) > 5.0:
+                fails.append(f"{zone} zone step {t}: {n1} type-1 chains, expected {n * pt:.1f} (z={z:.1f})")
+    return fails
+
+
+def pin_conversion_zone_law(O, n=20000):
+    """Bead 0 of the initial chains is uniform in the box, so with certain
+    flips (p = 1) the first conversion turns exactly the chains whose bead 0
+    lies in a zone: binomial with the zone's share of the box, per zone; the
+    second flips them all back; the A-bead count follows the types."""
+    fails = []
+    L, lo, hi = 4.0, 0.5, 1.25
+    for wall in (1, 0):
+        o = O(n, 4, 3, (3.0, 3.0, L), (6, 6, 8), 0.0, 0.0, A=0.2, seed=32 + wall, wall_z=wall)
+        o.set_conversion(1, lo, hi, (1.0, 1.0, 1.0, 1.0))
+        pos = o.init()
+        c4 = o.convert(pos, 0)
+        for k, (cnt, share) in enumerate(((c4[0], lo / L), (c4[2], hi / L))):
+            z = _binomial_z(int(cnt), n, share)
+            if abs(z) > 5.0:
+                fails.append(f"walls={wall}: zone {k} converted {cnt}, expected {n * share:.0f} (z={z:.1f})")
+        n1 = int(o.types.sum())
+        if n1 != c4[0] + c4[2]:
+            fails.append(f"walls={wall}: {n1} type-1 chains after {c4.tolist()}")
+        nA = int(o.density(pos)[0].sum())
+        if nA != (n - n1) * 3 + n1 * 1:
+            fails.append(f"walls={wall}: {nA} A beads for {n1} converted chains")
+        o.convert(pos, 1)
+        if int(o.types.sum()) != 0:
+            fails.append(f"walls={wall}: certain flips left {int(o.types.sum())} chains converted")
+    return fails
+
+
+def pin_conversion_type_field(O, blocks=16, per_block=15):
+    """Single beads of an A molecule converted to B at the first step (a
+    zone covering the box, p(0->1) = 1, p(1->0) = 0) then move in a frozen
+    field with the B field: occupancy proportional to exp(-w_B(c)), and no
+    A bead left."""
+    fails = []
+    rng = np.random.default_rng(41)
+    o = O(4096, 1, 1, (1.0, 1.5, 2.0), (2, 3, 4), 0.0, 0.0, A=0.6, seed=9)
+    o.set_conversion(0, 2.0, 0.0, (1.0, 0.0, 0.0, 0.0))
+    w = rng.normal(0.0, 0.8, size=(2, o.n_c))
+    pos = o.init()
+    o.run(pos, 0, 10, w_frozen=w, n_threads=NTHREADS)
+    if int(o.types.sum()) != o.d.n_poly:
+        fails.append(f"{int(o.types.sum())} of {o.d.n_poly} beads converted")
+    samples = []
+    for b in range(blocks):
+        r = o.run(pos, 10 + b * per_block, per_block, w_frozen=w, n_threads=NTHREADS, occ=True)
+        occ = r["occ"].reshape(2, o.n_c).astype(np.float64)
+        if occ[0].sum() != 0:
+            fails.append("A beads counted after the conversion")
+        samples.append(occ[1] / occ[1].sum())
+    p = np.exp(-w[1])
+    _block_test(fails, "converted bead occupancy", np.array(samples), p / p.sum())
+    return fails
+
+
+def pin_conversion_structure_factor(O, seeds=12):
+    """Ideal chains, every other one converted (its A block n_A_alt long):
+    S(q) = (1/N) sum over the two molecule types, each with half the weight,
+    of sum_ij s_i s_j exp(-q^2 |i-j| / (6(N-1)))."""
+    fails = []
+    n_poly, N, n_A, n_A_alt, L = 2048, 16, 8, 3, 4.0
+    ms = np.array([(1, 0, 0), (0, 1, 1), (1, 1, 1), (2, 0, 0)], np.int32)
+    ij = np.abs(np.arange(N)[:, None] - np.arange(N)[None, :])
+    s0 = np.where(np.arange(N) < n_A, 1.0, -1.0)
+    s1 = np.where(np.arange(N) < n_A_alt, 1.0, -1.0)
+    types = (np.arange(n_poly) % 2).astype(np.uint8)
+    est = []
+    for sd in range(seeds):
+        o = O(n_poly, N, n_A, (L, L, L), (16, 16, 16), 0.0, 0.0, seed=200 + sd)
+        o.set_conversion(n_A_alt, 0.0, 0.0, (0.0, 0.0, 0.0, 0.0))
+        o.set_types(types)
+        est.append(o.structure_factor(o.init(), ms))
+    est = np.array(est)
+    for k, m in enumerate(ms):
+        q2 = float(((2 * np.pi / L) ** 2) * (m ** 2).sum())
+        K = np.exp(-q2 * ij / (6.0 * (N - 1)))
+        exact = 0.5 * ((s0[:, None] * s0[None, :] * K).sum() + (s1[:, None] * s1[None, :] * K).sum()) / N
+        se = est[:, k].std(ddof=1) / np.sqrt(seeds)
+        _check(fails, f"S(q) with converted chains m={tuple(m)}", est[:, k].mean(), exact, 5 * se)
+    return fails
+
+
 ALL_PINS = {
     "philox_uniformity": pin_philox_uniformity,
     "philox_triton": pin_philox_triton,
@@ -577,4 +697,8 @@ ALL_PINS = {
     "wall_dimer_cell_pairs": pin_wall_dimer_cell_pairs,
     "density_profile": pin_density_profile,
     "vertical_correlation": pin_vertical_correlation,
+    "conversion_markov": pin_conversion_markov,
+    "conversion_zone_law": pin_conversion_zone_law,
+    "conversion_type_field": pin_conversion_type_field,
+    "conversion_structure_factor": pin_conversion_structure_factor,
 }

@@ -19,7 +19,7 @@ MUTATIONS = [
      "ideal_dynamics"),
     ("field term sign", "dE = k_b * dEb + wt[cell_of(d, rn)] - wt[cell_of(d, ri)];",
      "dE = k_b * dEb - wt[cell_of(d, rn)] + wt[cell_of(d, ri)];", "single_bead_field"),
-    ("types swapped", "return i < d->n_A ? 0 : 1;", "return i < d->n_A ? 1 : 0;", "dimer_cell_pairs"),
+    ("types swapped", "return i < nA ? 0 : 1;", "return i < nA ? 1 : 0;", "dimer_cell_pairs"),
     ("right neighbour dropped",
      "unit_closed_open(r[a]) - 1.0);\n        for (int j = i - 1; j <= i + 1; j += 2)",
      "unit_closed_open(r[a]) - 1.0);\n        for (int j = i - 1; j <= i - 1; j += 2)", "ideal_dynamics"),
@@ -35,7 +35,7 @@ MUTATIONS = [
     ("philox key bump", "k1 += W1;", "k1 += W0;", "philox_triton"),
     ("init bond variance", "std::sqrt(1.0 / (3.0 * (double)(d->N - 1)))",
      "std::sqrt(1.0 / (2.0 * (double)(d->N - 1)))", "init_statistics"),
-    ("composition sign lost", "double s = type_of(d, i) == 0 ? 1.0 : -1.0;", "double s = 1.0;",
+    ("composition sign lost", "double s = type_of(d, c, i) == 0 ? 1.0 : -1.0;", "double s = 1.0;",
      "structure_factor_ideal"),
     ("bond of second bead anchored to bead 0", "p[3 * i + 0] = p[3 * (i - 1) + 0] + sigma * z0;",
      "p[3 * i + 0] = p[0] + sigma * z0;", "init_statistics"),
@@ -65,8 +65,18 @@ MUTATIONS = [
     ("profile averaged over the wrong cell count", "for (int i = 0; i < 2 * n; ++i) out[i] /= (double)m;",
      "for (int i = 0; i < 2 * n; ++i) out[i] /= (double)nc;", "density_profile"),
     ("correlation pairs wrap between walls", "        if (d->wall_z) continue;\n", "", "vertical_correlation"),
-    ("placement weights of the other type", "const float* phi = target + (int64_t)type_of(d, 0) * nc;",
-     "const float* phi = target + (int64_t)(1 - type_of(d, 0)) * nc;", "place_bead0_law"),
+    ("placement weights of the other type", "const float* phi = target + (int64_t)(d->n_A > 0 ? 0 : 1) * nc;",
+     "const float* phi = target + (int64_t)(d->n_A > 0 ? 1 : 0) * nc;", "place_bead0_law"),
+    ("conversion directions swapped", "if ((uint64_t)r[0] < d->thr[2 * zone + m]) {",
+     "if ((uint64_t)r[0] < d->thr[2 * zone + 1 - m]) {", "conversion_markov"),
+    ("conversion zones swapped", "if ((uint64_t)r[0] < d->thr[2 * zone + m]) {",
+     "if ((uint64_t)r[0] < d->thr[2 * (1 - zone) + m]) {", "conversion_markov"),
+    ("top zone measured from the bottom", "const float zhi = (float)(L - d->zone_hi);",
+     "const float zhi = (float)d->zone_hi;", "conversion_zone_law"),
+    ("converted molecule keeps its A block", "? d->n_A_alt : d->n_A;", "? d->n_A : d->n_A;",
+     "conversion_type_field"),
+    ("conversion counts merged across directions", "if (counts4) counts4[2 * zone + m] += 1;",
+     "if (counts4) counts4[2 * zone] += 1;", "conversion_markov"),
 ]
 
 
