@@ -244,6 +244,44 @@ int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n
  * n != 2 n_cells; SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises. */
 int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int where);
 
+/* Boundary zones (Sec. 3.2): layers at the bottom and top of the box in z
+ * where molecules are converted to and from the continuum model's units, at
+ * rates the continuum model supplies and updates.  With conversion on,
+ * every chain carries a molecule type: 0, the system's own architecture
+ * (n_A A-beads), or 1, a converted molecule with n_A_alt A-beads (the rest
+ * B).  Each step then opens with the conversions: a chain whose bead 0 lies
+ * in the bottom zone (z < zone_lo) or the top zone (z >= L_z - zone_hi), both
+ * compared in FP32 with the stored z, changes its type iff word 0 of the
+ * Philox counter (0xFFFFFFFF, logical chain, step, system_id) is below
+ * floor(p 2^32 + 1/2), p the zone's per-step probability for the chain's
+ * current type: p[4] = {bottom 0->1, bottom 1->0, top 0->1, top 1->0} (host,
+ * not retained).  The step's moves and counts use the new types; the fields
+ * entering it come from the previous counts.  Calling again updates the
+ * zones and rates (types kept) and restarts the conversion counts.
+ * n_A_alt < 0 switches conversion off: every chain returns to type 0 and the
+ * counts and fields are rebuilt.  soma_place and the initial configuration
+ * build every chain as type 0.
+ * SOMA_EINVAL for a bad sys, n_A_alt > N, p NULL or outside [0, 1], or zone
+ * widths negative, not finite or together wider than L_z; SOMA_ENOTSUP on
+ * SOMA_PREC_FP64 handles and for chains longer than 64 beads.  Synchronises. */
+int soma_set_conversion(soma_handle* h, int sys, int32_t n_A_alt, double zone_lo, double zone_hi, const double* p);
+/* Conversions since the rates were last set, out[4] (host) in the order of
+ * p above (zeros if conversion was never on).  SOMA_EINVAL for a bad sys or
+ * NULL out.  Synchronises. */
+int soma_get_conversions(soma_handle* h, int sys, uint64_t* out);
+/* Molecule type (0 or 1) of every chain in logical order, out[n_poly]
+ * (host).  SOMA_EINVAL for a bad sys, NULL out or n != n_poly.
+ * Synchronises. */
+int soma_get_chain_types(soma_handle* h, int sys, uint8_t* out, size_t n);
+/* Set the molecule types (conversion must be on; each 0 or 1), in logical
+ * order, types[n_poly] (host); the counts of the current positions and
+ * their fields are rebuilt with the new types (fields supplied for the next
+ * step by soma_set_density are replaced).  With soma_get_state/soma_set_state
+ * this completes a checkpoint.  SOMA_EINVAL (state kept) for a bad sys,
+ * NULL types, n != n_poly, a value above 1, or conversion off.
+ * Synchronises. */
+int soma_set_chain_types(soma_handle* h, int sys, const uint8_t* types, size_t n);
+
 /* Test mode: hold the fields at w [2][n_cells] (FP32, copied) for every
  * later step (w == NULL releases them and rebuilds from the current counts).
  * SOMA_EINVAL for a bad sys or n != 2 n_cells; SOMA_ENOTSUP on

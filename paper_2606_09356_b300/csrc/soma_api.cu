@@ -261,6 +261,8 @@ void build_args(soma_handle* h) {
     a.err = h->d_err;
     a.smart = h->desc[s].move == SOMA_MOVE_SMART ? 1 : 0;
     a.wall_z = S.wall_z;
+    a.conv = S.conv;
+    a.n_A_alt = S.n_A_alt;
     {
       const double s2 = (double)S.A * (double)S.A / 3.0;
       a.sig = (float)std::sqrt(s2);
@@ -374,6 +376,14 @@ int enqueue_umbrella_fields(soma_handle* h, cudaStream_t s, int sys, bool graph,
   return SOMA_OK;
 }
 
+// Boundary-zone conversions that open step i of system sys (conversion on).
+int enqueue_convert(soma_handle* h, cudaStream_t s, int sys, bool graph, long long t0, int i) {
+  const SysDev& S = h->host_sys[sys];
+  if (!S.conv) return SOMA_OK;
+  CK(launch_convert(h->d_sys, sys, S.n_poly, step_ref(h, sys, graph, t0, i), h->sm_count, s));
+  return SOMA_OK;
+}
+
 // n steps of every system on stream `s`.  One system: one move kernel per
 // step (fields from the previous counts, fused histogram, clearing of the
 // next count buffer).  Several systems: one k_move_batch launch per step and
@@ -384,6 +394,8 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
   const bool batched = h->n_sys > 1;
   int rc;
   for (int i = 0; i < n; ++i) {
+    for (int sys = 0; sys < h->n_sys; ++sys)
+      if ((rc = enqueue_convert(h, s, sys, graph, t0, i))) return rc;
     if (batched) {
       for (size_t g = 0; g < h->batches.size(); ++g) {
         const BatchArgs* b = &h->batches[g];
@@ -486,16 +498,21 @@ int capture_graph(soma_handle* h, int steps) {
 
 // Clear the three count buffers, bin the current positions into buffer
 // (step - 1) mod 3 and fill the field array from them (unless held).
+int rebin_one(soma_handle* h, int g, cudaStream_t s) {
+  SysDev& S = h->host_sys[g];
+  CK(cudaMemsetAsync(S.counts, 0, sizeof(uint32_t) * 6 * S.n_c, s));
+  if (h->f64)
+    CK(launch_bin64(h->d_sys, g, (long long)h->step - 1, h->sm_count, s));
+  else
+    CK(launch_bin(h->d_sys, g, S.n_b, fixed_step((long long)h->step - 1), h->sm_count, s));
+  CK(launch_field(h->fargs[g], fixed_step((long long)h->step - 1), 0, s));
+  return SOMA_OK;
+}
+
 int rebin_all(soma_handle* h, cudaStream_t s) {
-  for (int g = 0; g < h->n_sys; ++g) {
-    SysDev& S = h->host_sys[g];
-    CK(cudaMemsetAsync(S.counts, 0, sizeof(uint32_t) * 6 * S.n_c, s));
-    if (h->f64)
-      CK(launch_bin64(h->d_sys, g, (long long)h->step - 1, h->sm_count, s));
-    else
-      CK(launch_bin(h->d_sys, g, S.n_b, fixed_step((long long)h->step - 1), h->sm_count, s));
-    CK(launch_field(h->fargs[g], fixed_step((long long)h->step - 1), 0, s));
-  }
+  int rc;
+  for (int g = 0; g < h->n_sys; ++g)
+    if ((rc = rebin_one(h, g, s))) return rc;
   return SOMA_OK;
 }
 
@@ -1206,6 +1223,100 @@ int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n
   return sync_all(h);
 }
 
+int soma_set_conversion(soma_handle* h, int sys, int32_t n_A_alt, double zone_lo, double zone_hi, const double* p) {
+  NvtxRange nvtx_range("soma_set_conversion");
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
+  SysDev& S = h->host_sys[sys];
+  const bool on = n_A_alt >= 0;
+  if (on) {
+    if (h->f64 || S.P == 0) return SOMA_ENOTSUP;  // register-path FP32 systems only
+    if (n_A_alt > S.N || !p) return SOMA_EINVAL;
+    const double Lz = h->desc[sys].box[2];
+    if (!std::isfinite(zone_lo) || !std::isfinite(zone_hi) || zone_lo < 0.0 || zone_hi < 0.0 ||
+        zone_lo + zone_hi > Lz)
+      return SOMA_EINVAL;
+    for (int k = 0; k < 4; ++k)
+      if (!(p[k] >= 0.0 && p[k] <= 1.0)) return SOMA_EINVAL;
+  }
+  if ((rc = sync_all(h))) return rc;
+  if (on) {
+    if (!S.conv_count) {
+      S.conv_count = (unsigned long long*)dev_alloc(h, 32);
+      if (!S.conv_count) return SOMA_ENOMEM;
+    }
+    CK(cudaMemset(S.conv_count, 0, 32));
+    S.conv = 1;
+    S.n_A_alt = n_A_alt;
+    S.zone_lo = (float)zone_lo;
+    S.zone_hi = (float)(h->desc[sys].box[2] - zone_hi);
+    for (int k = 0; k < 4; ++k)  // convert iff word < floor(p 2^32 + 1/2)
+      S.thr[k] = p[k] <= 0.0 ? 0ull
+                 : p[k] >= 1.0 ? 4294967296ull
+                               : (unsigned long long)std::floor(p[k] * 4294967296.0 + 0.5);
+  } else if (S.conv) {  // off: every chain back to the system's own molecule
+    CK(launch_set_types(h->d_sys, sys, nullptr, h->sm_count, h->stream));
+    S.conv = 0;
+  }
+  CK(cudaMemcpy(h->d_sys + sys, &S, sizeof(SysDev), cudaMemcpyHostToDevice));
+  build_args(h);
+  drop_graph(h);
+  if (!on) {  // the counts and fields follow the types
+    h->phi_pending[sys] = 0;
+    if ((rc = rebin_one(h, sys, h->stream))) return rc;
+  }
+  return sync_all(h);
+}
+
+int soma_get_conversions(soma_handle* h, int sys, uint64_t* out) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if ((rc = sync_all(h))) return rc;
+  if (!S.conv_count) {
+    for (int k = 0; k < 4; ++k) out[k] = 0;
+    return SOMA_OK;
+  }
+  CK(cudaMemcpy(out, S.conv_count, 32, cudaMemcpyDeviceToHost));
+  return SOMA_OK;
+}
+
+int soma_get_chain_types(soma_handle* h, int sys, uint8_t* out, size_t n) {
+  NvtxRange nvtx_range("soma_get_chain_types");
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if (n != (size_t)S.n_poly) return SOMA_EINVAL;
+  if ((rc = sync_all(h))) return rc;
+  uint8_t* stage = reinterpret_cast<uint8_t*>(h->d_stage_img);  // max_nb * 6 >= n_poly bytes
+  CK(launch_get_types(h->d_sys, sys, stage, h->sm_count, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(out, stage, n, cudaMemcpyDeviceToHost));
+  return SOMA_OK;
+}
+
+int soma_set_chain_types(soma_handle* h, int sys, const uint8_t* types, size_t n) {
+  NvtxRange nvtx_range("soma_set_chain_types");
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (sys < 0 || sys >= h->n_sys || !types) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[sys];
+  if (n != (size_t)S.n_poly || !S.conv) return SOMA_EINVAL;
+  for (size_t c = 0; c < n; ++c)
+    if (types[c] > 1) return SOMA_EINVAL;
+  if ((rc = sync_all(h))) return rc;
+  uint8_t* stage = reinterpret_cast<uint8_t*>(h->d_stage_img);
+  CK(cudaMemcpy(stage, types, n, cudaMemcpyHostToDevice));
+  CK(launch_set_types(h->d_sys, sys, stage, h->sm_count, h->stream));
+  // the counts of the current positions with the new types, and their fields
+  h->phi_pending[sys] = 0;
+  if ((rc = rebin_one(h, sys, h->stream))) return rc;
+  return sync_all(h);
+}
+
 int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int where) {
   NvtxRange nvtx_range("soma_place");
   int rc = check_live(h);
@@ -1352,8 +1463,11 @@ int soma_autotune(soma_handle* h) {
     CK(cudaMemcpy(p, S.w, S.n_c * 8, cudaMemcpyDeviceToHost));
   }
   const size_t acc_n = (size_t)h->acc_per_sys * h->n_sys;
-  std::vector<unsigned long long> acc_save(acc_n);
+  std::vector<unsigned long long> acc_save(acc_n), conv_save(4 * (size_t)h->n_sys, 0ull);
   CK(cudaMemcpy(acc_save.data(), h->d_acc, 8 * acc_n, cudaMemcpyDeviceToHost));
+  for (int s = 0; s < h->n_sys; ++s)
+    if (h->host_sys[s].conv_count)
+      CK(cudaMemcpy(&conv_save[4 * (size_t)s], h->host_sys[s].conv_count, 32, cudaMemcpyDeviceToHost));
   auto restore = [&]() -> int {
     for (int s = 0; s < h->n_sys; ++s) {
       const SysDev& S = h->host_sys[s];
@@ -1367,6 +1481,9 @@ int soma_autotune(soma_handle* h) {
       CK(cudaMemcpy(S.w, p, S.n_c * 8, cudaMemcpyHostToDevice));
     }
     CK(cudaMemcpy(h->d_acc, acc_save.data(), 8 * acc_n, cudaMemcpyHostToDevice));
+    for (int s = 0; s < h->n_sys; ++s)
+      if (h->host_sys[s].conv_count)
+        CK(cudaMemcpy(h->host_sys[s].conv_count, &conv_save[4 * (size_t)s], 32, cudaMemcpyHostToDevice));
     h->step = step0;
     return SOMA_OK;
   };

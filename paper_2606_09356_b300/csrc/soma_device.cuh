@@ -34,6 +34,12 @@ __device__ __forceinline__ void load_sys(SysDev* dst, const SysDev* src) {
   __syncthreads();
 }
 
+// A-block length of the chain in storage slot `slot`: n_A, or n_A_alt for a
+// converted molecule (conversion on and the chain-id word's top bit set).
+__device__ __forceinline__ int chain_n_A(const SysDev& S, int64_t slot) {
+  return (S.conv && (S.chain_id[slot] & kTypeBit)) ? S.n_A_alt : S.n_A;
+}
+
 __device__ __forceinline__ int cell_axis(float x, float cps, int n) {
   const int i = (int)(x * cps);  // x >= 0 (and a NaN converts to 0), so truncation is floor
   return min(i, n - 1);

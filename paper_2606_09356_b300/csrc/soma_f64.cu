@@ -205,7 +205,7 @@ __global__ void k_gather_state64(const SysDev* __restrict__ systems, int sys, do
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t lb = (int64_t)S.chain_id[b / S.N] * S.N + b % S.N;
+    const int64_t lb = (int64_t)(S.chain_id[b / S.N] & kIdMask) * S.N + b % S.N;
     pos[3 * lb + 0] = S.x64[b];
     pos[3 * lb + 1] = S.y64[b];
     pos[3 * lb + 2] = S.z64[b];
@@ -221,7 +221,7 @@ __global__ void k_scatter_state64(const SysDev* __restrict__ systems, int sys, c
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t lb = (int64_t)S.chain_id[b / S.N] * S.N + b % S.N;
+    const int64_t lb = (int64_t)(S.chain_id[b / S.N] & kIdMask) * S.N + b % S.N;
     S.x64[b] = pos[3 * lb + 0];
     S.y64[b] = pos[3 * lb + 1];
     S.z64[b] = pos[3 * lb + 2];

@@ -9,6 +9,12 @@ namespace soma {
 
 constexpr uint32_t kInitStep = 0xFFFFFFFFu;  // Philox step word reserved for init
 
+// Molecule types (boundary-zone conversion): the top bit of a chain-id word
+// is the chain's molecule type (1: converted), the rest its logical id.
+constexpr uint32_t kTypeBit = 0x80000000u;
+constexpr uint32_t kIdMask = 0x7FFFFFFFu;
+constexpr uint32_t kConvWord = 0xFFFFFFFFu;  // Philox bead word of the conversion draw (no bead has it)
+
 // Per-system constants and array pointers, one entry per system in a device
 // array.  Kernels copy their system's entry into shared memory.
 struct alignas(16) SysDev {
@@ -48,6 +54,12 @@ struct alignas(16) SysDev {
   float umbN_N;
   int32_t umbrella;             // 1: the restraint is on
   int32_t wall_z;               // 1: hard walls at z = 0 and z = L_z (z not periodic)
+  // molecule types and boundary-zone conversion (the types ride in chain_id's top bit)
+  int32_t conv;                 // 1: types honoured, conversion draws open every step
+  int32_t n_A_alt;              // A beads of a converted (type-1) molecule
+  float zone_lo, zone_hi;       // bottom zone: z < zone_lo; top zone: z >= zone_hi (FP32)
+  unsigned long long thr[4];    // convert iff word < thr: {bottom 0->1, bottom 1->0, top 0->1, top 1->0}
+  unsigned long long* conv_count;  // [4] conversions since the rates were last set
 };
 
 // Everything the move kernel needs for one system, passed by value as a
@@ -77,6 +89,8 @@ struct MoveArgs {
   // bond vectors, xi standard normal; s2 = A^2/3, drift = s2 k_b, sig = sqrt(s2)
   float sig, drift, inv2s2;  // inv2s2 = 1 / (2 s2)
   int32_t wall_z;            // 1: hard walls at z = 0 and z = L_z (host-side flag; kernels are templated)
+  int32_t conv;              // 1: molecule types in chain_id's top bit (single launches: templated)
+  int32_t n_A_alt;           // A beads of a converted molecule
 };
 
 // Up to kMaxBatch systems stepped by one persistent launch: their constants

@@ -51,7 +51,7 @@ __global__ void k_move_set_generic(const SysDev* __restrict__ systems, int sys, 
     const float bx = hb ? S.x[b + 1] : 0.f, by = hb ? S.y[b + 1] : 0.f, bz = hb ? S.z[b + 1] : 0.f;
     int cell = cell_of(S, x, y, z), wrap = 21;
     const float* wt = S.w + (i < S.n_A ? 0 : S.n_c);
-    const int ok = try_move(S, wt, (uint32_t)i, S.chain_id[slot], t, x, y, z, cell, wrap, ax, ay, az,
+    const int ok = try_move(S, wt, (uint32_t)i, S.chain_id[slot] & kIdMask, t, x, y, z, cell, wrap, ax, ay, az,
                             ha ? 1.f : 0.f, bx, by, bz, hb ? 1.f : 0.f);
     if (ok) {
       S.x[b] = x; S.y[b] = y; S.z[b] = z;
@@ -76,7 +76,7 @@ __global__ void k_bin(const SysDev* __restrict__ systems, int sys, StepRef r) {
   uint32_t* cnt = count_buffer(S.counts, S.n_c, r.get());
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(b % S.N);
-    atomicAdd(cnt + 2 * cell_of(S, S.x[b], S.y[b], S.z[b]) + (i < S.n_A ? 0 : 1), 1u);
+    atomicAdd(cnt + 2 * cell_of(S, S.x[b], S.y[b], S.z[b]) + (i < chain_n_A(S, b / S.N) ? 0 : 1), 1u);
   }
 }
 
@@ -387,7 +387,7 @@ __global__ void k_gather_state(const SysDev* __restrict__ systems, int sys, floa
   load_sys(&S, systems + sys);
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
     const int64_t slot = b / S.N, i = b % S.N;
-    const int64_t lb = (int64_t)S.chain_id[slot] * S.N + i;
+    const int64_t lb = (int64_t)(S.chain_id[slot] & kIdMask) * S.N + i;
     pos[3 * lb + 0] = S.x[b];
     pos[3 * lb + 1] = S.y[b];
     pos[3 * lb + 2] = S.z[b];
@@ -404,11 +404,60 @@ __global__ void k_scatter_state(const SysDev* __restrict__ systems, int sys, con
   load_sys(&S, systems + sys);
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
     const int64_t slot = b / S.N, i = b % S.N;
-    const int64_t lb = (int64_t)S.chain_id[slot] * S.N + i;
+    const int64_t lb = (int64_t)(S.chain_id[slot] & kIdMask) * S.N + i;
     S.x[b] = pos[3 * lb + 0];
     S.y[b] = pos[3 * lb + 1];
     S.z[b] = pos[3 * lb + 2];
     reinterpret_cast<short4*>(S.img)[b] = make_short4(img[3 * lb + 0], img[3 * lb + 1], img[3 * lb + 2], 0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Boundary zones (Sec. 3.2): the conversions that open step t.  A chain whose
+// bead 0 lies in the bottom zone (z < zone_lo) or the top zone (z >= zone_hi)
+// changes its molecule type iff word 0 of Philox counter (kConvWord, logical
+// id, t, system) is below the threshold of its zone and current type.  One
+// thread per chain; the four conversion counts are summed per CTA.
+// ---------------------------------------------------------------------------
+__global__ void k_convert(const SysDev* __restrict__ systems, int sys, StepRef r) {
+  __shared__ SysDev S;
+  __shared__ unsigned long long n_conv[4];
+  if (threadIdx.x < 4) n_conv[threadIdx.x] = 0;
+  load_sys(&S, systems + sys);  // synchronises
+  const uint32_t t = (uint32_t)r.get();
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
+    const float z = S.z[c * S.N];
+    const int zone = z < S.zone_lo ? 0 : (z >= S.zone_hi ? 1 : -1);
+    if (zone < 0) continue;
+    const uint32_t word = S.chain_id[c];
+    const int m = (word & kTypeBit) ? 1 : 0;
+    const uint4 w = philox10(make_uint4(kConvWord, word & kIdMask, t, (uint32_t)S.sys_index), S.rk);
+    if ((unsigned long long)w.x < S.thr[2 * zone + m]) {
+      S.chain_id[c] = word ^ kTypeBit;
+      atomicAdd(&n_conv[2 * zone + m], 1ull);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && n_conv[threadIdx.x]) atomicAdd(S.conv_count + threadIdx.x, n_conv[threadIdx.x]);
+}
+
+// Molecule types in logical chain order <-> the chain-id words' top bit.
+__global__ void k_get_types(const SysDev* __restrict__ systems, int sys, uint8_t* __restrict__ out) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t word = S.chain_id[c];
+    out[word & kIdMask] = (word & kTypeBit) ? 1 : 0;
+  }
+}
+
+// types == nullptr: every chain back to type 0.
+__global__ void k_set_types(const SysDev* __restrict__ systems, int sys, const uint8_t* __restrict__ types) {
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t id = S.chain_id[c] & kIdMask;
+    S.chain_id[c] = id | ((types && types[id]) ? kTypeBit : 0u);
   }
 }
 
@@ -552,7 +601,7 @@ __global__ void k_structure_factor(const SysDev* __restrict__ systems, int sys, 
     }
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
       const float fx = S.x[b] * S.invL[0], fy = S.y[b] * S.invL[1], fz = S.z[b] * S.invL[2];
-      const double s = ((int)(b % S.N) < S.n_A) ? 1.0 : -1.0;
+      const double s = ((int)(b % S.N) < chain_n_A(S, b / S.N)) ? 1.0 : -1.0;
 #pragma unroll
       for (int j = 0; j < kSqChunk; ++j) {
         float f = fmaf(mx[j], fx, fmaf(my[j], fy, mz[j] * fz));
@@ -692,6 +741,22 @@ cudaError_t launch_init(const SysDev* systems, int sys, int64_t n_poly, cudaStre
   const int threads = 128;
   const int64_t blocks = (n_poly + threads - 1) / threads;
   k_init<<<(unsigned)blocks, threads, 0, s>>>(systems, sys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const SysDev* systems, int sys, int64_t n_poly, StepRef r, int sm_count, cudaStream_t s) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_poly + 255) / 256, (int64_t)sm_count * 8));
+  k_convert<<<grid, 256, 0, s>>>(systems, sys, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_types(const SysDev* systems, int sys, uint8_t* out, int sm_count, cudaStream_t s) {
+  k_get_types<<<sm_count * 4, 256, 0, s>>>(systems, sys, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_types(const SysDev* systems, int sys, const uint8_t* types, int sm_count, cudaStream_t s) {
+  k_set_types<<<sm_count * 4, 256, 0, s>>>(systems, sys, types);
   return cudaGetLastError();
 }
 

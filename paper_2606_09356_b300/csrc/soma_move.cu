@@ -28,7 +28,9 @@
 // persistent launch (tiles of all systems in one sequence).  Both are
 // specialised on the proposal (uniform, or bond-force-biased: smart_pair)
 // and on the z boundary (periodic, or hard walls: a proposal leaving the
-// slab is rejected, z bonds are plain differences).
+// slab is rejected, z bonds are plain differences); k_move also on molecule
+// types (boundary-zone conversion: a bead's type follows the A block of its
+// chain's type, carried in the chain-id word's top bit).
 // Every mbarrier wait is bounded: on expiry the kernel sets kErrTimeout in the
 // device error word, drains its own copies (again bounded) and returns.
 #include <cuda_runtime.h>
@@ -505,7 +507,7 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, cons
 // it, moves the even then the odd beads of its chains, writes back, bins.
 // Returns the number of accepted moves of this lane.
 // prev: count buffer of step t-1 (fields), cur: count buffer of step t (histogram).
-template <bool kFromCounts, bool kSmart, bool kWall>
+template <bool kFromCounts, bool kSmart, bool kWall, bool kConv>
 __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, const MoveStage& st, uint64_t* empty,
                                                  long long tl, const uint2* __restrict__ prev,
                                                  uint32_t* __restrict__ cur, int warp, int lane) {
@@ -513,7 +515,6 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   const int k = lane & (P - 1);
   const int chain_in_tile = warp * (32 / P) + lane / P;
   const int e = 2 * k, o = 2 * k + 1;
-  const int te = e < a.n_A ? 0 : 1, to = o < a.n_A ? 0 : 1;
   const int c0 = tile * a.chains_per_tile;
   const int nch = min(a.chains_per_tile, a.n_poly - c0);
   const bool chain_ok = chain_in_tile < nch;
@@ -531,9 +532,18 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
     if (he) { xe = lds1(st.x + lb); ye = lds1(st.y + lb); ze = lds1(st.z + lb); }
     if (ho) { xo = lds1(st.x + lb + 1); yo = lds1(st.y + lb + 1); zo = lds1(st.z + lb + 1); }
   }
-  const uint32_t cid = chain_ok ? lds1(st.cid + chain_in_tile) : 0u;
+  const uint32_t cid_word = chain_ok ? lds1(st.cid + chain_in_tile) : 0u;
   __syncwarp();
   if (lane == 0) mbar_arrive(empty);  // this warp is done with the stage
+  // bead types: the A block of the chain's molecule type (with conversion
+  // on, the chain-id word's top bit; the random numbers follow the id alone)
+  uint32_t cid = cid_word;
+  int n_A = a.n_A;
+  if (kConv) {
+    cid = cid_word & kIdMask;
+    if (cid_word & kTypeBit) n_A = a.n_A_alt;
+  }
+  const int te = e < n_A ? 0 : 1, to = o < n_A ? 0 : 1;
 
   bool acc, acco;
   int ce, co;
@@ -605,7 +615,7 @@ __device__ __forceinline__ void drain(uint64_t* full, int issued, int* err) {
 }
 
 // Register budget for 3 resident CTAs per SM (72 registers, no spill).
-template <bool kFromCounts, bool kSmart, bool kWall>
+template <bool kFromCounts, bool kSmart, bool kWall, bool kConv>
 __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __grid_constant__ MoveArgs a, StepRef r) {
   __shared__ MoveStage stage[kStages];
   __shared__ __align__(8) uint64_t full[kStages];
@@ -634,7 +644,7 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __g
   for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
     const int s = it % kStages;
     if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, a.err)) break;
-    nacc += consume_tile<kFromCounts, kSmart, kWall>(a, tile, stage[s], &empty[s], tl, prev, cur, warp, lane);
+    nacc += consume_tile<kFromCounts, kSmart, kWall, kConv>(a, tile, stage[s], &empty[s], tl, prev, cur, warp, lane);
   }
   nacc = __reduce_add_sync(0xffffffffu, nacc);
   if (lane == 0 && nacc) atomicAdd(a.acc + blockIdx.x, (unsigned long long)nacc);
@@ -690,9 +700,15 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
     const uint2* prev = reinterpret_cast<const uint2*>(count_buffer(a.counts, a.n_c, tl - 1));
     uint32_t* cur = count_buffer(a.counts, a.n_c, tl);
     const int lt = tile - p.tile_start[sys];
-    unsigned n = a.from_counts
-                     ? consume_tile<true, kSmart, kWall>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
-                     : consume_tile<false, kSmart, kWall>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
+    unsigned n;
+    if (a.conv)
+      n = a.from_counts
+              ? consume_tile<true, kSmart, kWall, true>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
+              : consume_tile<false, kSmart, kWall, true>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
+    else
+      n = a.from_counts
+              ? consume_tile<true, kSmart, kWall, false>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
+              : consume_tile<false, kSmart, kWall, false>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
     n = __reduce_add_sync(0xffffffffu, n);
     if (lane == 0 && n) atomicAdd(a.acc + blockIdx.x, (unsigned long long)n);
   }
@@ -724,7 +740,7 @@ cudaError_t launch_wait_selfcheck(int* err, long long cycles, cudaStream_t s) {
 int move_kernel_max_ctas_per_sm() {
   int n = 0;
   const cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<true, false, false>, (kConsumerWarps + 1) * 32, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<true, false, false, false>, (kConsumerWarps + 1) * 32, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -737,13 +753,17 @@ int move_kernel_chains_per_tile(int P) { return kConsumerWarps * (32 / P); }
 cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s) {
   const int threads = (kConsumerWarps + 1) * 32;
   using Kernel = void (*)(MoveArgs, StepRef);
-  // [smart][wall][from_counts]
-  static const Kernel table[2][2][2] = {
-      {{k_move<false, false, false>, k_move<true, false, false>},
-       {k_move<false, false, true>, k_move<true, false, true>}},
-      {{k_move<false, true, false>, k_move<true, true, false>},
-       {k_move<false, true, true>, k_move<true, true, true>}}};
-  const Kernel k = table[a.smart ? 1 : 0][a.wall_z ? 1 : 0][from_counts ? 1 : 0];
+  // [conv][smart][wall][from_counts]
+  static const Kernel table[2][2][2][2] = {
+      {{{k_move<false, false, false, false>, k_move<true, false, false, false>},
+        {k_move<false, false, true, false>, k_move<true, false, true, false>}},
+       {{k_move<false, true, false, false>, k_move<true, true, false, false>},
+        {k_move<false, true, true, false>, k_move<true, true, true, false>}}},
+      {{{k_move<false, false, false, true>, k_move<true, false, false, true>},
+        {k_move<false, false, true, true>, k_move<true, false, true, true>}},
+       {{k_move<false, true, false, true>, k_move<true, true, false, true>},
+        {k_move<false, true, true, true>, k_move<true, true, true, true>}}}};
+  const Kernel k = table[a.conv ? 1 : 0][a.smart ? 1 : 0][a.wall_z ? 1 : 0][from_counts ? 1 : 0];
   k<<<grid, threads, 0, s>>>(a, r);
   return cudaGetLastError();
 }

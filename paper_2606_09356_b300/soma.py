@@ -45,7 +45,8 @@ EXPORTS = (
     "soma_get_state64", "soma_set_state64", "soma_observables", "soma_get_accepted", "soma_copy_accepted",
     "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
     "soma_philox4x32", "soma_structure_factor_noalloc", "soma_selfcheck_timeout",
-    "soma_normal_deviates",
+    "soma_normal_deviates", "soma_set_conversion", "soma_get_conversions", "soma_get_chain_types",
+    "soma_set_chain_types",
 )
 
 
@@ -141,6 +142,10 @@ def load_library(path=None):
     L.soma_autotune.argtypes = [vp]
     L.soma_philox4x32.argtypes = [vp, vp, vp, sz]
     L.soma_structure_factor_noalloc.argtypes = [vp, i64, ctypes.c_int32, ctypes.c_int32, vp, i32, vp, vp, vp]
+    L.soma_set_conversion.argtypes = [vp, i32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, vp]
+    L.soma_get_conversions.argtypes = [vp, i32, vp]
+    L.soma_get_chain_types.argtypes = [vp, i32, vp, sz]
+    L.soma_set_chain_types.argtypes = [vp, i32, vp, sz]
     for name in EXPORTS:
         if name not in ("soma_destroy", "soma_strerror"):
             getattr(L, name).restype = ctypes.c_int
@@ -352,6 +357,28 @@ class Handle:
         _check(self.lib.soma_freeze_fields(self.h, sys, _ptr(w), w.size, SOMA_HOST), "soma_freeze_fields")
 
     # -- state -----------------------------------------------------------
+    def set_conversion(self, n_A_alt, zone_lo=0.0, zone_hi=0.0, p=(0.0, 0.0, 0.0, 0.0), sys=0):
+        """Boundary-zone conversion: converted molecules have n_A_alt A beads;
+        zone widths in z; p = per-step probabilities (bottom 0->1, bottom
+        1->0, top 0->1, top 1->0).  n_A_alt < 0 switches it off."""
+        pv = np.ascontiguousarray(p, np.float64)
+        _check(self.lib.soma_set_conversion(self.h, sys, int(n_A_alt), float(zone_lo), float(zone_hi), _ptr(pv)),
+               "soma_set_conversion")
+
+    def conversions(self, sys=0):
+        out = np.zeros(4, np.uint64)
+        _check(self.lib.soma_get_conversions(self.h, sys, _ptr(out)), "soma_get_conversions")
+        return out
+
+    def chain_types(self, sys=0):
+        out = np.zeros(self.systems[sys].n_poly, np.uint8)
+        _check(self.lib.soma_get_chain_types(self.h, sys, _ptr(out), out.size), "soma_get_chain_types")
+        return out
+
+    def set_chain_types(self, types, sys=0):
+        t = np.ascontiguousarray(types, np.uint8)
+        _check(self.lib.soma_set_chain_types(self.h, sys, _ptr(t), t.size), "soma_set_chain_types")
+
     def set_umbrella(self, phi_target, lambdaN, sys=0):
         """Restraint toward target volume fractions [2, n_c]; None or 0 turns it off."""
         if phi_target is None or lambdaN == 0:

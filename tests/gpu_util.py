@@ -38,7 +38,7 @@ def band_for(system, k_b):
     return max(1e-5, 4.0 * k_b * 1.0 * float(ulp))
 
 
-def compare_step(h, sys=0, band=None, n_threads=NTHREADS, check_counts=True, w=None):
+def compare_step(h, sys=0, band=None, n_threads=NTHREADS, check_counts=True, w=None, orc=None, fields=None):
     """Run one GPU step and one oracle step from the same state and compare.
 
     Returns a dict of statistics.  Raises AssertionError on a mismatch: an
@@ -47,23 +47,36 @@ def compare_step(h, sys=0, band=None, n_threads=NTHREADS, check_counts=True, w=N
     (beads next to such a bead in the chain are set aside too), a position
     further than 1e-5 L from the oracle's, or counts that differ from the
     oracle's binning of the GPU's own positions.  ``w`` overrides the fields
-    the oracle moves against (default: the fields of the current counts)."""
+    the oracle moves against (default: the fields of the current counts, or
+    ``fields(orc, counts)``).  ``orc`` is the oracle to use; with its
+    boundary-zone conversion on, the GPU's molecule types are imported
+    before the step, the oracle converts before it moves, and the types and
+    conversion counts after the step must agree bit for bit."""
     system = h.systems[sys]
-    orc = oracle_for(system)
+    orc = oracle_for(system) if orc is None else orc
+    conv = orc.types is not None
     k_b, _, _ = orc.params()
     band = band_for(system, k_b) if band is None else band
     X0, step = unwrapped(h, sys)
+    if conv:
+        orc.set_types(h.chain_types(sys))
     counts0 = orc.density(X0)
     if check_counts:
         assert np.array_equal(h.get_density(sys), counts0), "counts differ before the step"
     if w is None:
-        w = orc.fields(counts0)
+        w = orc.fields(counts0) if fields is None else fields(orc, counts0)
+    if conv:
+        conv0 = h.conversions(sys).astype(np.int64)
+        c4 = orc.convert(X0, step)
     Xo = X0.copy()
     n_acc, acc, margin, face = orc.mc_step(Xo, w, step, n_threads=n_threads)
     a0 = h.accepted(sys)
     h.mc_steps(1)
     X1, step1 = unwrapped(h, sys)
     assert step1 == step + 1
+    if conv:
+        assert np.array_equal(h.chain_types(sys), orc.types), "molecule types differ after the conversions"
+        assert np.array_equal(h.conversions(sys).astype(np.int64) - conv0, c4), "conversion counts differ"
     moved = np.any(X1 != X0, axis=1)
     face_tol = 8.0 * float(np.spacing(np.float32(max(system.box))))
     suspect = (np.abs(margin) < band) | (face < face_tol)
