@@ -446,7 +446,7 @@ def run_gpu(args):
 
     # the bond-force-biased (smart) move on the same workload, timed like the
     # headline (L2 flushed between steps, CUDA events around each step)
-    smart = umbrella = None
+    smart = umbrella = zones = None
     if not args.no_smart:
         kw = rank_system_kwargs(args.workload, rank)
         smart = bench_variant(soma, torch, args.workload, kw, local, sptr, stream, flush, args.steps, args.warmup,
@@ -456,6 +456,12 @@ def run_gpu(args):
                                  args.warmup, hbm_peak, n_b, n_c, umbrella=50.0,
                                  note="umbrella restraint (lambdaN = 50) toward a lamellar target: field "
                                       "array from the counts, then the move kernel, per step; L2 flushed")
+        zones = bench_variant(soma, torch, args.workload, kw, local, sptr, stream, flush, args.steps,
+                              args.warmup, hbm_peak, n_b, n_c, wall_z=1,
+                              conversion=(kw["n_A"] // 2, 2.0, 2.0, (0.05, 0.02, 0.03, 0.04)),
+                              note="walls in z and boundary-zone conversion (zones 2 R_e wide, per-step "
+                                   "rates 0.02-0.05): conversion kernel, then the move kernel on molecule "
+                                   "types, per step; L2 flushed")
 
     # batched replicas vs sequential plain runs of the same 64 systems
     batched = None
@@ -475,6 +481,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(), "steady_state": steady, "energy": energy, "smart_moves": smart, "umbrella": umbrella,
+            "boundary_zones": zones,
             "batched": batched,
             "wall_s_timed": wall,
         }
@@ -510,12 +517,15 @@ def measure_energy(soma, torch, c, rank, local, sptr, stream, n_b, seconds=2.0):
 
 
 def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps, warmup, hbm_peak, n_b, n_c,
-                  move=0, umbrella=0.0, note=""):
-    """The workload with another trial move or with the umbrella restraint on:
-    moves/s over flushed steps and the move kernel's fraction of the HBM
-    roofline (same algorithmic bytes per step as the headline)."""
-    h = soma.Handle(soma.System(**{**kw, "move": move}), device=device, kernel_timing=1, graph_steps=0,
-                    autotune=1)
+                  move=0, umbrella=0.0, wall_z=0, conversion=None, note=""):
+    """The workload with another trial move, the umbrella restraint, or walls
+    and boundary-zone conversion: moves/s over flushed steps and the move
+    kernel's fraction of the HBM roofline (same algorithmic bytes per step as
+    the headline)."""
+    h = soma.Handle(soma.System(**{**kw, "move": move, "wall_z": wall_z}), device=device, kernel_timing=1,
+                    graph_steps=0, autotune=1)
+    if conversion:
+        h.set_conversion(*conversion)
     if umbrella:
         import numpy as np
         nx = kw["grid"][0]
@@ -540,6 +550,7 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
     total_ms = sum(x.elapsed_time(y) for x, y in ev)
     kt = h.kernel_times(reset=True)
     acc = (h.accepted() - a0) / (steps * n_b)
+    conv_n = int(h.conversions().sum()) if conversion else 0
     h.close()
     mv_ms, mv_n = kt["move"]
     fd_ms, fd_n = kt["field"]
@@ -550,6 +561,8 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
            "note": note}
     if fd_n:
         out["field_ms"] = fd_ms / fd_n
+    if conversion:
+        out["conversions_per_step"] = float(conv_n) / (steps + warmup)
     if move:
         out["traffic"] = _profiled_traffic(workload, "_smart")
     return out

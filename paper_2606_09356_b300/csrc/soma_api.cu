@@ -263,6 +263,10 @@ void build_args(soma_handle* h) {
     a.wall_z = S.wall_z;
     a.conv = S.conv;
     a.n_A_alt = S.n_A_alt;
+    a.zone_lo = S.zone_lo;
+    a.zone_hi = S.zone_hi;
+    std::memcpy(a.thr, S.thr, sizeof(a.thr));
+    a.conv_count = S.conv_count;
     {
       const double s2 = (double)S.A * (double)S.A / 3.0;
       a.sig = (float)std::sqrt(s2);
@@ -376,14 +380,6 @@ int enqueue_umbrella_fields(soma_handle* h, cudaStream_t s, int sys, bool graph,
   return SOMA_OK;
 }
 
-// Boundary-zone conversions that open step i of system sys (conversion on).
-int enqueue_convert(soma_handle* h, cudaStream_t s, int sys, bool graph, long long t0, int i) {
-  const SysDev& S = h->host_sys[sys];
-  if (!S.conv) return SOMA_OK;
-  CK(launch_convert(h->d_sys, sys, S.n_poly, step_ref(h, sys, graph, t0, i), h->sm_count, s));
-  return SOMA_OK;
-}
-
 // n steps of every system on stream `s`.  One system: one move kernel per
 // step (fields from the previous counts, fused histogram, clearing of the
 // next count buffer).  Several systems: one k_move_batch launch per step and
@@ -394,8 +390,6 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
   const bool batched = h->n_sys > 1;
   int rc;
   for (int i = 0; i < n; ++i) {
-    for (int sys = 0; sys < h->n_sys; ++sys)
-      if ((rc = enqueue_convert(h, s, sys, graph, t0, i))) return rc;
     if (batched) {
       for (size_t g = 0; g < h->batches.size(); ++g) {
         const BatchArgs* b = &h->batches[g];

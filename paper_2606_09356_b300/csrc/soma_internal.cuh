@@ -78,7 +78,7 @@ struct MoveArgs {
   float* y;
   float* z;
   int16_t* img;
-  const uint32_t* chain_id;
+  uint32_t* chain_id;        // read by the bulk copies; a converted chain's word is rewritten
   uint32_t* counts;          // [3 buffers][n_c][2 types]
   const float* w;            // [2 types][n_c], read only when fields are held
   float inv_rho, chiN_N, kappaN_N;
@@ -91,6 +91,9 @@ struct MoveArgs {
   int32_t wall_z;            // 1: hard walls at z = 0 and z = L_z (host-side flag; kernels are templated)
   int32_t conv;              // 1: molecule types in chain_id's top bit (single launches: templated)
   int32_t n_A_alt;           // A beads of a converted molecule
+  float zone_lo, zone_hi;    // conversion zones: bottom z < zone_lo, top z >= zone_hi
+  unsigned long long thr[4]; // convert iff word < thr: {bottom 0->1, bottom 1->0, top 0->1, top 1->0}
+  unsigned long long* conv_count;  // [4] conversions since the rates were last set
 };
 
 // Up to kMaxBatch systems stepped by one persistent launch: their constants

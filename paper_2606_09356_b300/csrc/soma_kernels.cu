@@ -412,35 +412,6 @@ __global__ void k_scatter_state(const SysDev* __restrict__ systems, int sys, con
   }
 }
 
-// ---------------------------------------------------------------------------
-// Boundary zones (Sec. 3.2): the conversions that open step t.  A chain whose
-// bead 0 lies in the bottom zone (z < zone_lo) or the top zone (z >= zone_hi)
-// changes its molecule type iff word 0 of Philox counter (kConvWord, logical
-// id, t, system) is below the threshold of its zone and current type.  One
-// thread per chain; the four conversion counts are summed per CTA.
-// ---------------------------------------------------------------------------
-__global__ void k_convert(const SysDev* __restrict__ systems, int sys, StepRef r) {
-  __shared__ SysDev S;
-  __shared__ unsigned long long n_conv[4];
-  if (threadIdx.x < 4) n_conv[threadIdx.x] = 0;
-  load_sys(&S, systems + sys);  // synchronises
-  const uint32_t t = (uint32_t)r.get();
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
-    const float z = S.z[c * S.N];
-    const int zone = z < S.zone_lo ? 0 : (z >= S.zone_hi ? 1 : -1);
-    if (zone < 0) continue;
-    const uint32_t word = S.chain_id[c];
-    const int m = (word & kTypeBit) ? 1 : 0;
-    const uint4 w = philox10(make_uint4(kConvWord, word & kIdMask, t, (uint32_t)S.sys_index), S.rk);
-    if ((unsigned long long)w.x < S.thr[2 * zone + m]) {
-      S.chain_id[c] = word ^ kTypeBit;
-      atomicAdd(&n_conv[2 * zone + m], 1ull);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 4 && n_conv[threadIdx.x]) atomicAdd(S.conv_count + threadIdx.x, n_conv[threadIdx.x]);
-}
-
 // Molecule types in logical chain order <-> the chain-id words' top bit.
 __global__ void k_get_types(const SysDev* __restrict__ systems, int sys, uint8_t* __restrict__ out) {
   __shared__ SysDev S;
@@ -741,12 +712,6 @@ cudaError_t launch_init(const SysDev* systems, int sys, int64_t n_poly, cudaStre
   const int threads = 128;
   const int64_t blocks = (n_poly + threads - 1) / threads;
   k_init<<<(unsigned)blocks, threads, 0, s>>>(systems, sys);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_convert(const SysDev* systems, int sys, int64_t n_poly, StepRef r, int sm_count, cudaStream_t s) {
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_poly + 255) / 256, (int64_t)sm_count * 8));
-  k_convert<<<grid, 256, 0, s>>>(systems, sys, r);
   return cudaGetLastError();
 }
 

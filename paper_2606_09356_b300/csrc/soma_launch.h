@@ -62,7 +62,6 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* ou
 // FP64-position form (soma_f64.cu).
 cudaError_t launch_move64(const SysDev* systems, int sys, StepRef r, int sm_count, cudaStream_t s);
 cudaError_t launch_init64(const SysDev* systems, int sys, int64_t n_poly, cudaStream_t s);
-cudaError_t launch_convert(const SysDev* systems, int sys, int64_t n_poly, StepRef r, int sm_count, cudaStream_t s);
 cudaError_t launch_get_types(const SysDev* systems, int sys, uint8_t* out, int sm_count, cudaStream_t s);
 cudaError_t launch_set_types(const SysDev* systems, int sys, const uint8_t* types, int sm_count, cudaStream_t s);
 cudaError_t launch_bin64(const SysDev* systems, int sys, long long t, int sm_count, cudaStream_t s);

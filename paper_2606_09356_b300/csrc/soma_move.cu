@@ -29,8 +29,10 @@
 // specialised on the proposal (uniform, or bond-force-biased: smart_pair)
 // and on the z boundary (periodic, or hard walls: a proposal leaving the
 // slab is rejected, z bonds are plain differences); k_move also on molecule
-// types (boundary-zone conversion: a bead's type follows the A block of its
-// chain's type, carried in the chain-id word's top bit).
+// types (boundary-zone conversion: each step opens with the conversions of
+// the chains whose bead 0 lies in a zone, decided by the chain's bead-0
+// lane; a bead's type follows the A block of its chain's type, carried in
+// the chain-id word's top bit).
 // Every mbarrier wait is bounded: on expiry the kernel sets kErrTimeout in the
 // device error word, drains its own copies (again bounded) and returns.
 #include <cuda_runtime.h>
@@ -540,8 +542,34 @@ __device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, co
   uint32_t cid = cid_word;
   int n_A = a.n_A;
   if (kConv) {
-    cid = cid_word & kIdMask;
-    if (cid_word & kTypeBit) n_A = a.n_A_alt;
+    // boundary zones (Sec. 3.2): the step opens with the conversions.  The
+    // chain's bead-0 lane (k = 0) holds bead 0's stored z: in a zone, it
+    // draws word 0 of counter (kConvWord, id, t, system) and flips the type
+    // if the word is below the zone's threshold for the current type; the
+    // chain's other lanes take the new word by a width-P shuffle.
+    uint32_t word = cid_word;
+    const bool in_lo = ze < a.zone_lo, in_hi = ze >= a.zone_hi;
+    const bool cand = he && k == 0 && (in_lo || in_hi);
+    if (__any_sync(0xffffffffu, cand)) {
+      int slot_conv = -1;  // 0..3 when this lane's chain converts
+      if (cand) {
+        const int zone = in_lo ? 0 : 1, m = (word & kTypeBit) ? 1 : 0;
+        const uint4 w = philox10(make_uint4(kConvWord, word & kIdMask, (uint32_t)tl, (uint32_t)a.sys_index), a.rk);
+        if ((unsigned long long)w.x < a.thr[2 * zone + m]) {
+          word ^= kTypeBit;
+          a.chain_id[c0 + chain_in_tile] = word;
+          slot_conv = 2 * zone + m;
+        }
+      }
+      word = __shfl_sync(0xffffffffu, word, 0, P);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int n_q = __popc(__ballot_sync(0xffffffffu, slot_conv == q));
+        if (lane == 0 && n_q) atomicAdd(a.conv_count + q, (unsigned long long)n_q);
+      }
+    }
+    cid = word & kIdMask;
+    if (word & kTypeBit) n_A = a.n_A_alt;
   }
   const int te = e < n_A ? 0 : 1, to = o < n_A ? 0 : 1;
 
@@ -767,6 +795,8 @@ cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r
   k<<<grid, threads, 0, s>>>(a, r);
   return cudaGetLastError();
 }
+
+static_assert(sizeof(BatchArgs) + sizeof(StepRef) <= 32764, "batch parameters exceed the kernel parameter space");
 
 cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStream_t s) {
   const bool smart = p.n_sys > 0 && p.sys[0].smart, wall = p.n_sys > 0 && p.sys[0].wall_z;
