@@ -18,8 +18,9 @@ Beside the headline the line carries: the move kernel's roofline fraction
 (with the DRAM traffic of the committed ncu summary when it was taken from
 the current kernel source), the CPU oracle on a bounded sample, the end to
 end rate through the C ABI with host buffers, CUDA-graph steady state,
-energy per step from NVML, the smart-move and umbrella variants of the
-same workload, and the 64-system batch against its systems run one by one.
+energy per step from NVML, the smart-move, umbrella and walls with
+boundary-zone conversion variants of the same workload, and the 64-system
+batch against its systems run one by one.
 
 ``--impl reference`` times the plain FP64 CPU oracle on the same workload
 shape (a bounded sample of it) on the host cores instead.
