@@ -1,7 +1,8 @@
 """Randomised shapes against the oracle (needs a GPU): chain lengths across
 the register and generic paths, odd and even N, anisotropic boxes, dyadic
-and non-dyadic grids, both move kinds, walls, the umbrella, held fields;
-and handles mixing such systems against the same systems run alone."""
+and non-dyadic grids, both move kinds, walls, the umbrella, held fields,
+boundary-zone conversion; and handles mixing such systems against the same
+systems run alone."""
 import numpy as np
 import pytest
 
@@ -38,6 +39,17 @@ def random_system(rng, i):
                        move=move, wall_z=int(rng.integers(0, 2)))
 
 
+def random_conversion(rng, s):
+    """Boundary-zone conversion for half of the register-path systems: a
+    random converted A block, zone widths and per-step rates (or None)."""
+    if s.N > 64 or rng.integers(0, 2) == 0:
+        return None
+    Lz = s.box[2]
+    lo = float(rng.uniform(0, 0.5 * Lz))
+    hi = float(rng.uniform(0, 0.5 * Lz))
+    return (int(rng.integers(0, s.N + 1)), lo, hi, tuple(float(v) for v in rng.uniform(0, 1, 4)))
+
+
 @pytest.mark.parametrize("seed", range(80))
 def test_random_shape_steps_match_oracle(seed):
     rng = np.random.default_rng(1000 + seed)
@@ -53,8 +65,14 @@ def test_random_shape_steps_match_oracle(seed):
         elif mode == 2:  # held fields
             w = rng.normal(0, 0.5, size=(2, s.n_cells)).astype(np.float32)
             h.freeze_fields(w)
+        conv = random_conversion(rng, s)
+        if conv:
+            orc.set_conversion(*conv)
+            h.set_conversion(*conv)
         for _ in range(3):
             X0, _ = G.unwrapped(h)
+            if conv:
+                orc.set_types(h.chain_types())
             counts = orc.density(X0)
             if mode == 1:
                 w64 = orc.fields_umbrella(counts, tg.astype(np.float64), lam)
@@ -62,7 +80,7 @@ def test_random_shape_steps_match_oracle(seed):
                 w64 = w.astype(np.float64)
             else:
                 w64 = orc.fields(counts)
-            st = G.compare_step(h, band=band, w=w64)
+            st = G.compare_step(h, band=band, w=w64, orc=orc)
             assert abs(st["acc_gpu"] - st["acc_orc"]) <= st["suspect"]
 
 
@@ -72,12 +90,19 @@ def test_random_mixed_handles_equal_solo_runs(seed):
     systems = [random_system(rng, i) for i in range(int(rng.integers(2, 7)))]
     steps = int(rng.integers(5, 30))
     opts = dict(graph_steps=int(rng.choice([0, 4])), sort_interval=int(rng.choice([0, 3])))
+    convs = [random_conversion(rng, s) for s in systems]
     with soma.Handle(systems, **opts) as hb:
+        for i, c in enumerate(convs):
+            if c:
+                hb.set_conversion(*c, sys=i)
         hb.mc_steps(steps)
-        batched = [(hb.get_state(i)[0], hb.get_density(i), hb.accepted(i)) for i in range(len(systems))]
+        batched = [(hb.get_state(i)[0], hb.get_density(i), hb.accepted(i), hb.chain_types(i))
+                   for i in range(len(systems))]
     for i, s in enumerate(systems):
         with soma.Handle(s, graph_steps=0, sort_interval=0) as h:
+            if convs[i]:
+                h.set_conversion(*convs[i])
             h.mc_steps(steps)
-            solo = (h.get_state()[0], h.get_density(), h.accepted())
+            solo = (h.get_state()[0], h.get_density(), h.accepted(), h.chain_types())
         for x, y in zip(batched[i], solo):
             assert np.array_equal(x, y)

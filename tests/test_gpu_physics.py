@@ -195,3 +195,50 @@ def test_long_run_slab_statistics_agree_with_oracle():
         assert abs(g[:, k].mean() - r[:, k].mean()) <= 3 * se + 1e-12, (name, g[:, k].mean(), r[:, k].mean(), se)
     # the walls deplete the layers next to them
     assert g[:, 2].mean() < 0.95
+
+
+def test_long_run_conversion_statistics_agree_with_oracle():
+    """Between walls with boundary-zone conversion (config 0 shape, zones
+    1 R_e wide, converted molecules A4B28): the time-averaged fraction of
+    converted chains, the A volume fraction of the two wall layers and the
+    acceptance from the GPU and the oracle agree within 3 sigma over 8 seeds
+    (chains diffuse in and out of the zones, so none of these has a closed
+    form)."""
+    kw = {**workloads.system_kwargs("config0"), "wall_z": 1}
+    conv = (4, 1.0, 1.0, (0.05, 0.02, 0.03, 0.04))
+    burn, steps, every = 300, 1200, 100
+
+    def stats(seed, gpu):
+        s = soma.System(**{**kw, "seed": seed})
+        o = G.oracle_for(s)
+        o.set_conversion(*conv)
+        frac, prof, acc = [], [], 0
+        if gpu:
+            h = soma.Handle(s)
+            h.set_conversion(*conv)
+            h.mc_steps(burn)
+            a0 = h.accepted()
+            for _ in range(steps // every):
+                h.mc_steps(every)
+                frac.append(h.chain_types().mean())
+                prof.append(h.density_profile(2)[0])
+            acc = (h.accepted() - a0) / (steps * s.n_beads)
+            h.close()
+        else:
+            X = o.init()
+            o.run(X, 0, burn, n_threads=G.NTHREADS)
+            for k in range(steps // every):
+                r = o.run(X, burn + k * every, every, n_threads=G.NTHREADS)
+                acc += r["accepted"]
+                frac.append(o.types.mean())
+                prof.append(o.density_profile(o.density(X), 2)[0])
+            acc /= steps * o.n_b
+        prof = np.mean(prof, axis=0)
+        return np.mean(frac), 0.5 * (prof[0] + prof[-1]), acc
+
+    g = np.array([stats(sd, True) for sd in range(1, 9)])
+    r = np.array([stats(sd, False) for sd in range(1, 9)])
+    for k, name in ((0, "converted fraction"), (1, "wall-layer A fraction"), (2, "acc")):
+        se = np.sqrt(g[:, k].var(ddof=1) / 8 + r[:, k].var(ddof=1) / 8)
+        assert abs(g[:, k].mean() - r[:, k].mean()) <= 3 * se + 1e-12, (name, g[:, k].mean(), r[:, k].mean(), se)
+    assert 0.05 < g[:, 0].mean() < 0.6  # conversions happen and are undone
