@@ -130,3 +130,11 @@ def test_null_arguments(lib):
     assert lib.soma_observables(None, 0, None) == soma.SOMA_EINVAL
     lib.soma_destroy(None)
     assert lib.soma_philox4x32(None, None, None, 0) == soma.SOMA_OK
+    # every handle call rejects a NULL handle before touching the device
+    assert lib.soma_set_conversion(None, 0, 1, 0.0, 0.0, None) == soma.SOMA_EINVAL
+    assert lib.soma_get_conversions(None, 0, None) == soma.SOMA_EINVAL
+    assert lib.soma_get_chain_types(None, 0, None, 0) == soma.SOMA_EINVAL
+    assert lib.soma_set_chain_types(None, 0, None, 0) == soma.SOMA_EINVAL
+    assert lib.soma_copy_accepted(None, 0, None, None) == soma.SOMA_EINVAL
+    assert lib.soma_set_umbrella(None, 0, None, 0, 0.0, 0) == soma.SOMA_EINVAL
+    assert lib.soma_place(None, 0, None, 0, 0) == soma.SOMA_EINVAL
