@@ -61,6 +61,8 @@ struct __align__(128) MoveStage {
   float y[kTileBeads];
   float z[kTileBeads];
   uint32_t cid[kTileChains];
+  uint32_t sys;  // batched launches: the tile's system, written by the producer
+  uint32_t pad[3];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -711,6 +713,7 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
         const int s = it % kStages;
         if (it >= kStages && !mbar_wait(&empty[s], (uint32_t)((it / kStages) - 1) & 1u, err)) break;
         const int sys = batch_system(p, tile);
+        stage[s].sys = (uint32_t)sys;  // ordered before the stage's arrive (release semantics)
         produce_tile(p.sys[sys], tile - p.tile_start[sys], stage[s], &full[s]);
       }
       drain(full, it, err);
@@ -723,7 +726,7 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
     const int s = it % kStages;
     if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, err)) break;
-    const int sys = batch_system(p, tile);
+    const int sys = (int)lds1(&stage[s].sys);  // the producer's search, not one per thread
     const MoveArgs& a = p.sys[sys];
     const uint2* prev = reinterpret_cast<const uint2*>(count_buffer(a.counts, a.n_c, tl - 1));
     uint32_t* cur = count_buffer(a.counts, a.n_c, tl);
