@@ -566,6 +566,8 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
         out["conversions_per_step"] = float(conv_n) / (steps + warmup)
     if move:
         out["traffic"] = _profiled_traffic(workload, "_smart")
+    elif conversion:
+        out["traffic"] = _profiled_traffic(workload, "_zones")
     return out
 
 
