@@ -161,3 +161,63 @@ def test_structure_factor_matches_oracle():
         R = orc.structure_factor(X, m)
         # FP32 phases of wrapped positions: |dphase| <= ~2e-6 rad per bead
         assert np.allclose(S, R, rtol=2e-4, atol=2e-4)
+
+
+@pytest.mark.parametrize("variant", ["uniform", "smart", "walls"])
+def test_steps_from_the_oracle_state_without_resync(variant):
+    """The oracle's own initial configuration (its FP32 image: wrapped
+    coordinate plus image count, the numbers the GPU stores) goes into the
+    GPU by soma_set_state; then both sides step four times on their own,
+    nothing passing from the GPU to the oracle.  Every decision and position
+    agrees except for beads set aside for cause, with their chains: a
+    margin inside the band or a position near a cell face, at any step so
+    far, or an old or new cell whose counts differ between the two sides."""
+    kw = dict(workloads.system_kwargs("config0"))
+    if variant == "smart":
+        kw["move"] = soma.SOMA_MOVE_SMART
+    if variant == "walls":
+        kw["wall_z"] = 1
+    s = soma.System(**kw)
+    orc = G.oracle_for(s)
+    k_b, A, _ = orc.params()
+    band = max(G.band_for(s, k_b), 1e-4 if variant == "smart" else 0.0)
+    # after the first step the GPU keeps FP32-rounded wrapped coordinates and
+    # the oracle exact FP64 ones: every step adds up to ulp(L) to their
+    # difference, and a bead's dE moves by at most 2 k_b |d| per unit of it
+    # for each of its two bonds (|d| <= 2 sqrt(3) A at the two ends)
+    ulp = float(np.spacing(np.float32(max(s.box))))
+    L = np.array(s.box)
+    X = orc.init()
+    img = np.floor(X / L)
+    xw = (X - img * L).astype(np.float32)
+    top = xw >= L.astype(np.float32)  # rounded up to L: the last cell's image is the next one
+    xw[top] = 0.0
+    img[top] += 1.0
+    X = xw.astype(np.float64) + img * L  # the oracle continues from exactly these numbers
+    N = s.N
+    face_tol = 8.0 * float(np.spacing(np.float32(max(s.box))))
+    excluded = np.zeros(s.n_poly, bool)
+    with soma.Handle(s, graph_steps=0) as h:
+        h.set_state(xw, img.astype(np.int16), 0)
+        assert np.array_equal(h.get_density(), orc.density(X))
+        for t in range(4):
+            counts = orc.density(X)
+            diff_cells = np.nonzero((h.get_density() != counts).any(axis=0))[0]
+            w = orc.fields(counts)
+            X0 = X.copy()
+            cells0 = np.array([orc.cell_index(r) for r in X0]) if diff_cells.size else None
+            _, acc, margin, face = orc.mc_step(X, w, t, n_threads=G.NTHREADS)
+            Xg0, _ = G.unwrapped(h)  # the GPU's own positions before its step
+            h.mc_steps(1)
+            Xg, _ = G.unwrapped(h)
+            band_t = band + 4.0 * k_b * 2.0 * np.sqrt(3.0) * A * ulp * t
+            sus = (np.abs(margin) < band_t) | (face < face_tol)
+            if diff_cells.size:
+                cells1 = np.array([orc.cell_index(r) for r in X])
+                sus |= np.isin(cells0, diff_cells) | np.isin(cells1, diff_cells)
+            excluded |= sus.reshape(-1, N).any(axis=1)
+            ok = np.repeat(~excluded, N)
+            assert ok.mean() > 0.9  # chains set aside accumulate over the steps
+            moved_g = np.any(Xg != Xg0, axis=1)
+            assert not (ok & (moved_g != acc.astype(bool))).any(), t
+            assert (np.abs(Xg - X)[ok] / L).max() <= 1e-5, t
