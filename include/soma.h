@@ -14,6 +14,12 @@
  *       w_A = [chiN phi_B + kappaN (phi_A + phi_B - 1)] / N, w_B likewise
  *       with phi_A in the chi term.
  *
+ * Per system, instead of (a): bond-force-biased proposals (desc.move =
+ * SOMA_MOVE_SMART); hard walls in z (desc.wall_z); molecule types with
+ * conversion in boundary zones (soma_set_conversion); a restraint toward
+ * target fields (soma_set_umbrella); fields given or held by the caller
+ * (soma_set_density, soma_freeze_fields).
+ *
  * Units: R_e = 1, kT = 1.  Random numbers: Philox4x32-10 (Salmon et al.,
  * SC'11) with counter (bead, logical chain, step, system_id) and key = seed,
  * so a trajectory does not depend on chain storage order or launch shape.
@@ -290,7 +296,8 @@ int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int wh
 
 /* Checkpoint: positions [n_beads][3] FP32 wrapped into [0, L), images
  * [n_beads][3] int16, and the step counter, in logical chain order (host or
- * device buffers per `where`; any of pos, img, step may be NULL).
+ * device buffers per `where`; any of pos, img, step may be NULL).  Molecule
+ * types, when conversion is on, are saved separately (soma_get_chain_types).
  * SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises. */
 int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* step, int where);
 /* Restore: positions must lie in [0, L) per axis (else SOMA_EINVAL and the
