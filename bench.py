@@ -1,6 +1,6 @@
 """Throughput benchmark of the SCMF Monte Carlo step (bead moves per second).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload config1]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload melt_131072x32]
                     [--impl reference] [--no-batched] [--no-e2e] [--no-cpu]
                     [--no-steady] [--no-smart] [--no-energy]
 
@@ -614,7 +614,7 @@ def main():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--workload", default="config1")
+    p.add_argument("--workload", default="melt_131072x32")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--batched-steps", type=int, default=20)

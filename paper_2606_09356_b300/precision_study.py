@@ -2,7 +2,7 @@
 
     python -m paper_2606_09356_b300.precision_study --steps 100000 --seeds 8
 
-For each seed the config1 system (131,072 AB diblocks, N = 32, box 16^3,
+For each seed the melt_131072x32 system (131,072 AB diblocks, N = 32, box 16^3,
 grid 128^3, chiN 30, kappaN 50) runs in both forms from its own GPU initial
 configuration.  After a burn-in, <R_e^2>, <R_g^2>, the acceptance rate, the
 non-bonded energy per chain and the composition structure factor at the
@@ -30,7 +30,7 @@ def shells(max_m2=4):
 
 
 def run(precision, seed, steps, burn, every, m, m2):
-    s = soma.System(**{**workloads.system_kwargs("config1"), "seed": seed})
+    s = soma.System(**{**workloads.system_kwargs("melt_131072x32"), "seed": seed})
     with soma.Handle(s, precision=precision) as h:
         h.mc_steps(burn)
         h.sync()
@@ -59,7 +59,7 @@ def main():
     _build.build()
     m, m2 = shells()
     names = ["acc", "Re2", "Rg2", "Enb_per_chain"] + [f"S(|m|^2={k})" for k in sorted(set(m2.tolist()))]
-    out = {"workload": "config1", "steps": a.steps, "burn": a.burn, "every": a.every, "seeds": a.seeds,
+    out = {"workload": "melt_131072x32", "steps": a.steps, "burn": a.burn, "every": a.every, "seeds": a.seeds,
            "observables": {}}
     res = {0: [], 1: []}
     secs = {0: 0.0, 1: 0.0}

@@ -1,7 +1,7 @@
 """Run a workload for a fixed number of Monte Carlo steps (a driver for
 profilers such as ncu; prints nothing but a one-line summary).
 
-    python -m paper_2606_09356_b300.profile_run --workload config1 --steps 20 [--move smart]
+    python -m paper_2606_09356_b300.profile_run --workload melt_131072x32 --steps 20 [--move smart]
         [--walls] [--conversion]
 
 --conversion switches on boundary-zone conversion (zones 2 R_e wide at the
@@ -17,7 +17,7 @@ from . import soma, workloads
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--workload", default="config1")
+    p.add_argument("--workload", default="melt_131072x32")
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--graph-steps", type=int, default=0)
     p.add_argument("--sort-interval", type=int, default=-1)

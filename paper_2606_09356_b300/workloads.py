@@ -5,11 +5,11 @@ The paper's own particle workload (a membrane-forming melt on a grid refined
 to R_e/10, Sec. 4) needs continuum-supplied fields and is not available; these
 AB diblock melts stand in for it at the same kind of SCMF densities.
 
-* ``config0``  512 chains x 32, f_A = 0.5, box 4^3, grid 16^3, chiN 20,
+* ``melt_512x32``  512 chains x 32, f_A = 0.5, box 4^3, grid 16^3, chiN 20,
   kappaN 50: the small case the oracle runs in full.
-* ``config1``  131,072 x 32 (4.19 M beads), box 16^3, grid 128^3, chiN 30:
+* ``melt_131072x32``  131,072 x 32 (4.19 M beads), box 16^3, grid 128^3, chiN 30:
   the single-GPU throughput workload.
-* ``config2``  1,048,576 x 64, f_A = 0.3 (n_A = 19), box 32^3, grid 256^3,
+* ``melt_1048576x64``  1,048,576 x 64, f_A = 0.3 (n_A = 19), box 32^3, grid 256^3,
   chiN 25 (67.1 M beads).
 * ``batch64``  64 independent systems of uneven size (``batch64.json``,
   written by ``make_batch64``): N in {16, 32, 64}, chains log-uniform in
@@ -24,19 +24,19 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 BATCH64_JSON = os.path.join(_HERE, "batch64.json")
 
-CONFIGS = {
-    "config0": dict(n_poly=512, N=32, n_A=16, box=(4.0, 4.0, 4.0), grid=(16, 16, 16), chiN=20.0, kappaN=50.0,
+WORKLOADS = {
+    "melt_512x32": dict(n_poly=512, N=32, n_A=16, box=(4.0, 4.0, 4.0), grid=(16, 16, 16), chiN=20.0, kappaN=50.0,
                     seed=1, steps=100),
-    "config1": dict(n_poly=131072, N=32, n_A=16, box=(16.0, 16.0, 16.0), grid=(128, 128, 128), chiN=30.0,
+    "melt_131072x32": dict(n_poly=131072, N=32, n_A=16, box=(16.0, 16.0, 16.0), grid=(128, 128, 128), chiN=30.0,
                     kappaN=50.0, seed=1, steps=1000),
-    "config2": dict(n_poly=1048576, N=64, n_A=19, box=(32.0, 32.0, 32.0), grid=(256, 256, 256), chiN=25.0,
+    "melt_1048576x64": dict(n_poly=1048576, N=64, n_A=19, box=(32.0, 32.0, 32.0), grid=(256, 256, 256), chiN=25.0,
                     kappaN=50.0, seed=1, steps=500),
 }
 
 
 def system_kwargs(name, **override):
     """Keyword arguments of ``soma.System`` / ``oracle.Oracle`` for a config."""
-    c = dict(CONFIGS[name])
+    c = dict(WORKLOADS[name])
     c.pop("steps")
     c.update(override)
     return c

@@ -14,7 +14,7 @@ def _lib():
 
 
 def test_set_state_rejects_positions_outside_the_box_and_keeps_state():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     with soma.Handle(s) as h:
         pos, img, step = h.get_state()
         bad = pos.copy()
@@ -29,7 +29,7 @@ def test_set_state_rejects_positions_outside_the_box_and_keeps_state():
 
 
 def test_argument_errors():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     with soma.Handle(s) as h:
         lib = h.lib
         buf = np.zeros(10, np.uint32)
@@ -41,7 +41,7 @@ def test_argument_errors():
 
 
 def test_set_density_drives_next_fields():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(s)
     rng = np.random.default_rng(3)
     phi = rng.uniform(0.0, 1.0, size=(2, s.n_cells)).astype(np.float32)
@@ -57,7 +57,7 @@ def test_set_density_drives_next_fields():
 
 
 def test_freeze_and_release_fields():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(s)
     w = np.full((2, s.n_cells), 0.25, np.float32)
     with soma.Handle(s) as h:
@@ -69,7 +69,7 @@ def test_freeze_and_release_fields():
 
 
 def test_info_and_kernel_timing():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     with soma.Handle(s, kernel_timing=1, sort_interval=4) as h:
         h.kernel_times(reset=True)
         info = h.info()
@@ -83,8 +83,8 @@ def test_info_and_kernel_timing():
 
 
 def test_many_handles_and_destroy():
-    s = soma.System(**workloads.system_kwargs("config0"))
-    hs = [soma.Handle(soma.System(**{**workloads.system_kwargs("config0"), "seed": k})) for k in range(4)]
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
+    hs = [soma.Handle(soma.System(**{**workloads.system_kwargs("melt_512x32"), "seed": k})) for k in range(4)]
     for h in hs:
         h.mc_steps(3)
     st = [h.get_state()[0] for h in hs]
@@ -95,7 +95,7 @@ def test_many_handles_and_destroy():
 
 def test_accepted_count_is_read_after_steps_on_a_caller_stream():
     import torch
-    s = soma.System(**workloads.system_kwargs("config1"))
+    s = soma.System(**workloads.system_kwargs("melt_131072x32"))
     st = torch.cuda.Stream()
     with soma.Handle(s, graph_steps=0) as h:
         h.mc_steps(1)
@@ -124,7 +124,7 @@ def _count_buffers(kind, n):
 @pytest.mark.parametrize("kind", ["pinned", "pinned_unaligned", "pageable"])
 def test_enqueued_accepted_counts_follow_each_step(kind):
     import torch
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     st = torch.cuda.Stream()
     dst, read = _count_buffers(kind, 6)
     with soma.Handle(s, graph_steps=0) as h:
@@ -143,7 +143,7 @@ def test_enqueued_accepted_counts_follow_each_step(kind):
 
 
 @pytest.mark.parametrize("kw", [
-    dict(workloads.system_kwargs("config0")),
+    dict(workloads.system_kwargs("melt_512x32")),
     dict(n_poly=300, N=24, n_A=9, box=(3.0, 3.3, 2.9), grid=(7, 11, 9), chiN=18.0, kappaN=45.0, wall_z=1),
 ])
 def test_density_profiles_and_vertical_correlation_match_oracle(kw):
@@ -162,7 +162,7 @@ def test_empty_and_zero_work_calls():
     """Zero steps change nothing (state, step, counts, accepted count);
     negative step counts are rejected with the state kept; empty S(q),
     Philox and normal-deviate requests return empty results."""
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     with soma.Handle(s, graph_steps=4) as h:
         h.mc_steps(3)
         before = h.get_state(), h.get_density(), h.accepted()

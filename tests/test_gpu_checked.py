@@ -21,12 +21,12 @@ sys.path.insert(0, ROOT)
 from paper_2606_09356_b300 import soma, workloads
 soma.load_library(LIB)
 shapes = [
-    dict(workloads.system_kwargs("config0")),
-    dict(workloads.system_kwargs("config0"), move=soma.SOMA_MOVE_SMART),
+    dict(workloads.system_kwargs("melt_512x32")),
+    dict(workloads.system_kwargs("melt_512x32"), move=soma.SOMA_MOVE_SMART),
     dict(n_poly=37, N=7, n_A=3, box=(4.0, 4.5, 5.0), grid=(16, 18, 20), chiN=15.0, kappaN=40.0, seed=7),
     dict(n_poly=40, N=80, n_A=30, box=(2.0, 2.0, 2.0), grid=(8, 8, 8), chiN=25.0, kappaN=50.0, seed=7),
     dict(n_poly=200, N=1, n_A=1, box=(2.0, 2.0, 2.0), grid=(4, 4, 4), chiN=5.0, kappaN=10.0, A=0.25),
-    dict(workloads.system_kwargs("config0"), move=soma.SOMA_MOVE_SMART, wall_z=1),
+    dict(workloads.system_kwargs("melt_512x32"), move=soma.SOMA_MOVE_SMART, wall_z=1),
 ]
 out = []
 for kw in shapes:

@@ -172,11 +172,11 @@ def test_conversion_arguments_are_checked():
         assert e.value.code == soma.SOMA_ENOTSUP
 
 
-def test_config1_between_walls_with_conversion_full_size():
-    """config1 with walls and zones 2 R_e wide: one step at full size in the
+def test_melt_131072x32_between_walls_with_conversion_full_size():
+    """melt_131072x32 with walls and zones 2 R_e wide: one step at full size in the
     bench's launch configuration; every chain's type and the whole grid's
     counts bit for bit, a 2048-chain sample of the moves against the oracle."""
-    s = soma.System(**dict(workloads.system_kwargs("config1"), wall_z=1))
+    s = soma.System(**dict(workloads.system_kwargs("melt_131072x32"), wall_z=1))
     orc = G.oracle_for(s)
     conv = (8, 2.0, 2.0, (0.05, 0.02, 0.03, 0.04))
     orc.set_conversion(*conv)

@@ -36,7 +36,7 @@ def _fields_bound(orc, counts, target, lam):
 
 
 def test_umbrella_fields_match_oracle():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(s)
     tg = _target(s)
     with soma.Handle(s) as h:
@@ -53,8 +53,8 @@ def test_umbrella_fields_match_oracle():
 
 
 @pytest.mark.parametrize("kw", [
-    dict(workloads.system_kwargs("config0")),
-    dict(workloads.system_kwargs("config0"), move=soma.SOMA_MOVE_SMART),
+    dict(workloads.system_kwargs("melt_512x32")),
+    dict(workloads.system_kwargs("melt_512x32"), move=soma.SOMA_MOVE_SMART),
     dict(n_poly=37, N=7, n_A=3, box=(4.0, 4.5, 5.0), grid=(16, 18, 20), chiN=15.0, kappaN=40.0, seed=7),
     dict(n_poly=40, N=80, n_A=30, box=(2.0, 2.0, 2.0), grid=(8, 8, 8), chiN=25.0, kappaN=50.0, seed=7),  # generic
 ])
@@ -101,7 +101,7 @@ def test_umbrella_invariant_to_graphs_and_batching():
 
 
 def test_umbrella_pulls_composition_toward_target():
-    s = soma.System(**workloads.system_kwargs("config0"), move=soma.SOMA_MOVE_UNIFORM)
+    s = soma.System(**workloads.system_kwargs("melt_512x32"), move=soma.SOMA_MOVE_UNIFORM)
     tg = _target(s)
     _, _, rho = G.oracle_for(s).params()
 
@@ -118,7 +118,7 @@ def test_umbrella_pulls_composition_toward_target():
 
 
 def test_place_matches_oracle():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(s)
     tg = _target(s, seed=8)
     ref = orc.place(tg)
@@ -134,7 +134,7 @@ def test_place_matches_oracle():
 
 
 def test_place_rejects_targets_without_weight_and_keeps_state():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     tg = np.zeros((2, s.n_cells), np.float32)
     tg[1] = 1.0  # bead 0 is type A: no weight
     with soma.Handle(s) as h:
@@ -148,7 +148,7 @@ def test_place_rejects_targets_without_weight_and_keeps_state():
 
 
 def test_place_then_umbrella_reproduces_target():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     tg = _target(s, seed=9)
     _, _, rho = G.oracle_for(s).params()
     with soma.Handle(s) as h:
@@ -190,7 +190,7 @@ def test_umbrella_switched_on_keeps_supplied_fields_for_the_next_step():
     """Fields supplied by soma_set_density for the next step stay as supplied
     when the restraint is switched on afterwards; the restraint enters the
     fields built after that step."""
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(s)
     tg = _target(s, seed=14)
     rng = np.random.default_rng(2)

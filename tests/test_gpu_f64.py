@@ -26,7 +26,7 @@ def _unwrapped64(h):
 
 
 def test_f64_one_step_tight_parity():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(s, pos64=True)
     with soma.Handle(s, **F64) as h:
         for _ in range(5):
@@ -46,7 +46,7 @@ def test_f64_one_step_tight_parity():
 
 
 def test_f64_follows_oracle_for_1000_steps():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(s, pos64=True)
     with soma.Handle(s, **F64) as h:
         X, step = _unwrapped64(h)
@@ -63,7 +63,7 @@ def test_f64_follows_oracle_for_1000_steps():
 
 
 def test_f64_restrictions():
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     with soma.Handle(s, **F64) as h:
         with pytest.raises(soma.SomaError) as e:
             h.get_state()

@@ -24,7 +24,7 @@ def test_bounded_wait_gives_up_and_the_context_survives():
     t0 = time.perf_counter()
     assert soma.soma_selfcheck_timeout(0, 100_000_000) == soma.SOMA_ETIMEOUT  # ~0.05 s of SM clock
     assert time.perf_counter() - t0 < 30.0
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     with soma.Handle(s, device=0) as h:
         h.mc_steps(3)
         h.sync()
@@ -58,7 +58,7 @@ class DryAllocator:
 @pytest.mark.parametrize("budget", [0, 3, 12])
 def test_allocator_running_dry_fails_cleanly(budget):
     lib = G.lib()
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     d = (soma.soma_system_desc * 1)(s.desc())
     o = soma.soma_options_default()
     o.device = 0
@@ -72,7 +72,7 @@ def test_allocator_running_dry_fails_cleanly(budget):
 
 def test_allocator_with_enough_memory_runs_and_returns_everything():
     lib = G.lib()
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     d = (soma.soma_system_desc * 1)(s.desc())
     o = soma.soma_options_default()
     o.device = 0

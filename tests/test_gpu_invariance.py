@@ -97,10 +97,10 @@ def test_reorder_keeps_logical_state():
 
 
 def test_persistent_grid_invariance_full_size():
-    """config1 at full size: with 1, 2 and 3 resident CTAs per SM every CTA
+    """melt_131072x32 at full size: with 1, 2 and 3 resident CTAs per SM every CTA
     cycles its stage ring many times per step; the trajectory must not
     depend on how the tiles are spread over the persistent CTAs."""
-    s = soma.System(**workloads.system_kwargs("config1"))
+    s = soma.System(**workloads.system_kwargs("melt_131072x32"))
     ref = None
     for c in (3, 1, 2):
         with soma.Handle(s, ctas_per_sm=c, graph_steps=0, sort_interval=0) as h:
@@ -114,10 +114,10 @@ def test_persistent_grid_invariance_full_size():
 
 @pytest.mark.parametrize("variant", ["uniform", "smart", "walls"])
 def test_long_run_grid_invariance_full_size(variant):
-    """A stage-ring race would show up only now and then: config1 at full
+    """A stage-ring race would show up only now and then: melt_131072x32 at full
     size for many steps, CUDA graphs and chain reorders on, with 3 and 1
     resident CTAs per SM, must stay bit-identical throughout."""
-    kw = dict(workloads.system_kwargs("config1"))
+    kw = dict(workloads.system_kwargs("melt_131072x32"))
     if variant == "smart":
         kw["move"] = soma.SOMA_MOVE_SMART
     if variant == "walls":

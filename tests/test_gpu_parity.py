@@ -37,8 +37,8 @@ def _fields_bound(orc, counts):
 
 
 @pytest.mark.parametrize("hist", [soma.SOMA_HIST_FUSED, soma.SOMA_HIST_SEPARATE])
-def test_density_and_fields_config0(hist):
-    sysm = soma.System(**workloads.system_kwargs("config0"))
+def test_density_and_fields_melt_512x32(hist):
+    sysm = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(sysm)
     with soma.Handle(sysm, hist_mode=hist) as h:
         for _ in range(3):
@@ -52,8 +52,8 @@ def test_density_and_fields_config0(hist):
             h.mc_steps(5)
 
 
-def test_step_parity_config0_ten_steps():
-    sysm = soma.System(**workloads.system_kwargs("config0"))
+def test_step_parity_melt_512x32_ten_steps():
+    sysm = soma.System(**workloads.system_kwargs("melt_512x32"))
     with soma.Handle(sysm, graph_steps=0) as h:
         tot_sus = 0
         for _ in range(10):
@@ -127,16 +127,16 @@ def _sampled_parity(name, n_sample, steps=2, **opts):
 BENCH_OPTS = dict(autotune=1, graph_steps=0, kernel_timing=1)
 
 
-def test_step_parity_config1_full_size_sampled():
-    _sampled_parity("config1", 4096, **BENCH_OPTS)
+def test_step_parity_melt_131072x32_full_size_sampled():
+    _sampled_parity("melt_131072x32", 4096, **BENCH_OPTS)
 
 
-def test_step_parity_config2_full_size_sampled():
-    _sampled_parity("config2", 2048, steps=1, **BENCH_OPTS)
+def test_step_parity_melt_1048576x64_full_size_sampled():
+    _sampled_parity("melt_1048576x64", 2048, steps=1, **BENCH_OPTS)
 
 
 def test_observables_match_oracle():
-    sysm = soma.System(**workloads.system_kwargs("config0"))
+    sysm = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(sysm)
     with soma.Handle(sysm) as h:
         h.mc_steps(7)
@@ -150,7 +150,7 @@ def test_observables_match_oracle():
 
 
 def test_structure_factor_matches_oracle():
-    sysm = soma.System(**workloads.system_kwargs("config0"))
+    sysm = soma.System(**workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(sysm)
     m = np.array([(x, y, z) for x in range(-3, 4) for y in range(-3, 4) for z in range(0, 4)
                   if 0 < x * x + y * y + z * z <= 12], np.int32)
@@ -172,7 +172,7 @@ def test_steps_from_the_oracle_state_without_resync(variant):
     agrees except for beads set aside for cause, with their chains: a
     margin inside the band or a position near a cell face, at any step so
     far, or an old or new cell whose counts differ between the two sides."""
-    kw = dict(workloads.system_kwargs("config0"))
+    kw = dict(workloads.system_kwargs("melt_512x32"))
     if variant == "smart":
         kw["move"] = soma.SOMA_MOVE_SMART
     if variant == "walls":

@@ -105,7 +105,7 @@ def test_long_run_statistics_agree_with_oracle(move):
     """chiN = 20, kappaN = 50 (config 0 shape): <R_e^2>, acceptance and the
     peak of S(q) from the GPU and the oracle agree within 3 sigma over seeds,
     for both trial-move kinds."""
-    kw = {**workloads.system_kwargs("config0"), "move": move}
+    kw = {**workloads.system_kwargs("melt_512x32"), "move": move}
     m = np.array([(x, y, z) for x in range(-4, 5) for y in range(-4, 5) for z in range(-4, 5)
                   if 0 < x * x + y * y + z * z <= 16], np.int32)
     shells = (m ** 2).sum(1)
@@ -158,7 +158,7 @@ def test_long_run_slab_statistics_agree_with_oracle():
     total-density profile of the two wall layers from the GPU and the oracle
     agree within 3 sigma over 8 seeds (the depletion at the walls is a
     property of the confined melt that neither side is told)."""
-    kw = {**workloads.system_kwargs("config0"), "wall_z": 1}
+    kw = {**workloads.system_kwargs("melt_512x32"), "wall_z": 1}
     burn, steps, every = 300, 1200, 100
 
     def stats(seed, gpu):
@@ -204,7 +204,7 @@ def test_long_run_conversion_statistics_agree_with_oracle():
     acceptance from the GPU and the oracle agree within 3 sigma over 8 seeds
     (chains diffuse in and out of the zones, so none of these has a closed
     form)."""
-    kw = {**workloads.system_kwargs("config0"), "wall_z": 1}
+    kw = {**workloads.system_kwargs("melt_512x32"), "wall_z": 1}
     conv = (4, 1.0, 1.0, (0.05, 0.02, 0.03, 0.04))
     burn, steps, every = 300, 1200, 100
 

@@ -42,8 +42,8 @@ def test_smart_step_parity_shapes(kw, ctas):
             assert abs(st["acc_gpu"] - st["acc_orc"]) <= st["suspect"]
 
 
-def test_smart_step_parity_config0_ten_steps():
-    sysm = soma.System(**{**workloads.system_kwargs("config0"), "move": SMART})
+def test_smart_step_parity_melt_512x32_ten_steps():
+    sysm = soma.System(**{**workloads.system_kwargs("melt_512x32"), "move": SMART})
     with soma.Handle(sysm, graph_steps=0) as h:
         tot_sus, acc = 0, 0
         for _ in range(10):
@@ -56,7 +56,7 @@ def test_smart_step_parity_config0_ten_steps():
 
 
 def test_smart_step_parity_in_held_fields():
-    sysm = soma.System(**{**workloads.system_kwargs("config0"), "move": SMART})
+    sysm = soma.System(**{**workloads.system_kwargs("melt_512x32"), "move": SMART})
     rng = np.random.default_rng(4)
     w = rng.normal(0.0, 0.8, size=(2, sysm.n_cells)).astype(np.float32)
     with soma.Handle(sysm, graph_steps=0) as h:
@@ -65,9 +65,9 @@ def test_smart_step_parity_in_held_fields():
             G.compare_step(h, band=BAND, w=w.astype(np.float64))
 
 
-@pytest.mark.parametrize("workload,n_sample", [("config1", 2048), ("config2", 1024)])
+@pytest.mark.parametrize("workload,n_sample", [("melt_131072x32", 2048), ("melt_1048576x64", 1024)])
 def test_smart_step_parity_full_size_sampled(workload, n_sample):
-    """config1 and config2 (64-bead chains, a whole warp per chain) with
+    """melt_131072x32 and melt_1048576x64 (64-bead chains, a whole warp per chain) with
     smart moves in the bench's launch configuration; the oracle recomputes
     a sample of chains with the full system's fields."""
     sysm = soma.System(**{**workloads.system_kwargs(workload), "move": SMART})

@@ -18,8 +18,8 @@ def _lib():
 
 
 SHAPES = [
-    dict(workloads.system_kwargs("config0")),
-    dict(workloads.system_kwargs("config0"), move=soma.SOMA_MOVE_SMART),
+    dict(workloads.system_kwargs("melt_512x32")),
+    dict(workloads.system_kwargs("melt_512x32"), move=soma.SOMA_MOVE_SMART),
     dict(n_poly=37, N=7, n_A=3, box=(4.0, 4.5, 5.0), grid=(16, 18, 20), chiN=15.0, kappaN=40.0, seed=7),
     dict(n_poly=40, N=80, n_A=30, box=(2.0, 2.0, 2.0), grid=(8, 8, 8), chiN=25.0, kappaN=50.0, seed=7),  # generic
     dict(n_poly=200, N=1, n_A=1, box=(2.0, 2.0, 2.0), grid=(4, 4, 4), chiN=5.0, kappaN=10.0, A=0.25),
@@ -38,7 +38,7 @@ def test_wall_step_parity(kw, ctas):
 
 
 def test_wall_initial_configuration_matches_oracle_and_stays_in_the_slab():
-    s = soma.System(wall_z=1, **workloads.system_kwargs("config0"))
+    s = soma.System(wall_z=1, **workloads.system_kwargs("melt_512x32"))
     orc = G.oracle_for(s)
     ref = orc.init()
     with soma.Handle(s) as h:

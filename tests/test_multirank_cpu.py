@@ -21,7 +21,7 @@ def _worker(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
-    kw = bench.rank_system_kwargs("config1", rank)
+    kw = bench.rank_system_kwargs("melt_131072x32", rank)
     # rank r pretends its timed region took 10 * (r + 1) ms for 1000 * (r + 1) moves
     max_ms, moves, value = bench.aggregate(10.0 * (rank + 1), 1000.0 * (rank + 1), dist, device="cpu")
     out[rank] = (kw["system_id"], kw["n_poly"], max_ms, moves, value)

@@ -20,7 +20,7 @@ def test_noalloc_structure_factor_matches_handle_twice():
     import gpu_util as G
     from paper_2606_09356_b300 import soma, workloads
     G.lib()
-    s = soma.System(**workloads.system_kwargs("config0"))
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
     m = _m()
     with soma.Handle(s) as h:
         pos_dev = torch.empty((s.n_beads, 3), dtype=torch.float32, device="cuda")
