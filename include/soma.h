@@ -81,7 +81,7 @@ extern "C" {
 #define SOMA_HIST_SEPARATE 2  /* separate histogram kernel after the moves */
 
 /* Trial-move kinds (soma_system_desc.move). */
-#define SOMA_MOVE_UNIFORM 0 /* displacement uniform in [-A, A)^3 (Sec. 2.1, step (a)) */
+#define SOMA_MOVE_UNIFORM 0 /* displacement uniform in [-A, A)^3 (step (a) above; Sec. 2, the SOMA paragraph) */
 #define SOMA_MOVE_SMART 1   /* bond-force-biased ("smart") move named in Sec. 2: a
                                Gaussian displacement of per-axis variance s2 = A^2/3
                                centred on (s2/2) F, F the bond force on the bead, with

@@ -277,7 +277,7 @@ __device__ __forceinline__ float2 propose_z(const MoveArgs& a, float ze, float z
 }
 
 // The bead pair of one lane: positions in, decisions, final cells and image
-// codes out.  Uniform proposals (Sec. 2.1, step (a)).
+// codes out.  Uniform proposals (Sec. 2, the SOMA paragraph: the MC propagation of beads).
 template <bool kFromCounts, bool kWall>
 __device__ __forceinline__ void uniform_pair(const MoveArgs& a, long long tl, const uint2* __restrict__ prev,
                                              uint32_t cid, int k, int e, int o,
