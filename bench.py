@@ -481,6 +481,8 @@ def run_gpu(args):
                        "tuned": {k: info_after[k] for k in ("ctas_per_sm", "hist_mode")},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "step_ms_stats": {"median": float(statistics.median(step_ms)), "min": float(min(step_ms)),
+                              "max": float(max(step_ms))},
             "clocks": clk.summary(), "steady_state": steady, "energy": energy, "smart_moves": smart, "umbrella": umbrella,
             "boundary_zones": zones,
             "batched": batched,

@@ -48,3 +48,5 @@ def test_headline_line():
     assert d["e2e"]["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["clocks"]["sm_mhz"] > 0 and isinstance(d["clocks"]["reasons"], list)
     assert "l2" in d["config"] and d["dtype"] == "f32" and d["data"] == "synthetic"
+    st = d["step_ms_stats"]
+    assert 0 < st["min"] <= st["median"] <= st["max"] and st["min"] <= d["ms_per_step"] <= st["max"]
