@@ -361,21 +361,27 @@ class Handle:
         """Boundary-zone conversion: converted molecules have n_A_alt A beads;
         zone widths in z; p = per-step probabilities (bottom 0->1, bottom
         1->0, top 0->1, top 1->0).  n_A_alt < 0 switches it off."""
-        pv = np.ascontiguousarray(p, np.float64)
+        pv = np.ascontiguousarray(p, np.float64).reshape(-1)
+        if pv.size != 4:
+            raise ValueError("p holds four per-step probabilities")
         _check(self.lib.soma_set_conversion(self.h, sys, int(n_A_alt), float(zone_lo), float(zone_hi), _ptr(pv)),
                "soma_set_conversion")
 
     def conversions(self, sys=0):
+        """Conversions since the rates were last set, in the order of p."""
         out = np.zeros(4, np.uint64)
         _check(self.lib.soma_get_conversions(self.h, sys, _ptr(out)), "soma_get_conversions")
         return out
 
     def chain_types(self, sys=0):
+        """Molecule type (0 own, 1 converted) of every chain, logical order."""
         out = np.zeros(self.systems[sys].n_poly, np.uint8)
         _check(self.lib.soma_get_chain_types(self.h, sys, _ptr(out), out.size), "soma_get_chain_types")
         return out
 
     def set_chain_types(self, types, sys=0):
+        """Set every chain's molecule type (conversion must be on); the counts
+        and fields are rebuilt with the new types."""
         t = np.ascontiguousarray(types, np.uint8)
         _check(self.lib.soma_set_chain_types(self.h, sys, _ptr(t), t.size), "soma_set_chain_types")
 
