@@ -165,6 +165,31 @@ def _where(a):
     return SOMA_DEVICE if hasattr(a, "data_ptr") and a.is_cuda else SOMA_HOST
 
 
+def _numel_f32(a, what):
+    """Element count of a float32 buffer (numpy array or contiguous float32
+    torch tensor, host or device)."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError(f"{what}: expected a contiguous float32 tensor")
+        return a.numel()
+    return a.size
+
+
+def _check_buffer(a, n, np_dtype, what):
+    """A caller buffer the C call fills or reads in full: contiguous, of the
+    right element type and exactly n elements (the C calls take no length)."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        tdt = {np.dtype(np.float32): torch.float32, np.dtype(np.int16): torch.int16,
+               np.dtype(np.float64): torch.float64}[np.dtype(np_dtype)]
+        ok = a.numel() == n and a.is_contiguous() and a.dtype == tdt
+    else:
+        ok = a.size == n and a.dtype == np_dtype and a.flags.c_contiguous
+    if not ok:
+        raise ValueError(f"{what}: expected a contiguous {np.dtype(np_dtype).name} buffer of {n} elements")
+
+
 def _check(code, what):
     if code != SOMA_OK:
         raise SomaError(code, what)
@@ -392,20 +417,26 @@ class Handle:
             return
         if not hasattr(phi_target, "data_ptr"):
             phi_target = np.ascontiguousarray(phi_target, np.float32)
-        _check(self.lib.soma_set_umbrella(self.h, sys, _ptr(phi_target), phi_target.size, float(lambdaN),
+        _check(self.lib.soma_set_umbrella(self.h, sys, _ptr(phi_target), _numel_f32(phi_target, "phi_target"),
+                                          float(lambdaN),
                                           _where(phi_target)), "soma_set_umbrella")
 
     def place(self, phi_target, sys=0):
         """New configuration of molecules placed from target volume fractions [2, n_c]."""
         if not hasattr(phi_target, "data_ptr"):
             phi_target = np.ascontiguousarray(phi_target, np.float32)
-        _check(self.lib.soma_place(self.h, sys, _ptr(phi_target), phi_target.size, _where(phi_target)),
+        _check(self.lib.soma_place(self.h, sys, _ptr(phi_target), _numel_f32(phi_target, "phi_target"),
+                                   _where(phi_target)),
                "soma_place")
 
     def get_state(self, sys=0, pos=None, img=None):
         nb = self.systems[sys].n_beads
         pos = np.zeros((nb, 3), np.float32) if pos is None else pos
         img = np.zeros((nb, 3), np.int16) if img is None else img
+        _check_buffer(pos, 3 * nb, np.float32, "pos")
+        _check_buffer(img, 3 * nb, np.int16, "img")
+        if _where(pos) != _where(img):
+            raise ValueError("pos and img must both be host or both be device buffers")
         step = ctypes.c_uint64()
         _check(self.lib.soma_get_state(self.h, sys, _ptr(pos), _ptr(img), ctypes.byref(step), _where(pos)),
                "soma_get_state")
@@ -416,6 +447,11 @@ class Handle:
         if where == SOMA_HOST:
             pos = np.ascontiguousarray(pos, np.float32)
             img = np.ascontiguousarray(img, np.int16)
+        nb = self.systems[sys].n_beads
+        _check_buffer(pos, 3 * nb, np.float32, "pos")
+        _check_buffer(img, 3 * nb, np.int16, "img")
+        if _where(img) != where:
+            raise ValueError("pos and img must both be host or both be device buffers")
         _check(self.lib.soma_set_state(self.h, sys, _ptr(pos), _ptr(img), int(step), where), "soma_set_state")
 
     def get_state64(self, sys=0):
@@ -430,6 +466,9 @@ class Handle:
     def set_state64(self, pos, img, step, sys=0):
         pos = np.ascontiguousarray(pos, np.float64)
         img = np.ascontiguousarray(img, np.int16)
+        nb = self.systems[sys].n_beads
+        _check_buffer(pos, 3 * nb, np.float64, "pos")
+        _check_buffer(img, 3 * nb, np.int16, "img")
         _check(self.lib.soma_set_state64(self.h, sys, _ptr(pos), _ptr(img), int(step), SOMA_HOST),
                "soma_set_state64")
 

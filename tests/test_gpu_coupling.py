@@ -205,3 +205,24 @@ def test_umbrella_switched_on_keeps_supplied_fields_for_the_next_step():
         counts = h.get_density()
         ref = orc.fields_umbrella(counts, tg.astype(np.float64), LAMBDA)
         assert np.all(np.abs(h.get_fields() - ref) <= _fields_bound(orc, counts, tg, LAMBDA))
+
+
+def test_device_tensors_as_targets_match_host_arrays():
+    """Targets given as CUDA tensors (SOMA_DEVICE) place and restrain exactly
+    as the same values given as host arrays."""
+    import torch
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
+    tg = _target(s, seed=21)
+    runs = []
+    for on_device in (False, True):
+        t = torch.from_numpy(tg).cuda() if on_device else tg
+        with soma.Handle(s, graph_steps=0) as h:
+            h.place(t)
+            h.set_umbrella(t, 30.0)
+            h.mc_steps(3)
+            runs.append((h.get_state()[0], h.get_density(), h.get_fields()))
+    for a, b in zip(*runs):
+        assert np.array_equal(a, b)
+    with soma.Handle(s, graph_steps=0) as h:  # a tensor of another type is refused before the C call
+        with pytest.raises(ValueError):
+            h.place(torch.from_numpy(tg).double().cuda())
