@@ -176,6 +176,17 @@ def _numel_f32(a, what):
     return a.size
 
 
+def _check_words(a, n, itemsize, what):
+    """A caller buffer of n contiguous elements of the given byte size
+    (numpy array or torch tensor, host or device)."""
+    if hasattr(a, "data_ptr"):
+        ok = a.numel() == n and a.element_size() == itemsize and a.is_contiguous()
+    else:
+        ok = a.size == n and a.itemsize == itemsize and a.flags.c_contiguous
+    if not ok:
+        raise ValueError(f"{what}: expected {n} contiguous elements of {itemsize} bytes")
+
+
 def _check_buffer(a, n, np_dtype, what):
     """A caller buffer the C call fills or reads in full: contiguous, of the
     right element type and exactly n elements (the C calls take no length)."""
@@ -348,6 +359,7 @@ class Handle:
     def get_density(self, sys=0, out=None):
         nc = self.systems[sys].n_cells
         out = np.zeros((2, nc), np.uint32) if out is None else out
+        _check_words(out, 2 * nc, 4, "out")
         _check(self.lib.soma_get_density(self.h, sys, _ptr(out), 2 * nc, _where(out)), "soma_get_density")
         return out
 
@@ -497,6 +509,7 @@ class Handle:
         """Enqueue the accepted count into dst (a 1-element uint64 host array;
         pinned and 8-byte aligned, the reduction kernel writes it directly,
         otherwise it is copied); valid after the stream synchronises."""
+        _check_words(dst, 1, 8, "dst")
         _check(self.lib.soma_copy_accepted(self.h, sys, _ptr(dst), stream), "soma_copy_accepted")
 
     def structure_factor(self, m, sys=0):
