@@ -69,7 +69,8 @@ struct soma_handle {
   std::vector<void*> owned;
   // launch geometry
   int max_ctas_per_sm = 1;
-  int max_ctas_batch = 1;
+  int max_ctas_batch = 1;              // the largest over the batch kernel's specialisations
+  int max_ctas_batch_kind[2][2] = {};  // [smart][wall]
   int ctas_per_sm = 1;
   int hist_mode = SOMA_HIST_FUSED;
   int sort_interval = kDefaultSortInterval;
@@ -408,7 +409,9 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
         for (int m = 0; m < b->n_sys; ++m)
           if ((rc = enqueue_umbrella_fields(h, s, h->batch_members[g][m], graph, t0, i))) return rc;
         if (timing) begin_timed(h, s, te, T_MOVE);
-        CK(launch_move_batch(*b, move_grid(h, b->tile_start[b->n_sys], h->max_ctas_batch),
+        // one wave: at most as many CTAs as this specialisation keeps resident
+        const int fit = h->max_ctas_batch_kind[b->sys[0].smart ? 1 : 0][b->sys[0].wall_z ? 1 : 0];
+        CK(launch_move_batch(*b, move_grid(h, b->tile_start[b->n_sys], fit),
                              step_ref(h, 0, graph, t0, i), s));
         if (timing) end_timed(h, s, te);
       }
@@ -642,7 +645,11 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
       cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming) != cudaSuccess)
     return bail(SOMA_ECUDA);
   h->max_ctas_per_sm = move_kernel_max_ctas_per_sm();
-  h->max_ctas_batch = move_batch_max_ctas_per_sm();
+  for (int sm = 0; sm < 2; ++sm)
+    for (int wz = 0; wz < 2; ++wz) {
+      h->max_ctas_batch_kind[sm][wz] = move_batch_max_ctas_per_sm(sm != 0, wz != 0);
+      h->max_ctas_batch = std::max(h->max_ctas_batch, h->max_ctas_batch_kind[sm][wz]);
+    }
   h->ctas_per_sm = o.ctas_per_sm ? std::min<int>(o.ctas_per_sm, h->max_ctas_per_sm) : h->max_ctas_per_sm;
   h->hist_mode = o.hist_mode == SOMA_HIST_AUTO ? SOMA_HIST_FUSED : o.hist_mode;
   h->sort_interval = o.sort_interval < 0 ? kDefaultSortInterval : o.sort_interval;

@@ -11,7 +11,7 @@ namespace soma {
 // Kernel (a) with fused (b), soma_move.cu.
 cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s);
 cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStream_t s);
-int move_batch_max_ctas_per_sm();
+int move_batch_max_ctas_per_sm(bool smart, bool wall);
 int move_kernel_max_ctas_per_sm();
 int move_kernel_chains_per_tile(int P);
 // The smart move's standard normal deviates of n words (verification aid).

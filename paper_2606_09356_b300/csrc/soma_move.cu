@@ -811,10 +811,14 @@ cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStrea
   return cudaGetLastError();
 }
 
-int move_batch_max_ctas_per_sm() {
+// Resident CTAs per SM of one specialisation of the batch kernel (they
+// differ in registers: the persistent grid must fit in one wave).
+int move_batch_max_ctas_per_sm(bool smart, bool wall) {
+  using Kernel = void (*)(BatchArgs, StepRef);
+  const Kernel k = smart ? (wall ? k_move_batch<true, true> : k_move_batch<true, false>)
+                         : (wall ? k_move_batch<false, true> : k_move_batch<false, false>);
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move_batch<false, false>, (kConsumerWarps + 1) * 32, 0) !=
-      cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, (kConsumerWarps + 1) * 32, 0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
