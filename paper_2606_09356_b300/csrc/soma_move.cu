@@ -695,8 +695,10 @@ __device__ __forceinline__ int batch_system(const BatchArgs& p, int tile) {
 }
 
 // One move kind and one z boundary per launch (the host groups systems so).
+// Register budget for 3 resident CTAs per SM as k_move (the bond-force-biased
+// specialisations spill a few bytes and still beat 2 CTAs per SM).
 template <bool kSmart, bool kWall>
-__global__ void __launch_bounds__((kConsumerWarps + 1) * 32)
+__global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3)
     k_move_batch(const __grid_constant__ BatchArgs p, StepRef r) {
   __shared__ MoveStage stage[kStages];
   __shared__ __align__(8) uint64_t full[kStages];
