@@ -7,7 +7,11 @@
 // (c) k_field: per-cell field array from the counts (the register move kernel
 //     evaluates the same fields from the counts on the fly; this kernel
 //     serves the generic path and requests for the field array).
-// plus initialisation, state gather/scatter, validation, observables and S(q).
+// plus initialisation, placement from target fields and the umbrella
+// restraint's field array (Sec. 3.2), molecule types of the boundary-zone
+// conversion (read and set; the conversion itself runs in the move kernel),
+// state gather/scatter, validation, layer profiles, vertical correlations,
+// observables and S(q).
 //
 // Layout (per system, see soma_internal.cuh): positions as three FP32 arrays
 // x, y, z [n_b] wrapped into [0, L), bead = slot * N + i; images int16
