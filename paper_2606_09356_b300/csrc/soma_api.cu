@@ -1,7 +1,8 @@
 // soma_api.cu -- the C ABI of include/soma.h: handle life cycle, step
 // scheduling (plain launches or CUDA-graph replay; a batch of independent
-// systems steps in one persistent launch), state I/O, observables, reorder
-// scheduling, per-kernel timing and the autotuner.
+// systems steps in one persistent launch), state I/O, the coupling calls
+// (fields given, held or restrained; placement; boundary-zone conversion),
+// observables, reorder scheduling, per-kernel timing and the autotuner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
