@@ -475,8 +475,8 @@ def run_gpu(args):
                               args.warmup, hbm_peak, n_b, n_c, wall_z=1,
                               conversion=(kw["n_A"] // 2, 2.0, 2.0, (0.05, 0.02, 0.03, 0.04)),
                               note="walls in z and boundary-zone conversion (zones 2 R_e wide, per-step "
-                                   "rates 0.02-0.05): conversion kernel, then the move kernel on molecule "
-                                   "types, per step; L2 flushed")
+                                   "rates 0.02-0.05): each chain's conversion decided inside the move kernel, "
+                                   "whose moves and counts use the new types; L2 flushed")
 
     # batched replicas vs sequential plain runs of the same 64 systems
     batched = None

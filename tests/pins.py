@@ -642,8 +642,9 @@ def pin_conversion_type_field(O, blocks=16, per_block=15):
     for b in range(blocks):
         r = o.run(pos, 10 + b * per_block, per_block, w_frozen=w, n_threads=NTHREADS, occ=True)
         occ = r["occ"].reshape(2, o.n_c).astype(np.float64)
-        if occ[0].sum() != 0:
+        if occ[0].sum() != 0 or occ[1].sum() == 0:
             fails.append("A beads counted after the conversion")
+            return fails
         samples.append(occ[1] / occ[1].sum())
     p = np.exp(-w[1])
     _block_test(fails, "converted bead occupancy", np.array(samples), p / p.sum())
