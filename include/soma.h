@@ -65,7 +65,7 @@ extern "C" {
 #define SOMA_ETIMEOUT (-4)      /* a bounded device-side wait ran out */
 #define SOMA_EDEVICE_CHECK (-5) /* a device-side consistency check failed */
 #define SOMA_ESTATE (-6)        /* handle already in a failed state */
-#define SOMA_ENOTSUP (-7)       /* valid request this build does not support */
+#define SOMA_ENOTSUP (-7)       /* valid request the library does not support */
 
 #define SOMA_HOST 0
 #define SOMA_DEVICE 1

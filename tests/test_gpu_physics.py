@@ -102,7 +102,7 @@ def test_dimer_cell_pair_law_in_frozen_field():
 
 @pytest.mark.parametrize("move", [soma.SOMA_MOVE_UNIFORM, soma.SOMA_MOVE_SMART])
 def test_long_run_statistics_agree_with_oracle(move):
-    """chiN = 20, kappaN = 50 (config 0 shape): <R_e^2>, acceptance and the
+    """chiN = 20, kappaN = 50 (512 chains of 32 beads): <R_e^2>, acceptance and the
     peak of S(q) from the GPU and the oracle agree within 3 sigma over seeds,
     for both trial-move kinds."""
     kw = {**workloads.system_kwargs("melt_512x32"), "move": move}
@@ -154,7 +154,7 @@ def test_long_run_statistics_agree_with_oracle(move):
 
 
 def test_long_run_slab_statistics_agree_with_oracle():
-    """Between hard walls in z (config 0 shape): <R_e^2>, acceptance and the
+    """Between hard walls in z (512 chains of 32 beads): <R_e^2>, acceptance and the
     total-density profile of the two wall layers from the GPU and the oracle
     agree within 3 sigma over 8 seeds (the depletion at the walls is a
     property of the confined melt that neither side is told)."""
@@ -198,7 +198,7 @@ def test_long_run_slab_statistics_agree_with_oracle():
 
 
 def test_long_run_conversion_statistics_agree_with_oracle():
-    """Between walls with boundary-zone conversion (config 0 shape, zones
+    """Between walls with boundary-zone conversion (512 chains of 32 beads, zones
     1 R_e wide, converted molecules A4B28): the time-averaged fraction of
     converted chains, the A volume fraction of the two wall layers and the
     acceptance from the GPU and the oracle agree within 3 sigma over 8 seeds
