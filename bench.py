@@ -69,19 +69,45 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(workload, variant=""):
-    """DRAM bytes per launch of the move kernel from the committed ncu summary,
-    if that summary was taken from the current kernel source."""
+def _profiled_value(workload, variant, key):
+    """A per-launch figure of the move kernel (`key: value` line) from the
+    committed ncu summary, if that summary was taken from the current kernel
+    source."""
     path = os.path.join(ROOT, "profiles", f"k_move{variant}_{workload}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    t = re.search(key + r":\s*([0-9.eE+]+)", text)
     if not m or not t or m.group(1) != _kernel_source_hash():
         return None
     return float(t.group(1))
+
+
+def _profiled_traffic(workload, variant=""):
+    """DRAM bytes per launch of the move kernel (ncu dram__bytes_read.sum +
+    dram__bytes_write.sum)."""
+    return _profiled_value(workload, variant, "dram_bytes_per_launch")
+
+
+def issue_roofline(workload, variant, move_ms, sm_max_mhz):
+    """The move kernel against the SM issue ceiling: its warp instructions per
+    launch (ncu smsp__inst_executed.sum of the same kernel source) over its
+    average launch time, against 4 warp instructions per cycle per SM (one
+    per scheduler) at the SM count and the maximum SM clock."""
+    inst = _profiled_value(workload, variant, "warp_instructions_per_launch")
+    if inst is None or not move_ms:
+        return None
+    import torch
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_max_mhz or 2032.0
+    peak = n_sm * 4 * mhz * 1e6 / 1e9
+    achieved = inst / (move_ms * 1e-3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp instructions/s",
+            "frac": achieved / peak, "warp_instructions": inst, "floor_ms": inst / (peak * 1e9) * 1e3,
+            "peak_kind": f"{n_sm} SMs x 4 schedulers x {mhz:.0f} MHz"
+                         + ("" if sm_max_mhz else " (nominal maximum clock)")}
 
 
 class _Nvml:
@@ -238,9 +264,10 @@ def move_kernel_bytes(n_b, n_c):
 
 # ---------------------------------------------------------------------------
 def cpu_baseline(name, budget_s=12.0, steps_cap=None):
-    """The oracle as it stands, on the host cores, on a bounded sample: a
-    system of the workload's shape (same Delta, density, N, chiN, kappaN) with
-    the box shrunk until the sampled steps take about budget_s seconds."""
+    """The oracle as it stands, on the host cores, on a bounded sample of
+    about budget_s seconds: the workload's system itself for as many steps as
+    fit, or, where three of its steps take longer, a system of its shape (same
+    Delta, density, N, chiN, kappaN) with the box shrunk to fit."""
     from oracle import Oracle
     from paper_2606_09356_b300 import workloads
     c = workloads.system_kwargs(name)
@@ -264,6 +291,8 @@ def cpu_baseline(name, budget_s=12.0, steps_cap=None):
     target_beads = rate * budget_s / steps
     L = min(L0, max(4.0, L0 * (target_beads / (c["n_poly"] * c["N"])) ** (1 / 3)))
     o = make(L)
+    if steps_cap is None:  # a full-size system done in under the budget: more steps of it
+        steps = max(steps, min(60, int(rate * budget_s / o.n_b)))
     X = o.init()
     t = time.perf_counter()
     o.run(X, 0, steps, n_threads=cores)
@@ -465,14 +494,14 @@ def run_gpu(args):
     if not args.no_smart:
         kw = rank_system_kwargs(args.workload, rank)
         smart = bench_variant(soma, torch, args.workload, kw, local, sptr, stream, flush, args.steps, args.warmup,
-                              hbm_peak, n_b, n_c, move=soma.SOMA_MOVE_SMART,
+                              hbm_peak, n_b, n_c, move=soma.SOMA_MOVE_SMART, sm_max_mhz=clk.max_mhz,
                               note="SOMA_MOVE_SMART, same workload, L2 flushed between timed steps")
         umbrella = bench_variant(soma, torch, args.workload, kw, local, sptr, stream, flush, args.steps,
                                  args.warmup, hbm_peak, n_b, n_c, umbrella=50.0,
                                  note="umbrella restraint (lambdaN = 50) toward a lamellar target: field "
                                       "array from the counts, then the move kernel, per step; L2 flushed")
         zones = bench_variant(soma, torch, args.workload, kw, local, sptr, stream, flush, args.steps,
-                              args.warmup, hbm_peak, n_b, n_c, wall_z=1,
+                              args.warmup, hbm_peak, n_b, n_c, wall_z=1, sm_max_mhz=clk.max_mhz,
                               conversion=(kw["n_A"] // 2, 2.0, 2.0, (0.05, 0.02, 0.03, 0.04)),
                               note="walls in z and boundary-zone conversion (zones 2 R_e wide, per-step "
                                    "rates 0.02-0.05): each chain's conversion decided inside the move kernel, "
@@ -485,6 +514,7 @@ def run_gpu(args):
     h.close()
 
     if rank == 0:
+        clk_summary = clk.summary()
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -497,7 +527,8 @@ def run_gpu(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "step_ms_stats": {"median": float(statistics.median(step_ms)), "min": float(min(step_ms)),
                               "max": float(max(step_ms))},
-            "clocks": clk.summary(), "steady_state": steady, "energy": energy, "smart_moves": smart, "umbrella": umbrella,
+            "issue_roofline": issue_roofline(args.workload, "", move_avg, clk_summary.get("sm_max_mhz")),
+            "clocks": clk_summary, "steady_state": steady, "energy": energy, "smart_moves": smart, "umbrella": umbrella,
             "boundary_zones": zones,
             "batched": batched,
             "wall_s_timed": wall,
@@ -534,7 +565,7 @@ def measure_energy(soma, torch, c, rank, local, sptr, stream, n_b, seconds=2.0):
 
 
 def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps, warmup, hbm_peak, n_b, n_c,
-                  move=0, umbrella=0.0, wall_z=0, conversion=None, note=""):
+                  move=0, umbrella=0.0, wall_z=0, conversion=None, note="", sm_max_mhz=None):
     """The workload with another trial move, the umbrella restraint, or walls
     and boundary-zone conversion: moves/s over flushed steps and the move
     kernel's fraction of the HBM roofline (same algorithmic bytes per step as
@@ -578,10 +609,12 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
         out["field_ms"] = fd_ms / fd_n
     if conversion:
         out["conversions_per_step"] = float(conv_n) / (steps + warmup)
-    if move:
-        out["traffic"] = _profiled_traffic(workload, "_smart")
-    elif conversion:
-        out["traffic"] = _profiled_traffic(workload, "_zones")
+    variant = "_smart" if move else "_zones" if conversion else None
+    if variant:
+        out["traffic"] = _profiled_traffic(workload, variant)
+        iss = issue_roofline(workload, variant, move_avg, sm_max_mhz)
+        if iss:
+            out["issue_frac"] = iss["frac"]
     return out
 
 

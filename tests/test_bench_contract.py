@@ -44,6 +44,10 @@ def test_headline_line():
     r = d["roofline"]
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and 0 < r["frac"] < 1.5
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9
+    iss = d["issue_roofline"]  # null when the committed ncu summary is of another kernel source
+    if iss is not None:
+        assert iss["bound"] == "alu" and 0 < iss["frac"] < 1.05
+        assert abs(iss["floor_ms"] / r["move_ms"] - iss["frac"]) < 1e-9
     assert d["gpu_launches"] >= d["steps"]  # at least the move kernel of every timed step
     assert d["e2e"]["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] > 0 and d["e2e"]["d2h_bytes_per_step"] > 0
     assert d["clocks"]["sm_mhz"] > 0 and isinstance(d["clocks"]["reasons"], list)
