@@ -19,27 +19,42 @@
 //   cells are c = (ix*ny + iy)*nz + iz; counts and fields are [type][cell].
 //
 // Parity status of each exported function (what pins it in tests/):
-//   orc_philox4x32        pinned: an independent third-party Philox4x32-10
+//   orc_philox4x32, orc_philox4x32_many
+//                         pinned: an independent third-party Philox4x32-10
 //                         (Triton's, run by its CPU interpreter) bit for bit;
 //                         chi-square uniformity of its words.
+//   orc_params            pinned: k_b, the proposal half-width (an FP32
+//                         number) and rho_bar of the melt workloads as their
+//                         definitions print them.
+//   orc_cell_index        pinned with orc_density (brute-force binning).
 //   orc_normal_quantile   pinned: scipy's ndtri and the mirror symmetry.
 //   orc_init              pinned: bond statistics of a Gaussian chain
 //                         (<b^2> = 1/(N-1), <R_e^2> = 1, <R_g^2> = (N+1)/6N).
 //   orc_density           pinned: count invariants and brute-force binning.
 //   orc_fields            pinned: central difference of the energy functional
 //                         and the incompressible exchange-field special case.
-//   orc_energy_nb         pinned with the fields: its central differences are
-//                         the fields, which the special case pins on their own.
+//   orc_energy_nb         pinned absolutely on counts built by hand (a uniform
+//                         phi_A = phi_B = 1/2 melt gives n_poly chiN/4, a
+//                         one-cell excess, two hand-worked cells at two
+//                         prefactors); its central differences are the fields.
+//   orc_fields_from_phi   pinned: the incompressible exchange-field case.
+//   orc_mc_step_chains    pinned: a sample of chains moves exactly as inside
+//                         the whole step of orc_mc_step.
 //   orc_mc_step/orc_run   pinned: <R_e^2> = 1 and the acceptance quadrature at
 //                         chiN = kappaN = 0; Boltzmann occupancy of one bead in
 //                         a frozen field; exact 64-state cell-pair law of an AB
 //                         dimer on a 2^3 grid.
-//   orc_observables       pinned through the same closed forms (R_e^2, R_g^2).
+//   orc_observables       pinned: rigid straight and right-angle chains whose
+//                         R_e^2, R_g^2 and bond energy are known by hand, and
+//                         equipartition on Gaussian chains read through this
+//                         function (<E_bond> per chain 3(N-1)/2, <R_e^2> = 1,
+//                         <R_g^2> = (N+1)/6N); E_nb as orc_energy_nb.
 //   orc_structure_factor  pinned: ideal-chain closed form at chiN = kappaN = 0.
 //   force-biased moves    pinned: the same Gaussian-chain statistics, the
 //                         one-bead Boltzmann law and the dimer cell-pair law
 //                         (detailed balance makes them stationary).
 //   orc_fields_umbrella   pinned: central difference of H_nb + H_umb.
+//   orc_energy_umbrella   pinned absolutely on counts and targets by hand.
 //   orc_vertical_correlation pinned: a cosine layer pattern (periodic), a
 //                         linear ramp between walls (closed forms), C(0) = 1.
 //   orc_density_profile   pinned: closed form on constructed counts and the
@@ -49,7 +64,8 @@
 //   orc_place             pinned: the exact law of the bead-0 cell (target
 //                         weights convolved with the uniform offset) and the
 //                         Gaussian bond statistics of the placed chains.
-//   orc_convert           pinned: the two-state Markov law of a molecule's
+//   orc_conversion_threshold, orc_convert
+//                         pinned: the two-state Markov law of a molecule's
 //                         type inside a zone (binomial counts after t steps),
 //                         the zone occupancy law of bead 0 (uniform, so the
 //                         fraction converted by certain flips is the zone's

@@ -21,6 +21,15 @@ list means the pin holds.  The facts used:
 * Fields: the exact central difference of the energy functional H_nb, and the
   exchange field chiN (phiB - phiA)/N of an incompressible cell.
 * S(q) of ideal chains: (1/N) sum_ij s_i s_j exp(-q^2 |i-j| / (6(N-1))).
+* Observables: rigid straight and right-angle chains (R_e^2, R_g^2 and the
+  bond energy by hand), equipartition of the harmonic bond energy and the
+  Gaussian-chain R_e^2, R_g^2 read through the observables themselves.
+* Non-bonded energy: its absolute value on counts built by hand (uniform
+  symmetric melt n_poly chiN/4, a one-cell excess, two hand-worked cells);
+  the umbrella energy likewise.
+* Model constants: k_b, the proposal half-width and rho_bar of the melt
+  workloads as their definitions print them.
+* A sample of chains stepped alone moves as inside the whole system.
 * Umbrella fields: the exact central difference of H_nb + H_umb.
 * Placement from target fields: the exact law of the bead-0 cell, the
   quantised target weights convolved with the uniform offset (piecewise-
@@ -562,6 +571,174 @@ def pin_vertical_correlation(O):
 
 
 # ---------------------------------------------------------------------------
+# Observables and the absolute scale of the non-bonded energy.
+def _unit_vectors(rng, n):
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def pin_observables_rigid_chains(O):
+    """Rigid chains whose observables are known by hand.  A straight chain of
+    N beads with bond length l has R_e^2 = ((N-1) l)^2, R_g^2 =
+    (N^2-1) l^2 / 12 (the variance of N equally spaced points) and bond
+    energy k_b (N-1) l^2 with k_b = 3(N-1)/2.  A planar right-angle chain
+    (n1 beads along one axis, then n2 along a perpendicular one, unit bonds)
+    has R_e^2 = (n1-1)^2 + n2^2.  Chains of different lengths and directions
+    make each mean over chains differ from a mean over beads or bonds."""
+    fails = []
+    rng = np.random.default_rng(51)
+    N, n_poly = 12, 40
+    o = O(n_poly, N, 5, (3.0, 3.0, 3.0), (6, 6, 6), 0.0, 0.0, seed=1)
+    ell = rng.uniform(0.02, 0.3, size=n_poly)
+    u = _unit_vectors(rng, n_poly)
+    x0 = rng.uniform(-5.0, 8.0, size=(n_poly, 3))
+    i = np.arange(N)
+    pos = x0[:, None, :] + ell[:, None, None] * i[None, :, None] * u[:, None, :]
+    got = o.observables(pos.reshape(-1, 3))
+    kb = 1.5 * (N - 1)
+    re2 = float(np.mean(((N - 1) * ell) ** 2))
+    rg2 = float(np.mean((N * N - 1) * ell ** 2 / 12.0))
+    eb = float(kb * (N - 1) * np.sum(ell ** 2))
+    _check(fails, "straight chains R_e^2", got["Re2"], re2, 1e-12 * re2)
+    _check(fails, "straight chains R_g^2", got["Rg2"], rg2, 1e-12 * rg2)
+    _check(fails, "straight chains E_bond", got["Ebond"], eb, 1e-12 * eb)
+    # right-angle chains: n1 = 5 beads along e1, then 7 beads along e2
+    n1, n2 = 5, N - 5
+    e1 = _unit_vectors(rng, 1)[0]
+    e2 = np.cross(e1, _unit_vectors(rng, 1)[0])
+    e2 /= np.linalg.norm(e2)
+    shape = np.array([k * e1 for k in range(n1)] + [(n1 - 1) * e1 + k * e2 for k in range(1, n2 + 1)])
+    pos = x0[:2, None, :] + 0.1 * shape[None]
+    o2 = O(2, N, 5, (3.0, 3.0, 3.0), (6, 6, 6), 0.0, 0.0, seed=1)
+    got = o2.observables(pos.reshape(-1, 3))
+    re2 = 0.01 * ((n1 - 1) ** 2 + n2 ** 2)
+    # R_g^2 of the corner chain from its two arms: coordinates along e1 are
+    # 0..n1-1 then n2 times n1-1; along e2 n1 zeros then 1..n2.
+    a = np.array(list(range(n1)) + [n1 - 1] * n2, float)
+    b = np.array([0] * n1 + list(range(1, n2 + 1)), float)
+    rg2 = 0.01 * (a.var() + b.var())
+    _check(fails, "corner chain R_e^2", got["Re2"], re2, 1e-12)
+    _check(fails, "corner chain R_g^2", got["Rg2"], rg2, 1e-12)
+    _check(fails, "corner chain E_bond", got["Ebond"], 2 * kb * 0.01 * (N - 1), 1e-10)
+    return fails
+
+
+def pin_observables_equipartition(O, seeds=4):
+    """Through the observables themselves, on Gaussian chains at chiN =
+    kappaN = 0 (whose bond statistics pin_init_statistics pins in numpy):
+    each of the 3(N-1) bond coordinates carries kT/2 in the harmonic bond
+    energy, so <E_bond> per chain = 3(N-1)/2; <R_e^2> = 1; <R_g^2> =
+    (N+1)/(6N)."""
+    fails = []
+    N, n_poly = 16, 4096
+    re2, rg2, eb = [], [], []
+    for sd in range(seeds):
+        o = O(n_poly, N, 8, (4.0, 4.0, 4.0), (8, 8, 8), 0.0, 0.0, seed=61 + sd)
+        g = o.observables(o.init())
+        re2.append(g["Re2"])
+        rg2.append(g["Rg2"])
+        eb.append(g["Ebond"] / n_poly)
+    # standard errors of the mean over seeds x chains, from the Gaussian law
+    m = seeds * n_poly
+    _check(fails, "<E_bond> per chain", np.mean(eb), 1.5 * (N - 1), 5 * np.sqrt(1.5 * (N - 1) / m))
+    _check(fails, "<R_e^2>", np.mean(re2), 1.0, 5 * np.sqrt(2.0 / 3.0 / m))
+    _check(fails, "<R_g^2>", np.mean(rg2), (N + 1) / (6.0 * N), 5 * 0.5 * (N + 1) / (6.0 * N) / np.sqrt(m))
+    return fails
+
+
+def pin_energy_nb_absolute(O):
+    """H_nb = (rho_bar/N) sum_c [chiN phiA phiB + (kappaN/2)(phiA + phiB - 1)^2]
+    on counts built by hand, so that its absolute scale (the rho_bar/N
+    prefactor, the 1/2 of the compressibility term) is fixed and not only its
+    derivatives:
+    * phiA = phiB = 1/2 in every cell: H_nb = n_poly chiN / 4;
+    * one cell of a pure-A melt with k beads too many: (rho_bar/N)(kappaN/2)(k/rho_bar)^2;
+    * two cells worked out by hand, rho_bar = 4, N = 4 (prefactor 1):
+      (2, 2) -> chiN/4; (5, 1) -> phi = (5/4, 1/4), chiN 5/16 + (kappaN/2)(1/4)."""
+    fails = []
+    chiN, kappaN = 23.0, 48.0
+    # uniform symmetric melt: 64 chains of 16 beads, 4^3 cells, rho_bar = 16
+    o = O(64, 16, 8, (2.0, 2.0, 2.0), (4, 4, 4), chiN, kappaN, seed=1)
+    counts = np.full((2, o.n_c), 8, np.uint32)
+    _check(fails, "uniform phi = 1/2 melt", o.energy_nb(counts), 64 * chiN / 4, 1e-9)
+    # pure A, one cell with 4 extra beads: prefactor rho_bar/N = 1, excess 1/4
+    counts = np.zeros((2, o.n_c), np.uint32)
+    counts[0] = 16
+    counts[0, 17] = 20
+    _check(fails, "one-cell excess", o.energy_nb(counts), kappaN / 2 * (4 / 16) ** 2, 1e-12)
+    # two cells, 2 chains of 4 beads
+    o = O(2, 4, 2, (1.0, 1.0, 2.0), (1, 1, 2), chiN, kappaN, seed=1)
+    counts = np.array([[2, 5], [2, 1]], np.uint32)
+    _check(fails, "two hand-worked cells", o.energy_nb(counts), chiN / 4 + chiN * 5 / 16 + kappaN / 2 / 4, 1e-12)
+    # and the same two cells with N = 8 beads per chain, one chain: prefactor 1/2
+    o = O(1, 8, 4, (1.0, 1.0, 2.0), (1, 1, 2), chiN, kappaN, seed=1)
+    _check(fails, "two cells, prefactor 1/2", o.energy_nb(counts), 0.5 * (chiN / 4 + chiN * 5 / 16 + kappaN / 2 / 4),
+           1e-12)
+    return fails
+
+
+
+def pin_umbrella_energy_absolute(O):
+    """H_umb = (rho_bar/N)(lambdaN/2) sum_c sum_t (phi_t - phi*_t)^2 on counts
+    and targets built by hand: a pure-A melt at rho_bar = N = 16 (prefactor 1)
+    held at phi = (1, 0) everywhere, the target off by 1/2 in one A cell and by
+    1/4 in one B cell: (lambdaN/2)(1/4 + 1/16)."""
+    fails = []
+    lam = 31.0
+    o = O(64, 16, 8, (2.0, 2.0, 2.0), (4, 4, 4), 23.0, 47.0, seed=1)
+    counts = np.zeros((2, o.n_c), np.uint32)
+    counts[0] = 16
+    target = np.zeros((2, o.n_c))
+    target[0] = 1.0
+    target[0, 5] = 0.5
+    target[1, 40] = 0.25
+    _check(fails, "umbrella energy by hand", o.energy_umbrella(counts, target, lam), lam / 2 * (0.25 + 0.0625), 1e-12)
+    return fails
+
+
+def pin_params_workload_values(O):
+    """The model constants of the melt workloads, as their definitions print
+    them: k_b = 3(N-1)/2 is 46.5 for N = 32 and 94.5 for N = 64; the default
+    proposal half-width 0.5/sqrt(N-1) is 0.0898 and 0.0630 to four digits and
+    held as an FP32 number; rho_bar is 4, 2 and 4 beads per cell."""
+    fails = []
+    for (n_poly, N, L, g), kb_x, A_x, rho_x in (((512, 32, 4.0, 16), 46.5, 0.0898, 4.0),
+                                                ((131072, 32, 16.0, 128), 46.5, 0.0898, 2.0),
+                                                ((1048576, 64, 32.0, 256), 94.5, 0.0630, 4.0)):
+        o = O(n_poly, N, N // 2, (L, L, L), (g, g, g), 20.0, 50.0, seed=1)
+        kb, A, rho = o.params()
+        _check(fails, f"k_b N={N}", kb, kb_x, 0.0)
+        _check(fails, f"A N={N}", A, A_x, 5e-5)
+        if A != float(np.float32(A)):
+            fails.append(f"A N={N} is not an FP32 number")
+        _check(fails, f"rho_bar {n_poly}x{N}", rho, rho_x, 0.0)
+    return fails
+
+
+def pin_step_chains_sample(O):
+    """Chains interact only through the frozen fields within a step, so a
+    sample of chains stepped alone (by logical id) moves exactly as inside
+    the whole system, whose step the dynamics pins above fix."""
+    fails = []
+    rng = np.random.default_rng(71)
+    o = O(300, 12, 5, (2.0, 2.0, 2.0), (8, 8, 8), 20.0, 50.0, seed=13, move=0)
+    pos = o.init()
+    w = o.fields(o.density(pos))
+    for t in range(3):
+        ids = np.sort(rng.choice(o.d.n_poly, 40, replace=False)).astype(np.uint32)
+        sub = np.ascontiguousarray(pos.reshape(o.d.n_poly, -1)[ids].reshape(-1, 3))
+        _, acc_s, _, _ = o.mc_step_chains(sub, ids, w, t)
+        _, acc, _, _ = o.mc_step(pos, w, t)
+        full = pos.reshape(o.d.n_poly, -1)[ids].reshape(-1, 3)
+        if not np.array_equal(sub, full):
+            fails.append(f"step {t}: sampled chains differ from the whole step")
+        if not np.array_equal(acc_s, acc.reshape(o.d.n_poly, -1)[ids].reshape(-1)):
+            fails.append(f"step {t}: sampled decisions differ from the whole step")
+        w = o.fields(o.density(pos))
+    return fails
+
+
+# ---------------------------------------------------------------------------
 # Molecule types and boundary-zone conversion (Sec. 3.2).
 def _binomial_z(k, n, p):
     return (k - n * p) / np.sqrt(max(n * p * (1.0 - p), 1e-12))
@@ -688,6 +865,12 @@ ALL_PINS = {
     "density_bruteforce": pin_density_bruteforce,
     "fields_derivative": pin_fields_derivative,
     "structure_factor_ideal": pin_structure_factor_ideal,
+    "observables_rigid_chains": pin_observables_rigid_chains,
+    "observables_equipartition": pin_observables_equipartition,
+    "energy_nb_absolute": pin_energy_nb_absolute,
+    "umbrella_energy_absolute": pin_umbrella_energy_absolute,
+    "params_workload_values": pin_params_workload_values,
+    "step_chains_sample": pin_step_chains_sample,
     "smart_ideal_dynamics": pin_smart_ideal_dynamics,
     "smart_single_bead_field": pin_smart_single_bead_field,
     "smart_dimer_cell_pairs": pin_smart_dimer_cell_pairs,

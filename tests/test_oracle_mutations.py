@@ -77,17 +77,53 @@ MUTATIONS = [
      "conversion_type_field"),
     ("conversion counts merged across directions", "if (counts4) counts4[2 * zone + m] += 1;",
      "if (counts4) counts4[2 * zone] += 1;", "conversion_markov"),
+    ("bond energy without k_b", "out->Ebond = bond_k(d) * eb;", "out->Ebond = eb;", "observables_rigid_chains"),
+    ("R_g^2 about bead 0", "g2 += (p[3 * i + a] - cm[a]) * (p[3 * i + a] - cm[a]);",
+     "g2 += (p[3 * i + a] - p[a]) * (p[3 * i + a] - p[a]);", "observables_rigid_chains"),
+    ("R_e^2 averaged per bead", "out->Re2 = re2 / d->n_poly;", "out->Re2 = re2 / (double)n_beads(d);",
+     "observables_rigid_chains"),
+    ("end-to-end vector to the second-last bead", "double v = p[3 * (N - 1) + a] - p[a];",
+     "double v = p[3 * (N - 2) + a] - p[a];", "observables_rigid_chains"),
+    ("bond energy over one axis", "      for (int a = 0; a < 3; ++a) {\n        double b = p[3 * i + a]",
+     "      for (int a = 0; a < 1; ++a) {\n        double b = p[3 * i + a]", "observables_equipartition"),
+    # consistent mistakes in the energy and its fields together: the fields
+    # stay the energy's derivative, only its absolute value catches them
+    ("energy prefactor rho_bar and fields without 1/N",
+     [("return (double)d->n_poly / (double)nc * sum;", "return (double)n_beads(d) / (double)nc * sum;"),
+      ("  const double N = (double)d->N;\n  double excess", "  const double N = 1.0;\n  double excess")],
+     None, "energy_nb_absolute"),
+    ("compressibility 1/2 dropped in the energy and doubled in the fields",
+     [("0.5 * d->kappaN * excess * excess", "d->kappaN * excess * excess"),
+      ("*wA = (d->chiN * phiB + d->kappaN * excess) / N;", "*wA = (d->chiN * phiB + 2.0 * d->kappaN * excess) / N;"),
+      ("*wB = (d->chiN * phiA + d->kappaN * excess) / N;", "*wB = (d->chiN * phiA + 2.0 * d->kappaN * excess) / N;")],
+     None, "energy_nb_absolute"),
+    ("umbrella 1/2 dropped in the energy and doubled in the fields",
+     [("return rho_bar / (double)d->N * 0.5 * lambdaN * sum;", "return rho_bar / (double)d->N * lambdaN * sum;"),
+      ("w[c] += lambdaN * (counts[c] / rho_bar - target[c]) / (double)d->N;",
+       "w[c] += 2.0 * lambdaN * (counts[c] / rho_bar - target[c]) / (double)d->N;")],
+     None, "umbrella_energy_absolute"),
+    ("proposal width 0.5/sqrt(N)", "0.5 / std::sqrt((double)(d->N - 1));", "0.5 / std::sqrt((double)d->N);",
+     "params_workload_values"),
+    ("proposal width kept in FP64", "  return (double)(float)a;\n", "  return a;\n", "params_workload_values"),
+    ("sampled chains draw by their position in the sample",
+     "const uint32_t chain = ids ? ids[c] : (uint32_t)c;", "const uint32_t chain = (uint32_t)c;",
+     "step_chains_sample"),
 ]
 
 
 @pytest.mark.parametrize("name,old,new,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
 def test_pin_catches_mutation(name, old, new, pin):
+    # old is one anchor replaced by new, or a list of (anchor, replacement)
+    # pairs planted together (new is then None)
+    edits = old if new is None else [(old, new)]
     src = open(_SRC).read()
-    assert src.count(old) == 1, f"mutation anchor not unique/found: {old}"
+    for a, b in edits:
+        assert src.count(a) == 1, f"mutation anchor not unique/found: {a}"
+        src = src.replace(a, b)
     with tempfile.TemporaryDirectory() as td:
         cpp = os.path.join(td, "mut.cpp")
         so = os.path.join(td, "libmut.so")
-        open(cpp, "w").write(src.replace(old, new))
+        open(cpp, "w").write(src)
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", so, cpp])
         fails = pins.ALL_PINS[pin](Oracle.with_library(so))
     assert fails, f"pin {pin} did not catch the planted mistake '{name}'"
