@@ -159,7 +159,8 @@ typedef struct soma_info {
 typedef struct soma_handle soma_handle;
 
 /* Fill *opt with defaults (device -1, default sort interval, full occupancy,
- * SOMA_HIST_AUTO, graphs of 16 steps, no timing, no autotune). */
+ * SOMA_HIST_AUTO, graphs of 16 steps, no timing, no autotune).
+ * Paper: no counterpart (configuration of this library). */
 int soma_options_default(soma_options* opt);
 
 /* Create a handle for n_sys independent systems that always step together
@@ -168,31 +169,47 @@ int soma_options_default(soma_options* opt);
  * configuration on the GPU (bead 0 uniform in the box, bonds Gaussian with
  * per-axis variance 1/(3(N-1)), Philox counter (bead, chain, 0xFFFFFFFF,
  * system_id)),
- * bins it, builds the fields and sorts the chains.  opt may be NULL. */
+ * bins it, builds the fields and sorts the chains.  opt may be NULL.
+ * Paper: Sec. 2, the SOMA paragraph (an SCMF system of soft coarse-grained
+ * polymers: chain architecture, box, grid, chiN, kappaN) and Sec. 2.2 (SOMA
+ * generates its bead coordinates and validates them on the GPU at start-up).
+ * The initial Gaussian-chain configuration is a reading; the paper gives no
+ * recipe. */
 int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
                 soma_handle** out);
+/* Paper: no counterpart (resource release and error reporting of this
+ * library). */
 void soma_destroy(soma_handle* h);
 const char* soma_strerror(int code);
 int soma_last_error(const soma_handle* h);
 
 /* Enqueue n_steps MC steps of every system on `stream` (cudaStream_t, NULL =
  * the handle's stream).  Asynchronous.  Steps are numbered from the current
- * step counter; the step counter must stay below 2^32 - 1. */
+ * step counter; the step counter must stay below 2^32 - 1.
+ * Paper: Sec. 2, the SOMA paragraph (MC propagation of the beads, non-bonded
+ * interactions through quasi-instantaneous fields) and Sec. 2.2 (the two
+ * kernels one step runs: mc_polymer_iteration, the trial moves and their
+ * energies, and update_density_fields, the density fields). */
 int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream);
 
-/* Wait for the handle's work and check the device error word. */
+/* Wait for the handle's work and check the device error word.
+ * Paper: no counterpart. */
 int soma_sync(soma_handle* h, void* stream);
 
 /* Density counts of the current configuration, [2][n_cells] uint32, to host
  * or device memory per `where`.  SOMA_EINVAL for a bad sys index, a NULL out
- * or n != 2 n_cells.  Synchronises. */
+ * or n != 2 n_cells.  Synchronises.
+ * Paper: Sec. 2.2 (the particle density fields update_density_fields
+ * builds) and Sec. 3.2 (the continuum model takes over the subdomain
+ * concentrations the particle run returns). */
 int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where);
 
 /* Laterally averaged volume fractions of the current configuration along
  * one axis (0 = x, 1 = y, 2 = z): out[t * n_layers + k] = the mean over the
  * cells of layer k of n_t(c) / rho_bar, in FP64 from exact integer layer
  * sums (the profiles phi_t(z) Sec. 4 compares); n must be 2 * grid[axis]
- * (host buffer).  Synchronises. */
+ * (host buffer).  Synchronises.  Paper: Sec. 4 (the particle, continuum
+ * and coupled runs are compared by such profiles). */
 int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t n);
 
 /* Vertical correlation of the type-`type` counts of the current
@@ -201,18 +218,23 @@ int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t 
  * over all cell pairs at vertical distance dz (periodic in z, or only those
  * inside the slab with wall_z), the variance over all cells; from exact
  * integer sums, in FP64.  out has n = grid[2] entries, dz = 0 .. nz-1 (host
- * buffer); 0 where the field has no variance.  Synchronises. */
+ * buffer); 0 where the field has no variance.  Synchronises.
+ * Paper: Sec. 4 (a vertical correlation compares the runs; its formula is a
+ * reading). */
 int soma_vertical_correlation(soma_handle* h, int sys, int type, double* out, size_t n);
 
 /* Fields used by the next step, [2][n_cells] FP32 (built from the current
  * counts unless held or supplied).  SOMA_EINVAL as for soma_get_density.
- * Synchronises. */
+ * Synchronises.
+ * Paper: Sec. 2, the SOMA paragraph (the quasi-instantaneous fields of the
+ * non-bonded interactions); their functional form is a reading. */
 int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where);
 
 /* Coupling write: replace the fields of the next step by those of the given
  * volume fractions phi [2][n_cells] (FP32, host or device per `where`;
- * copied); later steps rebuild from counts.  (Sec. 3.2: the particle run is
- * handed the continuum's concentrations.)  SOMA_EINVAL for a bad sys, NULL
+ * copied); later steps rebuild from counts.
+ * Paper: Sec. 3.2 (the particle run is handed the continuum's concentration
+ * fields at each synchronisation).  SOMA_EINVAL for a bad sys, NULL
  * phi or n != 2 n_cells; SOMA_ENOTSUP on SOMA_PREC_FP64 handles.
  * Synchronises. */
 int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int where);
@@ -232,7 +254,9 @@ int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int wh
  * array from the previous counts before the move kernel (one more launch per
  * step).
  * soma_observables' Enb excludes the restraint.  SOMA_ENOTSUP on
- * SOMA_PREC_FP64 handles.  Synchronises. */
+ * SOMA_PREC_FP64 handles.  Synchronises.
+ * Paper: Sec. 3.2 (equilibration under an umbrella potential for about half
+ * a synchronisation period); the harmonic form is a reading. */
 int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n, double lambdaN, int where);
 
 /* Coupling start-up: replace system `sys`'s configuration by molecules
@@ -247,7 +271,9 @@ int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n
  * acceptance counters of every system of the handle restart (as after
  * soma_set_state).
  * SOMA_EINVAL (state kept) when the weights of bead 0's type sum to zero or
- * n != 2 n_cells; SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises. */
+ * n != 2 n_cells; SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises.
+ * Paper: Sec. 3.2 (molecules placed within half a mean end-to-end distance
+ * of target positions that reproduce the supplied fields). */
 int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int where);
 
 /* Boundary zones (Sec. 3.2): layers at the bottom and top of the box in z
@@ -269,15 +295,19 @@ int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int w
  * build every chain as type 0.
  * SOMA_EINVAL for a bad sys, n_A_alt > N, p NULL or outside [0, 1], or zone
  * widths negative, not finite or together wider than L_z; SOMA_ENOTSUP on
- * SOMA_PREC_FP64 handles and for chains longer than 64 beads.  Synchronises. */
+ * SOMA_PREC_FP64 handles and for chains longer than 64 beads.  Synchronises.
+ * Paper: Sec. 3.2 (boundary zones as transition layers converting particles
+ * to and from continuum units at rates the continuum model updates); the
+ * mechanism is a reading. */
 int soma_set_conversion(soma_handle* h, int sys, int32_t n_A_alt, double zone_lo, double zone_hi, const double* p);
 /* Conversions since the rates were last set, out[4] (host) in the order of
  * p above (zeros if conversion was never on).  SOMA_EINVAL for a bad sys or
- * NULL out.  Synchronises. */
+ * NULL out.  Synchronises.  Paper: Sec. 3.2 (the boundary fluxes the
+ * continuum model keeps track of). */
 int soma_get_conversions(soma_handle* h, int sys, uint64_t* out);
 /* Molecule type (0 or 1) of every chain in logical order, out[n_poly]
  * (host).  SOMA_EINVAL for a bad sys, NULL out or n != n_poly.
- * Synchronises. */
+ * Synchronises.  Paper: Sec. 3.2 (molecule-type conversion). */
 int soma_get_chain_types(soma_handle* h, int sys, uint8_t* out, size_t n);
 /* Set the molecule types (conversion must be on; each 0 or 1), in logical
  * order, types[n_poly] (host); the counts of the current positions and
@@ -285,29 +315,38 @@ int soma_get_chain_types(soma_handle* h, int sys, uint8_t* out, size_t n);
  * step by soma_set_density are replaced).  With soma_get_state/soma_set_state
  * this completes a checkpoint.  SOMA_EINVAL (state kept) for a bad sys,
  * NULL types, n != n_poly, a value above 1, or conversion off.
- * Synchronises. */
+ * Synchronises.  Paper: Sec. 3.2 (molecule-type conversion); the checkpoint
+ * role has no counterpart. */
 int soma_set_chain_types(soma_handle* h, int sys, const uint8_t* types, size_t n);
 
 /* Test mode: hold the fields at w [2][n_cells] (FP32, copied) for every
  * later step (w == NULL releases them and rebuilds from the current counts).
  * SOMA_EINVAL for a bad sys or n != 2 n_cells; SOMA_ENOTSUP on
- * SOMA_PREC_FP64 handles.  Synchronises. */
+ * SOMA_PREC_FP64 handles.  Synchronises.
+ * Paper: no counterpart.  It serves the reading of Sec. 2's
+ * quasi-instantaneous fields as fixed within a step: with the fields held,
+ * one bead or an AB dimer has an exact Boltzmann law that the tests check. */
 int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int where);
 
 /* Checkpoint: positions [n_beads][3] FP32 wrapped into [0, L), images
  * [n_beads][3] int16, and the step counter, in logical chain order (host or
  * device buffers per `where`; any of pos, img, step may be NULL).  Molecule
  * types, when conversion is on, are saved separately (soma_get_chain_types).
- * SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises. */
+ * SOMA_ENOTSUP on SOMA_PREC_FP64 handles.  Synchronises.
+ * Paper: no counterpart (the paper restarts a subdomain by spawning a new
+ * run, Sec. 3.2).  State out and in serve checkpoint/resume and the
+ * step-by-step parity reading: the oracle and the GPU start each compared
+ * step from the same FP32 state. */
 int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* step, int where);
 /* Restore: positions must lie in [0, L) per axis (else SOMA_EINVAL and the
  * state is kept); resets the acceptance counters of every system of the
  * handle and re-bins; the step counter is shared by all systems and must be
- * below 2^32 - 1.  Synchronises. */
+ * below 2^32 - 1.  Synchronises.  Paper: as soma_get_state. */
 int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img, uint64_t step,
                    int where);
 
 /* The same for handles created with SOMA_PREC_FP64: positions FP64 [n][3].
+ * Paper: no counterpart (the FP64 form measures what FP32 positions cost).
  * (soma_get_state / soma_set_state return SOMA_ENOTSUP on such handles.) */
 int soma_get_state64(soma_handle* h, int sys, double* pos, int16_t* img, uint64_t* step, int where);
 int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* img, uint64_t step,
@@ -315,9 +354,14 @@ int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* 
 
 /* FP64 observables of the current configuration (R_e^2, R_g^2 from
  * unwrapped positions, E_bond, E_nb from the counts, acceptance since the
- * last restore).  SOMA_EINVAL for a bad sys or NULL out.  Synchronises. */
+ * last restore).  SOMA_EINVAL for a bad sys or NULL out.  Synchronises.
+ * Paper: no counterpart; the paper defines none of these measures.  They
+ * are the standard chain and melt observables the benchmark's statistical
+ * parity and precision study use (E_nb is the H_nb of the field reading). */
 int soma_observables(soma_handle* h, int sys, soma_obs* out);
-/* Accepted-move counter only (one small device-to-host read, ordered after
+/* Paper (this and soma_copy_accepted): no counterpart; the acceptance of the
+ * trial moves of Sec. 2.2's move kernel.
+ * Accepted-move counter only (one small device-to-host read, ordered after
  * the latest soma_mc_steps on whichever stream it was given; waits for it). */
 int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted);
 /* The same count, enqueued: on `stream` (NULL = the handle's stream), after
@@ -335,35 +379,43 @@ int soma_copy_accepted(soma_handle* h, int sys, uint64_t* dst, void* stream);
  * q = 2 pi m / L at the nq integer triples m_xyz [nq][3] (host); S is FP64
  * [nq] (host).  SOMA_EINVAL for a bad sys, nq < 0 or NULL buffers (nq = 0
  * does nothing).
- * Synchronises. */
+ * Synchronises.
+ * Paper: no counterpart; the composition structure factor is the standard
+ * measure of the microphase separation the model describes (Sec. 2). */
 int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz, double* S);
 
 /* Reorder the chains of every system now (storage order only; the
- * trajectory is unchanged because random numbers follow logical ids). */
+ * trajectory is unchanged because random numbers follow logical ids).
+ * Paper: no counterpart; Sec. 2.2 names memory coalescing and data reuse as
+ * what its kernel work improved, which the cell-sorted chain order serves. */
 int soma_reorder(soma_handle* h, void* stream);
 
-/* Shape and tuning facts of one system. */
+/* Shape and tuning facts of one system.  Paper: no counterpart. */
 int soma_get_info(soma_handle* h, int sys, soma_info* out);
 
 /* With kernel_timing = 1: accumulated milliseconds and launch counts of the
  * move kernel, the separate histogram kernel, the field kernel and the
- * reorder since the last reset (ms[4], launches[4]).  Synchronises. */
+ * reorder since the last reset (ms[4], launches[4]).  Synchronises.
+ * Paper: Sec. 2.2 profiles SOMA's time per kernel the same way. */
 int soma_kernel_times(soma_handle* h, double* ms, int64_t* launches, int reset);
 
 /* Run the autotuner now (also run by the first soma_mc_steps when
  * opt.autotune = 1).  The state is saved and restored, so the trajectory is
- * unchanged.  Synchronises. */
+ * unchanged.  Synchronises.
+ * Paper: Sec. 2.2 tunes launch configurations by hand; no counterpart. */
 int soma_autotune(soma_handle* h);
 
 /* The library's device Philox4x32-10 on n counters: ctr [n][4], key [n][2],
  * out [n][4], all uint32 host buffers (a verification aid; it runs the same
- * device function the move kernel uses).  Synchronous. */
+ * device function the move kernel uses).  Synchronous.
+ * Paper: no counterpart (the generator is a reading). */
 int soma_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n);
 
 /* The standard normal deviates the smart move draws from n Philox words,
  * xi = Phi^-1(((w >> 8) + 1/2) 2^-24) as the kernel evaluates it (FP32,
  * the lower tail of either half through normcdfinvf); words and out are
- * host buffers of n entries (a verification aid).  Synchronous. */
+ * host buffers of n entries (a verification aid).  Synchronous.
+ * Paper: Sec. 2 (the bond-force-biased moves these deviates drive). */
 int soma_normal_deviates(const uint32_t* words, float* out, size_t n);
 
 /* Failure-path self-check (no counterpart in the paper, which names no
@@ -384,11 +436,18 @@ int soma_selfcheck_timeout(int device, uint64_t cycles);
  * flight, or a loop that samples S(q) often and cannot pay an allocation per
  * sample.  It needs no soma handle.
  *   pos    device FP32 [n_beads][3], wrapped into [0, L), bead = chain*N + i
- *   N, n_A chain length and A-block length (types as in soma_system_desc)
+ *   N, n_A chain length and A-block length: every chain is taken as the base
+ *          diblock A_{n_A} B_{N-n_A} (no per-chain molecule types, so after
+ *          boundary-zone conversion this differs from the handle's S(q))
  *   box    host double[3], the box edges
- *   m_xyz  host int32 [nq][3] integer q vectors, q = 2 pi m / L
+ *   m_xyz  host int32 [nq][3] integer q vectors, q = 2 pi m / L; each call
+ *          copies them to the device with cudaMemcpyAsync on `stream`
  *   S      device double [nq] output, (1/n_beads)|sum_j s_j exp(i q.r_j)|^2
  *   stream cudaStream_t (NULL = default stream); asynchronous.
+ * pos and S must be device memory of the current device with room for
+ * 3 n_beads floats and nq doubles; they are not checked (SOMA_EINVAL only
+ * for NULL pointers, n_beads < 1, N < 1, n_A outside [0, N], n_beads not a
+ * multiple of N, a box edge <= 0, or nq outside [0, 4096]).
  * Scratch (the q list and the FP64 accumulators) is a fixed static device
  * array sized for at most 4096 q vectors (about 112 KiB on every GPU that
  * loads the library, held until exit); nq > 4096 returns SOMA_EINVAL.  The

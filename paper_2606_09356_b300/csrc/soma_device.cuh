@@ -1,6 +1,6 @@
 // soma_device.cuh -- device helpers shared by the kernels of libsoma:
 // Philox4x32-10, cell indexing, periodic wrap and minimum image, the
-// Metropolis trial of one bead, image bookkeeping.
+// Metropolis trial of one bead, image bookkeeping, the S(q) accumulation.
 #pragma once
 
 #include <cstdint>
@@ -131,6 +131,64 @@ __device__ __forceinline__ void apply_wrap(int16_t* img, int64_t bead, int wrap)
     v.y += (short)(((wrap >> 2) & 3) - 1);
     v.z += (short)(((wrap >> 4) & 3) - 1);
     *p = v;
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// S(q) accumulation, shared by the handle's structure-factor kernel and the
+// allocation-free entry point.  Per bead the phase 2 pi m.r/L is taken from
+// the wrapped position (q is a lattice vector, so images drop out) as the
+// fractional part of m.(r/L) in FP32, and s_j cos, s_j sin are accumulated in
+// FP64.  Each thread sums a chunk of up to kSqChunk q vectors over its beads
+// (grid-stride), warps reduce, and lane 0 adds to out[2 q + {0, 1}].
+// frac(b, fx, fy, fz) gives bead b's coordinates over the box edges, sign(b)
+// its composition sign (+1 for A, -1 for B).
+// ---------------------------------------------------------------------------
+constexpr int kSqChunk = 8;
+
+__device__ __forceinline__ double sq_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <class Frac, class Sign>
+__device__ __forceinline__ void sq_accumulate(int64_t n, const Frac& frac, const Sign& sign,
+                                              const int32_t* __restrict__ m, int nq, double* __restrict__ out) {
+  for (int q0 = 0; q0 < nq; q0 += kSqChunk) {
+    double re[kSqChunk], im[kSqChunk];
+    float mx[kSqChunk], my[kSqChunk], mz[kSqChunk];
+#pragma unroll
+    for (int j = 0; j < kSqChunk; ++j) {
+      re[j] = im[j] = 0.0;
+      const int q = q0 + j < nq ? q0 + j : nq - 1;
+      mx[j] = (float)m[3 * q + 0];
+      my[j] = (float)m[3 * q + 1];
+      mz[j] = (float)m[3 * q + 2];
+    }
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+      float fx, fy, fz;
+      frac(b, fx, fy, fz);
+      const double s = sign(b);
+#pragma unroll
+      for (int j = 0; j < kSqChunk; ++j) {
+        float f = fmaf(mx[j], fx, fmaf(my[j], fy, mz[j] * fz));
+        f -= floorf(f);
+        float sn, cs;
+        sincospif(2.f * f, &sn, &cs);
+        re[j] += s * (double)cs;
+        im[j] += s * (double)sn;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kSqChunk; ++j) {
+      const double r = sq_warp_sum(re[j]), i = sq_warp_sum(im[j]);
+      if ((threadIdx.x & 31) == 0 && q0 + j < nq) {
+        atomicAdd(out + 2 * (q0 + j) + 0, r);
+        atomicAdd(out + 2 * (q0 + j) + 1, i);
+      }
+    }
   }
 }
 

@@ -552,50 +552,21 @@ __global__ void k_obs_cells(const SysDev* __restrict__ systems, int sys, long lo
 }
 
 // ---------------------------------------------------------------------------
-// S(q): per bead the phase 2 pi m.r/L from the wrapped position (q is a
-// lattice vector, so images drop out), evaluated in FP32 from the fractional
-// part, accumulated in FP64.  Each thread sums a chunk of up to kSqChunk q
-// vectors over its beads; warps reduce and add to out[2 * q + {0, 1}].
+// S(q) of one system of the handle (sq_accumulate in soma_device.cuh): the
+// stored wrapped coordinates, the bead's type from its chain's A block.
 // ---------------------------------------------------------------------------
-constexpr int kSqChunk = 8;
-
 __global__ void k_structure_factor(const SysDev* __restrict__ systems, int sys, int nq,
                                    const int32_t* __restrict__ m, double* __restrict__ out) {
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
-  for (int q0 = 0; q0 < nq; q0 += kSqChunk) {
-    double re[kSqChunk], im[kSqChunk];
-    float mx[kSqChunk], my[kSqChunk], mz[kSqChunk];
-#pragma unroll
-    for (int j = 0; j < kSqChunk; ++j) {
-      re[j] = im[j] = 0.0;
-      const int q = q0 + j < nq ? q0 + j : nq - 1;
-      mx[j] = (float)m[3 * q + 0];
-      my[j] = (float)m[3 * q + 1];
-      mz[j] = (float)m[3 * q + 2];
-    }
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
-      const float fx = S.x[b] * S.invL[0], fy = S.y[b] * S.invL[1], fz = S.z[b] * S.invL[2];
-      const double s = ((int)(b % S.N) < chain_n_A(S, b / S.N)) ? 1.0 : -1.0;
-#pragma unroll
-      for (int j = 0; j < kSqChunk; ++j) {
-        float f = fmaf(mx[j], fx, fmaf(my[j], fy, mz[j] * fz));
-        f -= floorf(f);
-        float sn, cs;
-        sincospif(2.f * f, &sn, &cs);
-        re[j] += s * (double)cs;
-        im[j] += s * (double)sn;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kSqChunk; ++j) {
-      const double r = warp_sum(re[j]), i = warp_sum(im[j]);
-      if ((threadIdx.x & 31) == 0 && q0 + j < nq) {
-        atomicAdd(out + 2 * (q0 + j) + 0, r);
-        atomicAdd(out + 2 * (q0 + j) + 1, i);
-      }
-    }
-  }
+  sq_accumulate(
+      S.n_b,
+      [&](int64_t b, float& fx, float& fy, float& fz) {
+        fx = S.x[b] * S.invL[0];
+        fy = S.y[b] * S.invL[1];
+        fz = S.z[b] * S.invL[2];
+      },
+      [&](int64_t b) { return ((int)(b % S.N) < chain_n_A(S, b / S.N)) ? 1.0 : -1.0; }, m, nq, out);
 }
 
 // The device Philox on explicit counters and keys (verification entry point).

@@ -26,12 +26,12 @@
 #include <mutex>
 
 #include "../../include/soma.h"
+#include "soma_device.cuh"
 
 namespace {
 
 constexpr int kNoAllocMaxQ = 4096;
 constexpr int kNoAllocMaxDevices = 64;
-constexpr int kNoAllocChunk = 8;
 
 static __device__ __align__(256) double g_sq_acc[kNoAllocMaxQ][2];   // sum of s_j cos, s_j sin
 static __device__ __align__(256) int32_t g_sq_m[kNoAllocMaxQ][3];    // the q list, copied per call
@@ -73,50 +73,19 @@ __global__ void k_sq_clear(double* __restrict__ acc, int nq) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * nq; i += gridDim.x * blockDim.x) acc[i] = 0.0;
 }
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Same arithmetic as the handle's S(q) kernel: phase 2 pi m.r/L from the
-// wrapped position in FP32 via the fractional part, FP64 accumulation; the
-// positions here are an array [n][3] in logical bead order.
+// The handle's S(q) arithmetic (sq_accumulate in soma_device.cuh) on an
+// array [n][3] of wrapped positions in logical bead order; every chain is the
+// base diblock, beads 0 .. n_A-1 A and the rest B.
 __global__ void k_sq_accumulate(const float* __restrict__ pos, int64_t n, int N, int n_A, float ilx, float ily,
                                 float ilz, const int32_t* __restrict__ m, int nq, double* __restrict__ acc) {
-  for (int q0 = 0; q0 < nq; q0 += kNoAllocChunk) {
-    double re[kNoAllocChunk], im[kNoAllocChunk];
-    float mx[kNoAllocChunk], my[kNoAllocChunk], mz[kNoAllocChunk];
-#pragma unroll
-    for (int j = 0; j < kNoAllocChunk; ++j) {
-      re[j] = im[j] = 0.0;
-      const int q = q0 + j < nq ? q0 + j : nq - 1;
-      mx[j] = (float)m[3 * q + 0];
-      my[j] = (float)m[3 * q + 1];
-      mz[j] = (float)m[3 * q + 2];
-    }
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
-      const float fx = pos[3 * b] * ilx, fy = pos[3 * b + 1] * ily, fz = pos[3 * b + 2] * ilz;
-      const double s = ((int)(b % N) < n_A) ? 1.0 : -1.0;
-#pragma unroll
-      for (int j = 0; j < kNoAllocChunk; ++j) {
-        float f = fmaf(mx[j], fx, fmaf(my[j], fy, mz[j] * fz));
-        f -= floorf(f);
-        float sn, cs;
-        sincospif(2.f * f, &sn, &cs);
-        re[j] += s * (double)cs;
-        im[j] += s * (double)sn;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < kNoAllocChunk; ++j) {
-      const double r = warp_sum_d(re[j]), i = warp_sum_d(im[j]);
-      if ((threadIdx.x & 31) == 0 && q0 + j < nq) {
-        atomicAdd(acc + 2 * (q0 + j) + 0, r);
-        atomicAdd(acc + 2 * (q0 + j) + 1, i);
-      }
-    }
-  }
+  soma::sq_accumulate(
+      n,
+      [=](int64_t b, float& fx, float& fy, float& fz) {
+        fx = pos[3 * b] * ilx;
+        fy = pos[3 * b + 1] * ily;
+        fz = pos[3 * b + 2] * ilz;
+      },
+      [=](int64_t b) { return ((int)(b % N) < n_A) ? 1.0 : -1.0; }, m, nq, acc);
 }
 
 __global__ void k_sq_finish(const double* __restrict__ acc, int nq, double inv_n, double* __restrict__ S) {

@@ -245,11 +245,33 @@ def soma_philox4x32(ctr, key):
     return out
 
 
+def _check_current_device_tensor(a, what):
+    """A torch tensor the C call reads or writes on the device: it must be a
+    CUDA tensor on the current device, where the call runs."""
+    import torch
+    if not (isinstance(a, torch.Tensor) and a.is_cuda):
+        raise ValueError(f"{what}: expected a CUDA tensor (or a raw device pointer as an int)")
+    if a.device.index != torch.cuda.current_device():
+        raise ValueError(f"{what}: tensor on cuda:{a.device.index}, but the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+
+
 def soma_structure_factor_noalloc(pos, n_beads, N, n_A, box, m, S, stream=None):
-    """S(q) of device positions ``pos`` [n,3] into device ``S`` [nq] (torch
-    tensors or raw device pointers); the library allocates nothing."""
-    box = np.ascontiguousarray(box, np.float64)
+    """S(q) of device positions ``pos`` [n_beads, 3] FP32 into device ``S``
+    [nq] FP64; the library allocates nothing.  pos and S are CUDA tensors on
+    the current device (checked for type, size, contiguity and device) or
+    raw device pointers given as ints (not checked: the caller vouches for
+    them).  Every chain is taken as the base diblock (beads 0 .. n_A-1 A)."""
+    box = np.ascontiguousarray(box, np.float64).reshape(-1)
+    if box.size != 3:
+        raise ValueError("box: expected 3 edges")
     m = np.ascontiguousarray(m, np.int32).reshape(-1, 3)
+    tensors = [(a, n, dt, what) for a, n, dt, what in ((pos, 3 * int(n_beads), np.float32, "pos"),
+                                                       (S, len(m), np.float64, "S")) if not isinstance(a, int)]
+    for a, n, dt, what in tensors:
+        _check_buffer(a, n, dt, what)
+    for a, _, _, what in tensors:
+        _check_current_device_tensor(a, what)
     p = pos if isinstance(pos, int) else pos.data_ptr()
     q = S if isinstance(S, int) else S.data_ptr()
     _check(load_library().soma_structure_factor_noalloc(ctypes.c_void_p(p), int(n_beads), int(N), int(n_A),

@@ -138,3 +138,29 @@ def test_null_arguments(lib):
     assert lib.soma_copy_accepted(None, 0, None, None) == soma.SOMA_EINVAL
     assert lib.soma_set_umbrella(None, 0, None, 0, 0.0, 0) == soma.SOMA_EINVAL
     assert lib.soma_place(None, 0, None, 0, 0) == soma.SOMA_EINVAL
+
+
+def test_noalloc_binding_checks_buffers_before_the_c_call(lib, monkeypatch):
+    # A wrongly typed, short or host-side S (or pos) is refused in the binding,
+    # before the C call could write or read past it on the device.
+    import numpy as np
+    import torch
+
+    def no_c_call():
+        raise AssertionError("the C call was reached")
+
+    monkeypatch.setattr(soma, "load_library", no_c_call)
+    m = np.ones((5, 3), np.int32)
+    pos = torch.zeros((64, 3), dtype=torch.float32)
+    cases = [
+        (pos, torch.zeros(5, dtype=torch.float32), "S"),       # FP32 instead of FP64
+        (pos, torch.zeros(4, dtype=torch.float64), "S"),       # shorter than nq
+        (pos[:32], torch.zeros(5, dtype=torch.float64), "pos"),  # fewer than 3 n_beads floats
+        (pos.t(), torch.zeros(5, dtype=torch.float64), "pos"),   # not contiguous
+        (pos, torch.zeros(5, dtype=torch.float64), "CUDA"),    # host tensors on a CPU machine
+    ]
+    for p, S, what in cases:
+        with pytest.raises(ValueError, match=what):
+            soma.soma_structure_factor_noalloc(p, 64, 32, 16, (4.0, 4.0, 4.0), m, S)
+    with pytest.raises(ValueError, match="box"):
+        soma.soma_structure_factor_noalloc(pos, 64, 32, 16, (4.0, 4.0), m, torch.zeros(5, dtype=torch.float64))
