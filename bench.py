@@ -43,6 +43,7 @@ sys.path.insert(0, ROOT)
 METRIC = "bead MC moves/s on 1xB300 and % of HBM roofline; batched vs plain speedup"
 UNIT = "moves/s"
 FLUSH_BYTES = 256 << 20
+SECOND_WORKLOAD = "melt_1048576x64"  # the other full-size melt the roofline target names
 
 
 def _dist():
@@ -507,10 +508,24 @@ def run_gpu(args):
                                    "rates 0.02-0.05): each chain's conversion decided inside the move kernel, "
                                    "whose moves and counts use the new types; L2 flushed")
 
+    # the second full-size melt (1,048,576 chains of 64, grid 256^3), timed like
+    # the headline in the same run: the HBM-roofline target covers both
+    second = None
+    if not args.no_config2 and args.workload != SECOND_WORKLOAD:
+        kw2 = rank_system_kwargs(SECOND_WORKLOAD, rank)
+        s2 = soma.System(**kw2)
+        second = bench_variant(soma, torch, SECOND_WORKLOAD, kw2, local, sptr, stream, flush, args.steps,
+                               args.warmup, hbm_peak, s2.n_beads, s2.n_cells,
+                               note="second melt workload, uniform moves, L2 flushed between timed steps "
+                                    "(positions alone exceed the L2)")
+        second = {"workload": workload_desc(SECOND_WORKLOAD, workloads.system_kwargs(SECOND_WORKLOAD)),
+                  "n_beads": s2.n_beads, "n_cells": s2.n_cells, "steps": args.steps,
+                  "algorithmic_bytes_per_step": algorithmic_bytes(s2.n_beads, s2.n_cells), **second}
+
     # batched replicas vs sequential plain runs of the same 64 systems
     batched = None
     if rank == 0 and not args.no_batched:
-        batched = bench_batched(soma, workloads, torch, sptr, stream, steps=args.batched_steps)
+        batched = bench_batched(soma, workloads, torch, sptr, stream, hbm_peak, steps=args.batched_steps)
     h.close()
 
     if rank == 0:
@@ -530,6 +545,7 @@ def run_gpu(args):
             "issue_roofline": issue_roofline(args.workload, "", move_avg, clk_summary.get("sm_max_mhz")),
             "clocks": clk_summary, "steady_state": steady, "energy": energy, "smart_moves": smart, "umbrella": umbrella,
             "boundary_zones": zones,
+            "config2": second,
             "batched": batched,
             "wall_s_timed": wall,
         }
@@ -618,11 +634,14 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
     return out
 
 
-def bench_batched(soma, workloads, torch, sptr, stream, steps=20):
+def bench_batched(soma, workloads, torch, sptr, stream, hbm_peak, steps=20):
     """Aggregate moves/s of the 64-system batch in one handle (one launch per
     kernel per step for all systems, CUDA graphs) against the same systems run
     one after another, each in its own handle with plain launches (one
-    soma_mc_steps call per system; create excluded)."""
+    soma_mc_steps call per system; create excluded).  roofline_frac: the
+    batch's own algorithmic bytes per step (24 B per bead + 32 B per cell,
+    summed over the systems) over the batched step time, against the
+    measured copy bandwidth; the batch's positions (528 MB) exceed the L2."""
     specs = workloads.batch64()
     systems = [soma.System(**{k: v for k, v in d.items() if k != "f_A"}) for d in specs]
     moves = sum(s.n_beads for s in systems) * steps
@@ -651,9 +670,14 @@ def bench_batched(soma, workloads, torch, sptr, stream, steps=20):
         torch.cuda.synchronize()
         plain_ms += a.elapsed_time(b)
         h.close()
+    step_bytes = sum(algorithmic_bytes(s.n_beads, s.n_cells) for s in systems)
+    ms_step = batched_ms / steps
     return {"value": moves / (batched_ms * 1e-3), "plain_sequential": moves / (plain_ms * 1e-3),
             "speedup": plain_ms / batched_ms, "unit": UNIT, "systems": len(systems), "steps": steps,
-            "beads": sum(s.n_beads for s in systems)}
+            "beads": sum(s.n_beads for s in systems), "cells": sum(s.n_cells for s in systems),
+            "ms_per_step": ms_step, "algorithmic_bytes_per_step": step_bytes,
+            "roofline_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm_peak,
+            "speedup_at_roofline": plain_ms / steps / (step_bytes / (hbm_peak * 1e9) * 1e3)}
 
 
 def main():
@@ -669,6 +693,7 @@ def main():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-steady", action="store_true")
     p.add_argument("--no-smart", action="store_true")
+    p.add_argument("--no-config2", action="store_true")
     p.add_argument("--no-energy", action="store_true")
     args = p.parse_args()
     if args.warmup < 3:

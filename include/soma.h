@@ -177,6 +177,49 @@ int soma_options_default(soma_options* opt);
  * recipe. */
 int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
                 soma_handle** out);
+/* Chain partition of one system: a handle that holds the logical chains
+ * [chain_begin, chain_end) of the system *sys describes (sys->n_poly is the
+ * whole system's chain count).  Chains interact only through the fields,
+ * which come from the whole system's counts, so the system splits into
+ * partitions, one per GPU, that exchange exactly one thing per step: their
+ * partial counts, summed over all partitions (soma_exchange_counts).
+ * Random numbers follow logical chain ids, so the partitions of a system,
+ * stepped with the exchange, reproduce the whole system's trajectory bit for
+ * bit.  The partition's own chains are what soma_get_state/soma_set_state
+ * (logical order, chain_begin first), soma_get_chain_types, the acceptance
+ * counters, soma_observables' R_e^2, R_g^2 and E_bond and
+ * soma_structure_factor cover; soma_observables' E_nb, soma_get_density,
+ * soma_get_fields, soma_density_profile and soma_vertical_correlation read
+ * the counts, which are the whole system's once exchanged.  rho_bar and every
+ * field constant are the whole system's.
+ * Constraints: N <= 64, SOMA_PREC_FP32 (else SOMA_ENOTSUP); opt->autotune = 0
+ * and 0 <= chain_begin < chain_end <= sys->n_poly (else SOMA_EINVAL);
+ * soma_mc_steps takes one step per call (else SOMA_EINVAL), so that the
+ * exchange can follow it; soma_autotune returns SOMA_ENOTSUP.
+ * Paper: Sec. 2.2, the SOMA scaling figure and its discussion (standalone
+ * SOMA on 4 to 16 GPUs loses efficiency to the communication of the density
+ * fields between GPUs); the chain split is the reading of that
+ * decomposition. */
+int soma_create_partition(const soma_system_desc* sys, const soma_options* opt, int32_t chain_begin,
+                          int32_t chain_end, soma_handle** out);
+
+/* The counts the next step of handle h reads: *counts receives a device
+ * pointer (the handle's GPU, owned by the handle) to uint32 [n_cells][2] --
+ * cell-major, the A and B counts of a cell side by side, cell = (ix * ny +
+ * iy) * nz + iz -- and *n_words = 2 n_cells.  For a chain partition these
+ * are its own chains' counts until the caller replaces them, in place, by
+ * their sum over all partitions of the system (for example
+ * ncclAllReduce(p, p, n_words, ncclUint32, ncclSum, comm, stream)), ordered
+ * after the call that wrote them and before the next step: after
+ * soma_create_partition, after every soma_mc_steps, and after soma_set_state,
+ * soma_place and soma_set_chain_types.  For any other one-system handle the
+ * same buffer holds the whole counts.  The pointer stays valid until the
+ * handle's next call that steps or re-bins.  Does not synchronise.
+ * SOMA_EINVAL for NULL arguments, a handle of several systems or
+ * SOMA_PREC_FP64.
+ * Paper: Sec. 2.2 (the density fields communicated between GPUs). */
+int soma_exchange_counts(soma_handle* h, uint32_t** counts, size_t* n_words);
+
 /* Paper: no counterpart (resource release and error reporting of this
  * library). */
 void soma_destroy(soma_handle* h);

@@ -58,6 +58,7 @@ struct soma_handle {
   cudaEvent_t order_ev = nullptr;  // recorded after every soma_mc_steps, on its stream
   soma_options opt{};
   int n_sys = 0;
+  bool partition = false;  // the handle holds a range of one system's chains (soma_create_partition)
   std::vector<soma_system_desc> desc;
   std::vector<SysDev> host_sys;  // device pointers and constants (fixed for the handle's life)
   SysDev* d_sys = nullptr;
@@ -592,11 +593,16 @@ void soma_destroy(soma_handle* h) {
   delete h;
 }
 
-int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt, soma_handle** out) {
-  NvtxRange nvtx_range("soma_create");
+// Create a handle for n_sys systems, or (part_end >= 0, n_sys = 1) for the
+// logical chains [part_begin, part_end) of one system.
+static int create_handle(const soma_system_desc* sys, int n_sys, const soma_options* opt, int64_t part_begin,
+                         int64_t part_end, soma_handle** out) {
   if (!out) return SOMA_EINVAL;
   *out = nullptr;
   if (!sys || n_sys < 1 || n_sys > (1 << 16)) return SOMA_EINVAL;
+  const bool partition = part_end >= 0;
+  if (partition && (n_sys != 1 || part_begin < 0 || part_end <= part_begin || part_end > sys[0].n_poly))
+    return SOMA_EINVAL;
   int64_t total_chains = 0;
   for (int s = 0; s < n_sys; ++s) {
     if (validate_desc(sys[s]) != SOMA_OK) return SOMA_EINVAL;
@@ -617,6 +623,13 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   }
   for (int s = 0; s < n_sys; ++s)
     if (sys[s].move == SOMA_MOVE_SMART && sys[s].N > 64) return SOMA_ENOTSUP;
+  if (partition) {
+    // the exchange follows every step: one step per call, no autotuner (its
+    // trial steps would run between exchanges), fields from the counts of the
+    // register move kernel (chains of at most 64 beads), FP32 positions
+    if (o.autotune) return SOMA_EINVAL;
+    if (sys[0].N > 64 || o.precision != SOMA_PREC_FP32) return SOMA_ENOTSUP;
+  }
   if (o.hist_mode < SOMA_HIST_AUTO || o.hist_mode > SOMA_HIST_SEPARATE) return SOMA_EINVAL;
   if (o.graph_steps < 0 || o.graph_steps > 4096) return SOMA_EINVAL;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SOMA_EINVAL;
@@ -625,6 +638,7 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   if (!h) return SOMA_ENOMEM;
   h->opt = o;
   h->n_sys = n_sys;
+  h->partition = partition;
   h->desc.assign(sys, sys + n_sys);
   int rc = SOMA_OK;
   auto bail = [&](int code) {
@@ -665,7 +679,8 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
     const soma_system_desc& d = sys[s];
     SysDev& S = h->host_sys[s];
     std::memset(&S, 0, sizeof(S));
-    S.n_poly = d.n_poly;
+    S.n_poly = partition ? (int32_t)(part_end - part_begin) : d.n_poly;
+    S.id_base = partition ? (uint32_t)part_begin : 0u;
     S.N = d.N;
     S.n_A = d.n_A;
     S.P = d.N <= 64 ? next_pow2((d.N + 1) / 2) : 0;
@@ -674,8 +689,9 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
     S.nz = d.grid[2];
     S.sys_index = d.system_id;
     S.wall_z = d.wall_z;
-    S.n_b = (int64_t)d.n_poly * d.N;
+    S.n_b = (int64_t)S.n_poly * d.N;
     S.n_c = (int64_t)d.grid[0] * d.grid[1] * d.grid[2];
+    S.rho_bar = (double)d.n_poly * d.N / (double)S.n_c;  // the whole system's density
     for (int a = 0; a < 3; ++a) {
       S.L[a] = (float)d.box[a];
       S.invL[a] = (float)(1.0 / d.box[a]);
@@ -685,7 +701,7 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
     S.kb = (float)(1.5 * (d.N - 1));
     S.chiN_N = (float)(d.chiN / d.N);
     S.kappaN_N = (float)(d.kappaN / d.N);
-    S.inv_rho = (float)((double)S.n_c / (double)S.n_b);
+    S.inv_rho = (float)(1.0 / S.rho_bar);
     uint32_t k0 = (uint32_t)(d.seed & 0xFFFFFFFFu), k1 = (uint32_t)(d.seed >> 32);
     for (int r = 0; r < 10; ++r) {
       S.rk[r][0] = k0;
@@ -700,19 +716,19 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
     }
     // field differences of the FP64 form: (chiN dn_other + kappaN dn_total) / (N rho_bar)
     {
-      const double rho = (double)S.n_b / (double)S.n_c;
+      const double rho = S.rho_bar;
       S.chiN64 = d.chiN / d.N / rho;
       S.kappaN64 = d.kappaN / d.N / rho;
     }
     S.chain_base = chain_base;
-    chain_base += d.n_poly;
+    chain_base += S.n_poly;
     S.acc_first = s * h->acc_per_sys;
     S.acc_count = h->acc_per_sys;
     h->max_nb = std::max<int64_t>(h->max_nb, S.n_b);
     h->max_nc = std::max<int64_t>(h->max_nc, S.n_c);
 
     // bulk copies read whole 16-byte granules: pad position and id arrays
-    const size_t nb = (size_t)S.n_b + 8, nc = (size_t)S.n_c, np = (size_t)d.n_poly + 8;
+    const size_t nb = (size_t)S.n_b + 8, nc = (size_t)S.n_c, np = (size_t)S.n_poly + 8;
     S.x = (float*)dev_alloc(h, nb * 4);
     S.y = (float*)dev_alloc(h, nb * 4);
     S.z = (float*)dev_alloc(h, nb * 4);
@@ -791,6 +807,27 @@ int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt,
   return SOMA_OK;
 }
 
+int soma_create(const soma_system_desc* sys, int n_sys, const soma_options* opt, soma_handle** out) {
+  NvtxRange nvtx_range("soma_create");
+  return create_handle(sys, n_sys, opt, 0, -1, out);
+}
+
+int soma_create_partition(const soma_system_desc* sys, const soma_options* opt, int32_t chain_begin,
+                          int32_t chain_end, soma_handle** out) {
+  NvtxRange nvtx_range("soma_create_partition");
+  return create_handle(sys, 1, opt, chain_begin, chain_end, out);
+}
+
+int soma_exchange_counts(soma_handle* h, uint32_t** counts, size_t* n_words) {
+  int rc = check_live(h);
+  if (rc) return rc;
+  if (!counts || !n_words || h->f64 || h->n_sys != 1) return SOMA_EINVAL;
+  const SysDev& S = h->host_sys[0];
+  *counts = count_buffer(S.counts, S.n_c, (long long)h->step - 1);
+  *n_words = 2 * (size_t)S.n_c;
+  return SOMA_OK;
+}
+
 int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
   NvtxRange nvtx_range("soma_mc_steps");
   int rc = check_live(h);
@@ -798,6 +835,7 @@ int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
   if (n_steps < 0) return SOMA_EINVAL;
   if (h->step + (uint64_t)n_steps >= (uint64_t)kInitStep) return SOMA_EINVAL;
   if (n_steps == 0) return SOMA_OK;
+  if (h->partition && n_steps != 1) return SOMA_EINVAL;  // the counts are exchanged after every step
   if (!h->tuned) {
     rc = soma_autotune(h);
     if (rc) return rc;
@@ -898,7 +936,7 @@ int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t 
   CK(cudaMemcpyAsync(sums.data(), d_sum, sizeof(unsigned long long) * sums.size(), cudaMemcpyDeviceToHost,
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  const double rho_bar = (double)S.n_b / (double)S.n_c;
+  const double rho_bar = S.rho_bar;
   const double per_layer = (double)(S.n_c / layers);
   for (int k = 0; k < layers; ++k)
     for (int t = 0; t < 2; ++t) out[(size_t)t * layers + k] = (double)sums[2 * (size_t)k + t] / rho_bar / per_layer;
@@ -1156,10 +1194,10 @@ int soma_observables(soma_handle* h, int sys, soma_obs* out) {
   out->accepted = acc;
   out->attempted = (uint64_t)S.n_b * (h->step - h->acc_since);
   out->acc = out->attempted ? (double)acc / (double)out->attempted : 0.0;
-  out->Re2 = r[0] / d.n_poly;
-  out->Rg2 = r[1] / d.n_poly;
+  out->Re2 = r[0] / S.n_poly;  // over the handle's chains (a partition: its own)
+  out->Rg2 = r[1] / S.n_poly;
   out->Ebond = 1.5 * (d.N - 1) * r[2];
-  out->Enb = (double)d.n_poly / (double)S.n_c * r[3];
+  out->Enb = (double)d.n_poly / (double)S.n_c * r[3];  // rho_bar / N of the whole system
   return SOMA_OK;
 }
 
@@ -1407,7 +1445,7 @@ int soma_get_info(soma_handle* h, int sys, soma_info* out) {
   out->n_cells = S.n_c;
   out->k_b = S.kb;
   out->A = S.A;
-  out->rho_bar = (double)S.n_b / (double)S.n_c;
+  out->rho_bar = S.rho_bar;
   out->lanes_per_chain = S.P;
   out->ctas_per_sm = h->ctas_per_sm;
   out->sort_interval = h->sort_interval;
@@ -1448,6 +1486,7 @@ int soma_autotune(soma_handle* h) {
   NvtxRange nvtx_range("soma_autotune");
   int rc = check_live(h);
   if (rc) return rc;
+  if (h->partition) return SOMA_ENOTSUP;  // its trial steps would run between count exchanges
   h->tuned = true;
   if ((rc = sync_all(h))) return rc;
   const uint64_t step0 = h->step;

@@ -41,6 +41,9 @@ struct alignas(16) SysDev {
   unsigned long long* acc;      // accepted moves, one counter per move tile
   int32_t acc_first, acc_count; // this system's range of accepted-move slots
   int64_t chain_base;           // first chain of this system in the global chain order
+  uint32_t id_base;             // logical id of this handle's first chain (a chain partition; else 0)
+  int32_t pad_id;
+  double rho_bar;               // beads per cell of the whole system (a partition holds only its share)
   // FP64-position form (precision reference): wrapped FP64 positions
   double* x64;
   double* y64;

@@ -286,10 +286,11 @@ __global__ void k_set_step(unsigned long long* counters, int n_sys, unsigned lon
 __device__ void grow_chain(const SysDev& S, int64_t c, double X, double Y, double Z) {
   const int N = S.N;
   const double sigma = N > 1 ? sqrt(1.0 / (3.0 * (N - 1))) : 0.0;
-  S.chain_id[c] = (uint32_t)c;
+  const uint32_t id = (uint32_t)c + S.id_base;  // logical chain id
+  S.chain_id[c] = id;
   for (int i = 0; i < N; ++i) {
     if (i > 0) {
-      const uint4 r = philox10(make_uint4((uint32_t)i, (uint32_t)c, kInitStep, (uint32_t)S.sys_index), S.rk);
+      const uint4 r = philox10(make_uint4((uint32_t)i, id, kInitStep, (uint32_t)S.sys_index), S.rk);
       const double m1 = sqrt(-2.0 * log(((double)(r.x >> 8) + 0.5) * 0x1p-24));
       const double m2 = sqrt(-2.0 * log(((double)(r.z >> 8) + 0.5) * 0x1p-24));
       double s1, c1, s2, c2;
@@ -330,7 +331,7 @@ __global__ void k_init(const SysDev* __restrict__ systems, int sys) {
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 r = philox10(make_uint4(0u, (uint32_t)c, kInitStep, (uint32_t)S.sys_index), S.rk);
+    const uint4 r = philox10(make_uint4(0u, (uint32_t)c + S.id_base, kInitStep, (uint32_t)S.sys_index), S.rk);
     grow_chain(S, c, (double)S.L[0] * ((double)(r.x >> 8) * 0x1p-24),
                (double)S.L[1] * ((double)(r.y >> 8) * 0x1p-24), (double)S.L[2] * ((double)(r.z >> 8) * 0x1p-24));
   }
@@ -360,9 +361,10 @@ __global__ void k_place(const SysDev* __restrict__ systems, int sys, const unsig
   load_sys(&S, systems + sys);
   const double h = 0.5 / sqrt(3.0);  // correctly rounded, as on the host
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
-    const uint4 r0 = philox10(make_uint4(0u, (uint32_t)c, kPlaceStep, (uint32_t)S.sys_index), S.rk);
-    const uint4 r1 = philox10(make_uint4(1u, (uint32_t)c, kPlaceStep, (uint32_t)S.sys_index), S.rk);
-    const uint4 r2 = philox10(make_uint4(2u, (uint32_t)c, kPlaceStep, (uint32_t)S.sys_index), S.rk);
+    const uint32_t id = (uint32_t)c + S.id_base;  // logical chain id
+    const uint4 r0 = philox10(make_uint4(0u, id, kPlaceStep, (uint32_t)S.sys_index), S.rk);
+    const uint4 r1 = philox10(make_uint4(1u, id, kPlaceStep, (uint32_t)S.sys_index), S.rk);
+    const uint4 r2 = philox10(make_uint4(2u, id, kPlaceStep, (uint32_t)S.sys_index), S.rk);
     const unsigned long long r = ((unsigned long long)r0.y << 32) | r0.x;
     const unsigned long long k = __umul64hi(r, Q);
     int64_t lo = 0, hi = S.n_c - 1;  // first cell whose running sum exceeds k
@@ -391,7 +393,7 @@ __global__ void k_gather_state(const SysDev* __restrict__ systems, int sys, floa
   load_sys(&S, systems + sys);
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
     const int64_t slot = b / S.N, i = b % S.N;
-    const int64_t lb = (int64_t)(S.chain_id[slot] & kIdMask) * S.N + i;
+    const int64_t lb = (int64_t)((S.chain_id[slot] & kIdMask) - S.id_base) * S.N + i;
     pos[3 * lb + 0] = S.x[b];
     pos[3 * lb + 1] = S.y[b];
     pos[3 * lb + 2] = S.z[b];
@@ -408,7 +410,7 @@ __global__ void k_scatter_state(const SysDev* __restrict__ systems, int sys, con
   load_sys(&S, systems + sys);
   for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < S.n_b; b += (int64_t)gridDim.x * blockDim.x) {
     const int64_t slot = b / S.N, i = b % S.N;
-    const int64_t lb = (int64_t)(S.chain_id[slot] & kIdMask) * S.N + i;
+    const int64_t lb = (int64_t)((S.chain_id[slot] & kIdMask) - S.id_base) * S.N + i;
     S.x[b] = pos[3 * lb + 0];
     S.y[b] = pos[3 * lb + 1];
     S.z[b] = pos[3 * lb + 2];
@@ -422,7 +424,7 @@ __global__ void k_get_types(const SysDev* __restrict__ systems, int sys, uint8_t
   load_sys(&S, systems + sys);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t word = S.chain_id[c];
-    out[word & kIdMask] = (word & kTypeBit) ? 1 : 0;
+    out[(word & kIdMask) - S.id_base] = (word & kTypeBit) ? 1 : 0;
   }
 }
 
@@ -432,7 +434,7 @@ __global__ void k_set_types(const SysDev* __restrict__ systems, int sys, const u
   load_sys(&S, systems + sys);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_poly; c += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t id = S.chain_id[c] & kIdMask;
-    S.chain_id[c] = id | ((types && types[id]) ? kTypeBit : 0u);
+    S.chain_id[c] = id | ((types && types[id - S.id_base]) ? kTypeBit : 0u);
   }
 }
 
@@ -533,7 +535,7 @@ __global__ void k_obs_cells(const SysDev* __restrict__ systems, int sys, long lo
   load_sys(&S, systems + sys);
   // counts of the current configuration sit in buffer (steps_done - 1) mod 3
   const uint32_t* cur = count_buffer(S.counts, S.n_c, t_done - 1);
-  const double rho = (double)S.n_b / (double)S.n_c;
+  const double rho = S.rho_bar;
   const double chiN = (double)S.chiN_N * S.N, kappaN = (double)S.kappaN_N * S.N;
   double f = 0;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < S.n_c; c += (int64_t)gridDim.x * blockDim.x) {

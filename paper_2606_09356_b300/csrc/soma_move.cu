@@ -122,7 +122,11 @@ __device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15
 // program order before the warp releases the stage to the producer.  (A
 // plain load may legally be re-executed later by the compiler to save a
 // register, and after the release the stage may already hold the next tile,
-// written by the copy engine outside the compiler's view.)
+// written by the copy engine outside the compiler's view.)  Keep them
+// volatile: an earlier build with plain stage loads under a tighter register
+// cap gave trajectories that changed with the number of resident CTAs per SM
+// -- a stage value re-read after the early release, once the producer had
+// refilled the stage, fits that symptom exactly.
 __device__ __forceinline__ float2 lds2(const float* p) {
   float2 v;
   asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(smem_u32(p)) : "memory");
@@ -725,14 +729,17 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3)
   }
 
   const long long tl = r.get();
+  // the step's count buffers, as indices (each system's buffers sit at the
+  // same positions within its own block of three)
+  const int prev_buf = count_buffer_index(tl - 1), cur_buf = count_buffer_index(tl);
   int it = 0;
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
     const int s = it % kStages;
     if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, err)) break;
     const int sys = (int)lds1(&stage[s].sys);  // the producer's search, not one per thread
     const MoveArgs& a = p.sys[sys];
-    const uint2* prev = reinterpret_cast<const uint2*>(count_buffer(a.counts, a.n_c, tl - 1));
-    uint32_t* cur = count_buffer(a.counts, a.n_c, tl);
+    const uint2* prev = reinterpret_cast<const uint2*>(a.counts) + (int64_t)prev_buf * a.n_c;
+    uint32_t* cur = a.counts + (int64_t)cur_buf * 2 * a.n_c;
     const int lt = tile - p.tile_start[sys];
     unsigned n;
     if (a.conv)

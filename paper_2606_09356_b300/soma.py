@@ -46,7 +46,7 @@ EXPORTS = (
     "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
     "soma_philox4x32", "soma_structure_factor_noalloc", "soma_selfcheck_timeout",
     "soma_normal_deviates", "soma_set_conversion", "soma_get_conversions", "soma_get_chain_types",
-    "soma_set_chain_types",
+    "soma_set_chain_types", "soma_create_partition", "soma_exchange_counts",
 )
 
 
@@ -146,6 +146,9 @@ def load_library(path=None):
     L.soma_get_conversions.argtypes = [vp, i32, vp]
     L.soma_get_chain_types.argtypes = [vp, i32, vp, sz]
     L.soma_set_chain_types.argtypes = [vp, i32, vp, sz]
+    L.soma_create_partition.argtypes = [ctypes.POINTER(soma_system_desc), ctypes.POINTER(soma_options),
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vp)]
+    L.soma_exchange_counts.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(sz)]
     for name in EXPORTS:
         if name not in ("soma_destroy", "soma_strerror"):
             getattr(L, name).restype = ctypes.c_int
@@ -226,6 +229,23 @@ def soma_create(descs, options=None):
     rc = L.soma_create(arr, len(descs), ctypes.byref(options) if options is not None else None, ctypes.byref(h))
     _check(rc, "soma_create")
     return h
+
+
+def soma_create_partition(desc, chain_begin, chain_end, options=None):
+    """A handle for the logical chains [chain_begin, chain_end) of one system."""
+    L = load_library()
+    h = ctypes.c_void_p()
+    rc = L.soma_create_partition(ctypes.byref(desc), ctypes.byref(options) if options is not None else None,
+                                 int(chain_begin), int(chain_end), ctypes.byref(h))
+    _check(rc, "soma_create_partition")
+    return h
+
+
+def soma_exchange_counts(h):
+    """(device pointer, number of uint32 words) of the counts the next step reads."""
+    p, n = ctypes.c_void_p(), ctypes.c_size_t()
+    _check(load_library().soma_exchange_counts(h, ctypes.byref(p), ctypes.byref(n)), "soma_exchange_counts")
+    return p.value, n.value
 
 
 def soma_destroy(h):
@@ -331,10 +351,26 @@ class System:
         return d
 
 
-class Handle:
-    """Owns a soma_handle for a list of systems that step together."""
+class PartitionOf(System):
+    """The logical chains [begin, end) of a system: sizes are the partition's
+    (n_poly = end - begin), the descriptor the whole system's."""
 
-    def __init__(self, systems, **options):
+    def __init__(self, system, begin, end):
+        super().__init__(system.n_poly, system.N, system.n_A, system.box, system.grid, system.chiN,
+                         system.kappaN, system.A, system.seed, system.system_id, system.move, system.wall_z)
+        self.whole, self.begin, self.end = system, int(begin), int(end)
+        self.n_poly = self.end - self.begin
+
+    def desc(self):
+        return self.whole.desc()
+
+
+class Handle:
+    """Owns a soma_handle for a list of systems that step together, or, with
+    partition=(begin, end), for the logical chains [begin, end) of one system
+    (soma_create_partition)."""
+
+    def __init__(self, systems, partition=None, **options):
         if isinstance(systems, System):
             systems = [systems]
         self.systems = list(systems)
@@ -345,7 +381,13 @@ class Handle:
                 raise TypeError(f"unknown soma option {k}")
             setattr(o, k, v)
         self.precision = o.precision
-        self.h = soma_create([s.desc() for s in self.systems], o)
+        if partition is not None:
+            if len(self.systems) != 1:
+                raise ValueError("a partition holds chains of one system")
+            self.systems = [PartitionOf(self.systems[0], *partition)]
+            self.h = soma_create_partition(self.systems[0].desc(), partition[0], partition[1], o)
+        else:
+            self.h = soma_create([s.desc() for s in self.systems], o)
 
     def close(self):
         if self.h:
@@ -367,6 +409,11 @@ class Handle:
     # -- stepping --------------------------------------------------------
     def mc_steps(self, n, stream=None):
         soma_mc_steps(self.h, n, stream)
+
+    def exchange_counts(self):
+        """(device pointer, uint32 words) of the counts the next step reads
+        (a partition: to be summed over all partitions before that step)."""
+        return soma_exchange_counts(self.h)
 
     def sync(self, stream=None):
         soma_sync(self.h, stream)

@@ -54,3 +54,7 @@ def test_headline_line():
     assert "l2" in d["config"] and d["dtype"] == "f32" and d["data"] == "synthetic"
     st = d["step_ms_stats"]
     assert 0 < st["min"] <= st["median"] <= st["max"] and st["min"] <= d["ms_per_step"] <= st["max"]
+    c2 = d["config2"]  # the second full-size melt, timed in the same run
+    assert c2["n_beads"] == 1048576 * 64 and c2["n_cells"] == 256 ** 3 and c2["steps"] == 5
+    assert abs(c2["frac"] - c2["achieved_gbs"] / r["peak"]) < 1e-9 and 0 < c2["frac"] < 1.5
+    assert c2["value"] > 0 and c2["move_ms"] <= c2["ms_per_step"] * 1.05
