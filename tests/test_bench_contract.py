@@ -58,3 +58,17 @@ def test_headline_line():
     assert c2["n_beads"] == 1048576 * 64 and c2["n_cells"] == 256 ** 3 and c2["steps"] == 5
     assert abs(c2["frac"] - c2["achieved_gbs"] / r["peak"]) < 1e-9 and 0 < c2["frac"] < 1.5
     assert c2["value"] > 0 and c2["move_ms"] <= c2["ms_per_step"] * 1.05
+
+
+@pytest.mark.gpu
+def test_partitioned_line_at_one_rank():
+    # the chain-partition mode at N = 1: the whole system as one partition,
+    # the exchange a no-op; its line keeps the contract's keys
+    d = _run(["--partition", "--partition-workload", "melt_131072x32", "--steps", "5", "--warmup", "3"],
+             timeout=900)
+    for k in BASE_KEYS + ("roofline", "gpu_launches", "clocks"):
+        assert k in d, k
+    assert d["scaling"] == "strong" and d["n_gpus"] == 1 and d["value"] > 0
+    assert d["config"]["n_beads"] == 131072 * 32 and d["gpu_launches"] == 5
+    r = d["roofline"]
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-9 and 0 < r["frac"] < 1.5
