@@ -50,6 +50,10 @@ constexpr int kConsumerWarps = 8;
 constexpr int kStages = 4;
 constexpr int kTileBeads = kConsumerWarps * 64;   // a warp holds at most 64 beads
 constexpr int kTileChains = kConsumerWarps * 32;  // at most 32 chains per warp (P = 1)
+// A tile's bulk copies start at chain c0 = tile * kConsumerWarps * 32/P and
+// bead c0 * N; both addresses are 16-byte aligned for every P and N only
+// when the chains per tile are a multiple of 4 (P = 32: kConsumerWarps).
+static_assert(kConsumerWarps % 4 == 0, "tile copies would start off a 16-byte boundary");
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz: a wait that long is an error
 constexpr float kLog2e = 1.4426950408889634f;
 
