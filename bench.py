@@ -381,7 +381,10 @@ def run_gpu(args):
     # timings are distorted (serialised, cache-flushed launches), so profiling
     # runs pass --no-autotune and get the default launch shape, which is what
     # the autotuner picks on this workload outside a profiler
-    h = soma.Handle(system, device=local, kernel_timing=1, graph_steps=0, autotune=0 if args.no_autotune else 1)
+    # kernel_timing = 0: no timing events of the library's own inside the step
+    # windows; a step is one launch of the move kernel (the launch counts
+    # below confirm it), so the window is that launch's duration
+    h = soma.Handle(system, device=local, kernel_timing=0, graph_steps=0, autotune=0 if args.no_autotune else 1)
     sptr = stream.cuda_stream
 
     def one_step():
@@ -417,15 +420,23 @@ def run_gpu(args):
     # used) per step, and three per chain reorder (keys, permute, copy back)
     launches = kt["move"][1] + kt["bin"][1] + kt["field"][1] + sorts * 3
 
-    # dominant kernel: the move kernel (its average launch duration)
-    mv_ms, mv_n = kt["move"]
-    fd_ms, fd_n = kt["field"]
-    move_avg = mv_ms / max(1, mv_n)
+    # dominant kernel: the move kernel, its average launch duration = the
+    # step windows' mean when every step is exactly one move launch
+    mv_n = kt["move"][1]
+    one_launch = mv_n == args.steps and launches == args.steps
+    move_avg = total_ms / args.steps if one_launch else None
+    if move_avg is None:  # a reorder or a separate histogram launch inside a window:
+        # time the move kernel alone with the library's events, same shape
+        move_avg = move_kernel_ms(soma, torch, system, local, sptr, stream, flush, args.steps, args.warmup,
+                                  info_after)
     achieved = move_kernel_bytes(n_b, n_c) / (move_avg * 1e-3) / 1e9
     traffic = _profiled_traffic(args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "k_move", "move_ms": move_avg, "field_ms": (fd_ms / fd_n) if fd_n else None,
+                "kernel": "k_move", "move_ms": move_avg,
+                "timing": ("CUDA events around each step's single launch of the move kernel, on its stream"
+                           if one_launch else "the library's CUDA events around each move launch, a separate "
+                           "pass in the same launch shape"),
                 "step_frac": algorithmic_bytes(n_b, n_c) * args.steps / (total_ms * 1e-3) / 1e9 / hbm_peak}
 
     # steady state without flushes: CUDA-graph replay of many steps (L2-warm)
@@ -660,14 +671,34 @@ def measure_energy(soma, torch, c, rank, local, sptr, stream, n_b, seconds=2.0):
             "note": "NVML total-energy counter over CUDA-graph replays (L2 warm), whole GPU board"}
 
 
+def move_kernel_ms(soma, torch, system, device, sptr, stream, flush, steps, warmup, info):
+    """Average move-kernel launch time by the library's CUDA events around
+    each launch, in the given launch shape (ctas_per_sm, hist_mode), L2
+    flushed before every step."""
+    h = soma.Handle(system, device=device, kernel_timing=1, graph_steps=0, autotune=0,
+                    ctas_per_sm=info["ctas_per_sm"], hist_mode=info["hist_mode"])
+    warm_up(torch, stream, flush, lambda: h.mc_steps(1, stream=sptr), warmup)
+    h.kernel_times(reset=True)
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+        h.mc_steps(1, stream=sptr)
+    torch.cuda.synchronize()
+    ms, n = h.kernel_times(reset=True)["move"]
+    h.close()
+    return ms / max(1, n)
+
+
 def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps, warmup, hbm_peak, n_b, n_c,
                   move=0, umbrella=0.0, wall_z=0, conversion=None, note="", sm_max_mhz=None):
     """The workload with another trial move, the umbrella restraint, or walls
     and boundary-zone conversion: moves/s over flushed steps and the move
     kernel's fraction of the HBM roofline (same algorithmic bytes per step as
     the headline)."""
-    h = soma.Handle(soma.System(**{**kw, "move": move, "wall_z": wall_z}), device=device, kernel_timing=1,
-                    graph_steps=0, autotune=1)
+    # one launch per step unless the umbrella's field pass precedes it: then
+    # the library's events time the two kernels apart
+    h = soma.Handle(soma.System(**{**kw, "move": move, "wall_z": wall_z}), device=device,
+                    kernel_timing=1 if umbrella else 0, graph_steps=0, autotune=1)
     if conversion:
         h.set_conversion(*conversion)
     if umbrella:
@@ -693,10 +724,17 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
     kt = h.kernel_times(reset=True)
     acc = (h.accepted() - a0) / (steps * n_b)
     conv_n = int(h.conversions().sum()) if conversion else 0
+    info = h.info()
     h.close()
     mv_ms, mv_n = kt["move"]
     fd_ms, fd_n = kt["field"]
-    move_avg = mv_ms / max(1, mv_n)
+    if umbrella:
+        move_avg = mv_ms / max(1, mv_n)
+    elif mv_n == steps and kt["bin"][1] == 0 and kt["reorder"][1] == 0:
+        move_avg = total_ms / steps  # each window is one launch of the move kernel
+    else:
+        move_avg = move_kernel_ms(soma, torch, soma.System(**{**kw, "move": move, "wall_z": wall_z}), device, sptr,
+                                  stream, flush, steps, warmup, info)
     achieved = move_kernel_bytes(n_b, n_c) / (move_avg * 1e-3) / 1e9
     out = {"value": steps * n_b / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / steps,
            "move_ms": move_avg, "achieved_gbs": achieved, "frac": achieved / hbm_peak, "acceptance": acc,

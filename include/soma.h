@@ -436,9 +436,11 @@ int soma_reorder(soma_handle* h, void* stream);
 /* Shape and tuning facts of one system.  Paper: no counterpart. */
 int soma_get_info(soma_handle* h, int sys, soma_info* out);
 
-/* With kernel_timing = 1: accumulated milliseconds and launch counts of the
- * move kernel, the separate histogram kernel, the field kernel and the
- * reorder since the last reset (ms[4], launches[4]).  Synchronises.
+/* Launch counts of the move kernel, the separate histogram kernel, the field
+ * kernel and the reorder since the last reset (launches[4]; plain launches --
+ * launches replayed from a CUDA graph are not counted), and, with
+ * kernel_timing = 1, their accumulated milliseconds (ms[4]; 0 otherwise).
+ * Synchronises when timings are pending.
  * Paper: Sec. 2.2 profiles SOMA's time per kernel the same way. */
 int soma_kernel_times(soma_handle* h, double* ms, int64_t* launches, int reset);
 

@@ -41,6 +41,7 @@ enum { T_MOVE = 0, T_BIN = 1, T_FIELD = 2, T_SORT = 3 };
 struct TimedEvent {
   cudaEvent_t a, b;
   int kind;
+  bool timed;  // a and b were created and recorded
 };
 
 int next_pow2(int v) {
@@ -327,16 +328,24 @@ void drop_graph(soma_handle* h) {
   }
 }
 
-void begin_timed(soma_handle* h, cudaStream_t s, TimedEvent& te, int kind) {
+// Around every launch of the library's kernels: CUDA events when the handle
+// times its kernels (kernel_timing), and the launch count of its kind unless
+// the launch is being captured into a graph (a captured launch runs once per
+// replay, which the host does not see).
+void begin_timed(soma_handle* h, cudaStream_t s, TimedEvent& te, int kind, bool timing) {
   te.kind = kind;
+  te.timed = timing;
+  if (!timing) return;
   cudaEventCreate(&te.a);
   cudaEventCreate(&te.b);
   cudaEventRecord(te.a, s);
 }
-void end_timed(soma_handle* h, cudaStream_t s, TimedEvent& te) {
-  cudaEventRecord(te.b, s);
-  h->pending.push_back(te);
-  h->launches[te.kind] += 1;
+void end_timed(soma_handle* h, cudaStream_t s, TimedEvent& te, bool count) {
+  if (te.timed) {
+    cudaEventRecord(te.b, s);
+    h->pending.push_back(te);
+  }
+  if (count) h->launches[te.kind] += 1;
 }
 
 // Step i of a sequence: the fixed number t0 + i (plain launches) or the
@@ -351,19 +360,19 @@ int enqueue_aux(soma_handle* h, cudaStream_t s, int sys, StepRef r, bool timing,
   const SysDev& S = h->host_sys[sys];
   TimedEvent te;
   if (S.P == 0 && !moved) {
-    if (timing) begin_timed(h, s, te, T_MOVE);
+    begin_timed(h, s, te, T_MOVE, timing);
     CK(launch_move_generic(h->d_sys, sys, S.n_poly, S.N, r, h->sm_count, s));
-    if (timing) end_timed(h, s, te);
+    end_timed(h, s, te, !r.use_counter);
   }
   if (S.P == 0 || h->hist_mode == SOMA_HIST_SEPARATE) {
-    if (timing) begin_timed(h, s, te, T_BIN);
+    begin_timed(h, s, te, T_BIN, timing);
     CK(launch_bin(h->d_sys, sys, S.n_b, r, h->sm_count, s));
-    if (timing) end_timed(h, s, te);
+    end_timed(h, s, te, !r.use_counter);
   }
   if (S.P == 0) {
-    if (timing) begin_timed(h, s, te, T_FIELD);
+    begin_timed(h, s, te, T_FIELD, timing);
     CK(launch_field(h->fargs[sys], r, 1, s));
-    if (timing) end_timed(h, s, te);
+    end_timed(h, s, te, !r.use_counter);
   }
   return SOMA_OK;
 }
@@ -377,9 +386,9 @@ int enqueue_umbrella_fields(soma_handle* h, cudaStream_t s, int sys, bool graph,
   if (!S.P || !S.umbrella || S.frozen || (i == 0 && h->phi_pending[sys])) return SOMA_OK;
   TimedEvent te;
   const bool timing = h->opt.kernel_timing != 0;
-  if (timing) begin_timed(h, s, te, T_FIELD);
+  begin_timed(h, s, te, T_FIELD, timing);
   CK(launch_field(h->fargs[sys], step_ref(h, sys, graph, t0, i - 1), 0, s));
-  if (timing) end_timed(h, s, te);
+  end_timed(h, s, te, !graph);
   return SOMA_OK;
 }
 
@@ -410,20 +419,20 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
         TimedEvent te;
         for (int m = 0; m < b->n_sys; ++m)
           if ((rc = enqueue_umbrella_fields(h, s, h->batch_members[g][m], graph, t0, i))) return rc;
-        if (timing) begin_timed(h, s, te, T_MOVE);
+        begin_timed(h, s, te, T_MOVE, timing);
         // one wave: at most as many CTAs as this specialisation keeps resident
         const int fit = h->max_ctas_batch_kind[b->sys[0].smart ? 1 : 0][b->sys[0].wall_z ? 1 : 0];
         CK(launch_move_batch(*b, move_grid(h, b->tile_start[b->n_sys], fit),
                              step_ref(h, 0, graph, t0, i), s));
-        if (timing) end_timed(h, s, te);
+        end_timed(h, s, te, !graph);
       }
       for (int sys = 0; sys < h->n_sys; ++sys)
         if ((rc = enqueue_aux(h, s, sys, step_ref(h, sys, graph, t0, i), timing, false))) return rc;
     } else if (h->f64) {
       TimedEvent te;
-      if (timing) begin_timed(h, s, te, T_MOVE);
+      begin_timed(h, s, te, T_MOVE, timing);
       CK(launch_move64(h->d_sys, 0, step_ref(h, 0, graph, t0, i), h->sm_count, s));
-      if (timing) end_timed(h, s, te);
+      end_timed(h, s, te, !graph);
     } else {
       const SysDev& S = h->host_sys[0];
       const StepRef r = step_ref(h, 0, graph, t0, i);
@@ -431,9 +440,9 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
         const bool from_counts = !S.frozen && !S.umbrella && !(i == 0 && h->phi_pending[0]);
         if ((rc = enqueue_umbrella_fields(h, s, 0, graph, t0, i))) return rc;
         TimedEvent te;
-        if (timing) begin_timed(h, s, te, T_MOVE);
+        begin_timed(h, s, te, T_MOVE, timing);
         CK(launch_move(h->margs[0], move_grid(h, h->n_tiles[0], h->max_ctas_per_sm), from_counts, r, s));
-        if (timing) end_timed(h, s, te);
+        end_timed(h, s, te, !graph);
       }
       if ((rc = enqueue_aux(h, s, 0, r, timing, false))) return rc;
     }
@@ -468,9 +477,9 @@ int enqueue_reorder(soma_handle* h, cudaStream_t s) {
   int rc = ensure_sort_work(h);
   if (rc) return rc;
   TimedEvent te;
-  if (h->opt.kernel_timing) begin_timed(h, s, te, T_SORT);
+  begin_timed(h, s, te, T_SORT, h->opt.kernel_timing != 0);
   CK(launch_reorder(h->d_sys, h->n_sys, h->sort, h->sm_count, s));
-  if (h->opt.kernel_timing) end_timed(h, s, te);
+  end_timed(h, s, te, true);
   h->steps_since_sort = 0;
   return SOMA_OK;
 }
