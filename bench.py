@@ -743,8 +743,10 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
         out["field_ms"] = fd_ms / fd_n
     if conversion:
         out["conversions_per_step"] = float(conv_n) / (steps + warmup)
-    variant = "_smart" if move else "_zones" if conversion else None
-    if variant:
+    # the committed ncu summary of this kernel specialisation and workload
+    # (the plain uniform move of another workload too), when there is one
+    variant = "_smart" if move else "_zones" if conversion else None if umbrella else ""
+    if variant is not None:
         out["traffic"] = _profiled_traffic(workload, variant)
         iss = issue_roofline(workload, variant, move_avg, sm_max_mhz)
         if iss:
