@@ -456,6 +456,18 @@ int soma_autotune(soma_handle* h);
  * Paper: no counterpart (the generator is a reading). */
 int soma_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n);
 
+/* The library's stable radix sort on n (key, value) pairs: keys [n] uint64
+ * and vals [n] uint32 (host, read), sorted by the key bits [0, end_bit)
+ * into keys_out and vals_out (host, n entries each); pairs with equal key
+ * bits keep their input order.  It is the sort of the chain reorder, which
+ * orders chains by the Morton key of their first bead (a verification aid;
+ * allocates and frees device memory).  SOMA_EINVAL for NULL buffers,
+ * end_bit outside [1, 64] or n >= 2^32.  Synchronous.
+ * Paper: no counterpart (Sec. 2.2 names data reuse among the optimisations;
+ * the spatial chain order serves it). */
+int soma_sort_pairs(const uint64_t* keys, const uint32_t* vals, size_t n, int end_bit, uint64_t* keys_out,
+                    uint32_t* vals_out);
+
 /* The standard normal deviates the smart move draws from n Philox words,
  * xi = Phi^-1(((w >> 8) + 1/2) 2^-24) as the kernel evaluates it (FP32,
  * the lower tail of either half through normcdfinvf); words and out are

@@ -11,7 +11,8 @@ LIB = os.path.join(HERE, "libsoma.so")
 # device error word, the stand-in for a memory checker on this platform
 OBJ_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libsoma_debug.so")
-SOURCES = ["soma_move.cu", "soma_kernels.cu", "soma_f64.cu", "soma_sort.cu", "soma_api.cu", "soma_noalloc.cu"]
+SOURCES = ["soma_move.cu", "soma_kernels.cu", "soma_f64.cu", "soma_sort.cu", "soma_scan.cu", "soma_api.cu",
+           "soma_noalloc.cu"]
 HEADERS = ["soma_internal.cuh", "soma_launch.h", "soma_device.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -786,7 +786,7 @@ static int create_handle(const soma_system_desc* sys, int n_sys, const soma_opti
     int bits = 0;
     while ((1 << bits) < n_sys) ++bits;
     h->sort.n_chains = chain_base;
-    h->sort.end_bit = 40 + bits;
+    h->sort.end_bit = 30 + bits;  // the sort keys: 30 bits of Morton key, then the system
     if ((h->sort_interval != 0 || o.autotune) && (rc = ensure_sort_work(h)) != SOMA_OK) return bail(rc);
   }
   if (cudaMemcpy(h->d_sys, h->host_sys.data(), sizeof(SysDev) * n_sys, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1633,6 +1633,34 @@ int soma_philox4x32(const uint32_t* ctr, const uint32_t* key, uint32_t* out, siz
       launch_philox(d, d + 4 * n, d + 6 * n, (int64_t)n, 0) != cudaSuccess ||
       cudaMemcpy(out, d + 6 * n, n * 16, cudaMemcpyDeviceToHost) != cudaSuccess)
     rc = SOMA_ECUDA;
+  cudaFree(d);
+  return rc;
+}
+
+int soma_sort_pairs(const uint64_t* keys, const uint32_t* vals, size_t n, int end_bit, uint64_t* keys_out,
+                    uint32_t* vals_out) {
+  if (n == 0) return SOMA_OK;
+  if (!keys || !vals || !keys_out || !vals_out || end_bit < 1 || end_bit > 64 || n > (size_t)UINT32_MAX)
+    return SOMA_EINVAL;
+  const size_t temp = radix_sort_temp_bytes((int64_t)n);
+  char* d = nullptr;
+  if (cudaMalloc(&d, n * 24 + temp) != cudaSuccess) {
+    cudaGetLastError();
+    return SOMA_ENOMEM;
+  }
+  auto* ka = reinterpret_cast<unsigned long long*>(d);
+  auto* kb = ka + n;
+  auto* va = reinterpret_cast<uint32_t*>(kb + n);
+  auto* vb = va + n;
+  bool in_b = false;
+  int rc = SOMA_OK;
+  if (cudaMemcpy(ka, keys, n * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(va, vals, n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      launch_radix_sort_pairs(ka, kb, va, vb, (int64_t)n, end_bit, vb + n, &in_b, 0) != cudaSuccess ||
+      cudaMemcpy(keys_out, in_b ? kb : ka, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(vals_out, in_b ? vb : va, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = SOMA_ECUDA;
+  cudaGetLastError();
   cudaFree(d);
   return rc;
 }

@@ -20,7 +20,6 @@
 #include <cstdint>
 
 #include <algorithm>
-#include <cub/device/device_scan.cuh>
 
 #include "soma_device.cuh"
 #include "soma_internal.cuh"
@@ -642,8 +641,8 @@ cudaError_t launch_place(const SysDev* systems, int sys, const SysDev& host, con
   k_place_weights<<<sm_count * 4, 256, 0, s>>>(w, nc, q);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  size_t bytes = temp_bytes;
-  e = cub::DeviceScan::InclusiveSum(temp, bytes, q, prefix, nc, s);
+  (void)temp_bytes;
+  e = launch_scan_u64(q, prefix, nc, true, temp, s);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyAsync(total, prefix + nc - 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return e;
@@ -655,12 +654,7 @@ cudaError_t launch_place(const SysDev* systems, int sys, const SysDev& host, con
   return cudaGetLastError();
 }
 
-size_t place_temp_bytes(int64_t n_c) {
-  size_t bytes = 0;
-  cub::DeviceScan::InclusiveSum(nullptr, bytes, (const unsigned long long*)nullptr, (unsigned long long*)nullptr,
-                                n_c);
-  return bytes;
-}
+size_t place_temp_bytes(int64_t n_c) { return scan_temp_bytes_u64(n_c); }
 
 cudaError_t launch_profile(const uint32_t* counts, int nx, int ny, int nz, int axis, unsigned long long* out,
                            cudaStream_t s) {

@@ -91,6 +91,18 @@ struct SortWork {
   int end_bit;
 };
 size_t sort_temp_bytes(int64_t n_chains, int end_bit);
+
+// Prefix sums and the stable radix sort (soma_scan.cu).  The scans take
+// scratch of scan_temp_bytes_u64(n) bytes; out may be in.
+size_t scan_temp_bytes_u64(int64_t n);
+cudaError_t launch_scan_u64(const unsigned long long* in, unsigned long long* out, int64_t n, bool inclusive,
+                            void* temp, cudaStream_t s);
+// Sort n (key, value) pairs by the key's bits [0, end_bit), stably; a and b
+// are ping-pong buffers (the input in a), *in_b says where the result is.
+size_t radix_sort_temp_bytes(int64_t n);
+cudaError_t launch_radix_sort_pairs(unsigned long long* keys_a, unsigned long long* keys_b, uint32_t* vals_a,
+                                    uint32_t* vals_b, int64_t n, int end_bit, void* temp, bool* in_b,
+                                    cudaStream_t s);
 cudaError_t launch_reorder(SysDev* systems, int n_sys, const SortWork& w, int sm_count, cudaStream_t s);
 
 }  // namespace soma

@@ -6,9 +6,8 @@
 // the move kernel and the count atomics of the histogram then touch compact,
 // cache-resident cell ranges.  The random numbers follow the logical chain id
 // carried along in chain_id, so a reorder never changes the trajectory.
-// The sort itself is CUB's device radix sort (a library primitive); keys,
+// The sort is the library's own stable radix sort (soma_scan.cu); keys,
 // permutation and copy-back are kernels of this file.
-#include <cub/device/device_radix_sort.cuh>
 #include <cuda_runtime.h>
 
 #include "soma_launch.h"
@@ -38,7 +37,8 @@ __global__ void k_sort_keys(const SysDev* __restrict__ systems, const int32_t* _
     const uint32_t qx = quant1024(S.x[b], S.invL[0]);
     const uint32_t qy = quant1024(S.y[b], S.invL[1]);
     const uint32_t qz = quant1024(S.z[b], S.invL[2]);
-    keys[g] = ((unsigned long long)s << 40) | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    // 30 bits of Morton key, the system above them: a sort over 30 + log2(systems) bits
+    keys[g] = ((unsigned long long)s << 30) | (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     vals[g] = (uint32_t)g;
   }
 }
@@ -85,20 +85,18 @@ __global__ void k_copy_back(const SysDev* __restrict__ systems, const int32_t* _
 }
 
 size_t sort_temp_bytes(int64_t n_chains, int end_bit) {
-  size_t bytes = 0;
-  cub::DeviceRadixSort::SortPairs(nullptr, bytes, (const unsigned long long*)nullptr, (unsigned long long*)nullptr,
-                                  (const uint32_t*)nullptr, (uint32_t*)nullptr, (int64_t)n_chains, 0, end_bit);
-  return bytes;
+  (void)end_bit;
+  return radix_sort_temp_bytes(n_chains);
 }
 
 cudaError_t launch_reorder(SysDev* systems, int n_sys, const SortWork& w, int sm_count, cudaStream_t s) {
   const int blocks = sm_count * 8;
   k_sort_keys<<<blocks, 256, 0, s>>>(systems, w.chain_sys, w.n_chains, w.keys_in, w.vals_in);
-  size_t bytes = w.temp_bytes;
-  cudaError_t e = cub::DeviceRadixSort::SortPairs(w.temp, bytes, w.keys_in, w.keys_out, w.vals_in, w.vals_out,
-                                                  w.n_chains, 0, w.end_bit, s);
+  bool in_b = false;
+  cudaError_t e = launch_radix_sort_pairs(w.keys_in, w.keys_out, w.vals_in, w.vals_out, w.n_chains, w.end_bit, w.temp,
+                                          &in_b, s);
   if (e != cudaSuccess) return e;
-  k_permute<<<blocks, 256, 0, s>>>(systems, w.chain_sys, w.n_chains, w.vals_out);
+  k_permute<<<blocks, 256, 0, s>>>(systems, w.chain_sys, w.n_chains, in_b ? w.vals_out : w.vals_in);
   k_copy_back<<<blocks, 256, 0, s>>>(systems, w.chain_sys, w.n_chains);
   return cudaGetLastError();
 }

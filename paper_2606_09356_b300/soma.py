@@ -46,7 +46,7 @@ EXPORTS = (
     "soma_structure_factor", "soma_reorder", "soma_get_info", "soma_kernel_times", "soma_autotune",
     "soma_philox4x32", "soma_structure_factor_noalloc", "soma_selfcheck_timeout",
     "soma_normal_deviates", "soma_set_conversion", "soma_get_conversions", "soma_get_chain_types",
-    "soma_set_chain_types", "soma_create_partition", "soma_exchange_counts",
+    "soma_set_chain_types", "soma_create_partition", "soma_exchange_counts", "soma_sort_pairs",
 )
 
 
@@ -149,6 +149,7 @@ def load_library(path=None):
     L.soma_create_partition.argtypes = [ctypes.POINTER(soma_system_desc), ctypes.POINTER(soma_options),
                                         ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vp)]
     L.soma_exchange_counts.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(sz)]
+    L.soma_sort_pairs.argtypes = [vp, vp, sz, i32, vp, vp]
     for name in EXPORTS:
         if name not in ("soma_destroy", "soma_strerror"):
             getattr(L, name).restype = ctypes.c_int
@@ -297,6 +298,19 @@ def soma_structure_factor_noalloc(pos, n_beads, N, n_A, box, m, S, stream=None):
     _check(load_library().soma_structure_factor_noalloc(ctypes.c_void_p(p), int(n_beads), int(N), int(n_A),
                                                          _ptr(box), len(m), _ptr(m), ctypes.c_void_p(q), stream),
            "soma_structure_factor_noalloc")
+
+
+def soma_sort_pairs(keys, vals, end_bit=64):
+    """The library's stable radix sort of (uint64 key, uint32 value) pairs by
+    the key bits [0, end_bit) (verification aid)."""
+    keys = np.ascontiguousarray(keys, np.uint64)
+    vals = np.ascontiguousarray(vals, np.uint32)
+    if keys.shape != vals.shape or keys.ndim != 1:
+        raise ValueError("keys and vals: two 1-D arrays of the same length")
+    ko, vo = np.empty_like(keys), np.empty_like(vals)
+    _check(load_library().soma_sort_pairs(_ptr(keys), _ptr(vals), keys.size, int(end_bit), _ptr(ko), _ptr(vo)),
+           "soma_sort_pairs")
+    return ko, vo
 
 
 def soma_normal_deviates(words):

@@ -226,3 +226,17 @@ def test_device_tensors_as_targets_match_host_arrays():
     with soma.Handle(s, graph_steps=0) as h:  # a tensor of another type is refused before the C call
         with pytest.raises(ValueError):
             h.place(torch.from_numpy(tg).double().cuda())
+
+
+def test_place_on_the_131072_chain_melt_matches_oracle():
+    """Placement on a 128^3 grid (2,097,152 cells: the running weight sums
+    span many scan tiles) against the oracle, every chain."""
+    s = soma.System(**workloads.system_kwargs("melt_131072x32"))
+    orc = G.oracle_for(s)
+    tg = _target(s, seed=13)
+    ref = orc.place(tg)
+    with soma.Handle(s) as h:
+        h.place(tg)
+        X, _ = G.unwrapped(h)
+        assert np.abs(X - ref).max() <= 1e-5 * max(s.box)
+        assert np.array_equal(h.get_density(), orc.density(X))
