@@ -29,11 +29,13 @@ class _DeviceWords:
 
 
 def counts_tensor(handle):
-    """The counts the handle's next step reads, as an int32 CUDA tensor that
-    aliases the library's buffer (valid until the handle steps or re-bins)."""
+    """The counts the handle's next step reads, as an int32 CUDA tensor on
+    the handle's GPU that aliases the library's buffer (valid until the
+    handle steps or re-bins)."""
     import torch
     ptr, n = handle.exchange_counts()
-    return torch.as_tensor(_DeviceWords(ptr, n), device="cuda")
+    with torch.cuda.device(handle.device):
+        return torch.as_tensor(_DeviceWords(ptr, n), device=f"cuda:{handle.device}")
 
 
 def all_reduce_sum(group=None):

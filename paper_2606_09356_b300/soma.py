@@ -395,6 +395,13 @@ class Handle:
                 raise TypeError(f"unknown soma option {k}")
             setattr(o, k, v)
         self.precision = o.precision
+        self.device = int(o.device)
+        if self.device < 0:
+            try:
+                import torch
+                self.device = torch.cuda.current_device() if torch.cuda.is_available() else 0
+            except ImportError:
+                self.device = 0
         if partition is not None:
             if len(self.systems) != 1:
                 raise ValueError("a partition holds chains of one system")

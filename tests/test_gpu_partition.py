@@ -83,6 +83,29 @@ def test_partitions_with_umbrella_restraint():
     _check_same(s, whole, parts)
 
 
+def test_partitions_place_as_the_whole_system():
+    """Placement from target fields draws per logical chain, so partitions
+    place exactly the whole system's chains; steps after it stay equal."""
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
+    x = (np.arange(16) + 0.5) / 16
+    pA = np.clip(np.repeat(0.5 + 0.45 * np.sin(2 * np.pi * x), 256), 0.0, 1.0)
+    target = np.stack([pA, 1.0 - pA]).astype(np.float32)
+    st = torch.cuda.Stream()
+    whole = soma.Handle(s)
+    parts = [soma.Handle(s, partition=r) for r in [(0, 200), (200, 512)]]
+    for h in [whole] + parts:
+        h.place(target)
+    torch.cuda.synchronize()
+    partition.sum_on_one_device(parts, st)  # placement re-bins: exchange
+    for _ in range(5):
+        whole.mc_steps(1, stream=st.cuda_stream)
+        for h in parts:
+            h.mc_steps(1, stream=st.cuda_stream)
+        partition.sum_on_one_device(parts, st)
+    torch.cuda.synchronize()
+    _check_same(s, whole, parts)
+
+
 def test_two_partitions_of_the_131072_chain_melt():
     """The melt of 131,072 chains of 32 beads (grid 128^3) in two halves, in
     the benchmark's launch configuration (persistent move kernel at full
@@ -130,3 +153,4 @@ def test_partition_arguments():
             h.autotune()
         assert e.value.code == soma.SOMA_ENOTSUP
         assert h.info()["rho_bar"] == 4.0 and h.info()["n_beads"] == 256 * 32
+        assert partition.counts_tensor(h).device == torch.device(f"cuda:{h.device}")
