@@ -130,6 +130,10 @@ typedef struct soma_options {
   soma_alloc_fn alloc;   /* optional device allocator, with free and ctx */
   soma_free_fn free;
   void* alloc_ctx;
+  int32_t move_warps;    /* consumer warps per CTA of the one-system move kernel: 0 = 8, or the
+                            autotuner's choice of 8 and 12; 8 or 12 fixes it (else SOMA_EINVAL).
+                            A handle of several systems always uses 8 (the batch kernel). */
+  int32_t reserved;      /* 0 */
 } soma_options;
 
 typedef struct soma_obs {
@@ -152,7 +156,7 @@ typedef struct soma_info {
   int32_t ctas_per_sm;     /* move-kernel CTAs per SM in use */
   int32_t sort_interval;   /* reorder interval in use */
   int32_t hist_mode;       /* histogram strategy in use */
-  int32_t reserved;
+  int32_t move_warps;      /* consumer warps per CTA of the move kernel in use (8 or 12) */
   int32_t reserved2;
 } soma_info;
 

@@ -71,7 +71,9 @@ struct soma_handle {
   std::vector<char> phi_pending;  // next step moves against coupling-supplied fields
   std::vector<void*> owned;
   // launch geometry
-  int max_ctas_per_sm = 1;
+  int max_ctas_per_sm = 1;             // of the single-system move kernel in its current shape
+  int move_warps = 8;                  // its consumer warps per CTA (8 or 12; the autotuner picks)
+  int max_ctas_warps[2] = {1, 1};      // resident CTAs per SM of the 8- and 12-warp shapes
   int max_ctas_batch = 1;              // the largest over the batch kernel's specialisations
   int max_ctas_batch_kind[2][2] = {};  // [smart][wall]
   int ctas_per_sm = 1;
@@ -246,7 +248,8 @@ void build_args(soma_handle* h) {
     a.P = S.P;
     a.sys_index = S.sys_index;
     a.n_poly = S.n_poly;
-    a.chains_per_tile = S.P ? move_kernel_chains_per_tile(S.P) : 0;
+    // several systems step in the batch kernel, whose tiles are 8 warps
+    a.chains_per_tile = S.P ? move_kernel_chains_per_tile(S.P, h->n_sys > 1 ? 8 : h->move_warps) : 0;
     a.n_tiles = S.P ? (int)(((int64_t)S.n_poly + a.chains_per_tile - 1) / a.chains_per_tile) : 0;
     a.bin = h->hist_mode == SOMA_HIST_FUSED ? 1 : 0;
     a.n_c = S.n_c;
@@ -441,7 +444,8 @@ int enqueue_steps(soma_handle* h, cudaStream_t s, int n, bool graph, long long t
         if ((rc = enqueue_umbrella_fields(h, s, 0, graph, t0, i))) return rc;
         TimedEvent te;
         begin_timed(h, s, te, T_MOVE, timing);
-        CK(launch_move(h->margs[0], move_grid(h, h->n_tiles[0], h->max_ctas_per_sm), from_counts, r, s));
+        CK(launch_move(h->margs[0], move_grid(h, h->n_tiles[0], h->max_ctas_per_sm), from_counts, r, s,
+                       h->move_warps));
         end_timed(h, s, te, !graph);
       }
       if ((rc = enqueue_aux(h, s, 0, r, timing, false))) return rc;
@@ -546,7 +550,9 @@ int set_frozen(soma_handle* h, int sys, int frozen) {
   return SOMA_OK;
 }
 
-void apply_geometry(soma_handle* h, int ctas_per_sm, int hist_mode) {
+void apply_geometry(soma_handle* h, int ctas_per_sm, int hist_mode, int move_warps) {
+  h->move_warps = move_warps;
+  h->max_ctas_per_sm = h->max_ctas_warps[move_warps == 12 ? 1 : 0];
   h->ctas_per_sm = std::max(1, std::min(ctas_per_sm, std::max(h->max_ctas_per_sm, h->max_ctas_batch)));
   h->hist_mode = hist_mode;
   build_args(h);
@@ -642,6 +648,7 @@ static int create_handle(const soma_system_desc* sys, int n_sys, const soma_opti
   if (o.hist_mode < SOMA_HIST_AUTO || o.hist_mode > SOMA_HIST_SEPARATE) return SOMA_EINVAL;
   if (o.graph_steps < 0 || o.graph_steps > 4096) return SOMA_EINVAL;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SOMA_EINVAL;
+  if (o.move_warps != 0 && o.move_warps != 8 && o.move_warps != 12) return SOMA_EINVAL;
 
   soma_handle* h = new (std::nothrow) soma_handle();
   if (!h) return SOMA_ENOMEM;
@@ -668,7 +675,10 @@ static int create_handle(const soma_system_desc* sys, int n_sys, const soma_opti
       cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming) != cudaSuccess)
     return bail(SOMA_ECUDA);
-  h->max_ctas_per_sm = move_kernel_max_ctas_per_sm();
+  h->max_ctas_warps[0] = move_kernel_max_ctas_per_sm(8);
+  h->max_ctas_warps[1] = move_kernel_max_ctas_per_sm(12);
+  h->move_warps = (o.move_warps == 12 && n_sys == 1) ? 12 : 8;
+  h->max_ctas_per_sm = h->max_ctas_warps[h->move_warps == 12 ? 1 : 0];
   for (int sm = 0; sm < 2; ++sm)
     for (int wz = 0; wz < 2; ++wz) {
       h->max_ctas_batch_kind[sm][wz] = move_batch_max_ctas_per_sm(sm != 0, wz != 0);
@@ -679,7 +689,8 @@ static int create_handle(const soma_system_desc* sys, int n_sys, const soma_opti
   h->sort_interval = o.sort_interval < 0 ? kDefaultSortInterval : o.sort_interval;
   h->f64 = o.precision == SOMA_PREC_FP64;
   if (h->f64) h->sort_interval = 0;  // the precision reference keeps its storage order
-  h->acc_per_sys = h->sm_count * std::max(h->max_ctas_per_sm, h->max_ctas_batch);
+  h->acc_per_sys =
+      h->sm_count * std::max(std::max(h->max_ctas_warps[0], h->max_ctas_warps[1]), h->max_ctas_batch);
 
   // --- per-system constants and arrays ---------------------------------
   h->host_sys.resize(n_sys);
@@ -1459,7 +1470,7 @@ int soma_get_info(soma_handle* h, int sys, soma_info* out) {
   out->ctas_per_sm = h->ctas_per_sm;
   out->sort_interval = h->sort_interval;
   out->hist_mode = h->hist_mode;
-  out->reserved = 0;
+  out->move_warps = h->n_sys > 1 ? 8 : h->move_warps;
   return SOMA_OK;
 }
 
@@ -1539,34 +1550,42 @@ int soma_autotune(soma_handle* h) {
   };
   const int steps = 6;
   float best = 1e30f;
-  int best_c = h->ctas_per_sm, best_h = h->hist_mode;
+  int best_c = h->ctas_per_sm, best_h = h->hist_mode, best_w = h->move_warps;
   cudaEvent_t a, b;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
   const int timing = h->opt.kernel_timing;
   h->opt.kernel_timing = 0;
-  const int max_c = h->n_sys > 1 ? h->max_ctas_batch : h->max_ctas_per_sm;
-  for (int c = 1; c <= max_c; ++c) {
-    if (h->opt.ctas_per_sm && c != h->opt.ctas_per_sm) continue;
-    for (int hm = SOMA_HIST_FUSED; hm <= SOMA_HIST_SEPARATE; ++hm) {
-      if (h->opt.hist_mode != SOMA_HIST_AUTO && hm != h->opt.hist_mode) continue;
-      apply_geometry(h, c, hm);
-      if ((rc = enqueue_steps(h, h->stream, 2, false, (long long)step0))) return rc;  // warm-up
-      CK(cudaEventRecord(a, h->stream));
-      if ((rc = enqueue_steps(h, h->stream, steps, false, (long long)step0 + 2))) return rc;
-      CK(cudaEventRecord(b, h->stream));
-      CK(cudaEventSynchronize(b));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, a, b));
-      if (ms < best) {
-        best = ms;
-        best_c = c;
-        best_h = hm;
+  // block shapes: one system tries 8 and 12 consumer warps per CTA (the
+  // batch kernel and the FP64 form have one shape)
+  const bool shapes = h->n_sys == 1 && !h->f64 && h->host_sys[0].P > 0;
+  for (int w : {8, 12}) {
+    if (w == 12 && !shapes) continue;
+    if (h->opt.move_warps && w != h->opt.move_warps) continue;
+    const int max_c = h->n_sys > 1 ? h->max_ctas_batch : h->max_ctas_warps[w == 12 ? 1 : 0];
+    for (int c = 1; c <= max_c; ++c) {
+      if (h->opt.ctas_per_sm && c != h->opt.ctas_per_sm) continue;
+      for (int hm = SOMA_HIST_FUSED; hm <= SOMA_HIST_SEPARATE; ++hm) {
+        if (h->opt.hist_mode != SOMA_HIST_AUTO && hm != h->opt.hist_mode) continue;
+        apply_geometry(h, c, hm, w);
+        if ((rc = enqueue_steps(h, h->stream, 2, false, (long long)step0))) return rc;  // warm-up
+        CK(cudaEventRecord(a, h->stream));
+        if ((rc = enqueue_steps(h, h->stream, steps, false, (long long)step0 + 2))) return rc;
+        CK(cudaEventRecord(b, h->stream));
+        CK(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) {
+          best = ms;
+          best_c = c;
+          best_h = hm;
+          best_w = w;
+        }
+        if ((rc = restore())) return rc;
       }
-      if ((rc = restore())) return rc;
     }
   }
-  apply_geometry(h, best_c, best_h);
+  apply_geometry(h, best_c, best_h, best_w);
 
   // Sort interval (opt.sort_interval < 0): time one chain reorder, then the
   // step time at growing distances j from it (chains drift out of cell

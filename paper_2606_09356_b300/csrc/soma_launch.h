@@ -9,11 +9,12 @@
 namespace soma {
 
 // Kernel (a) with fused (b), soma_move.cu.
-cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s);
+// warps: consumer warps per CTA of the single-system kernel, 8 or 12.
+cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s, int warps);
 cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStream_t s);
 int move_batch_max_ctas_per_sm(bool smart, bool wall);
-int move_kernel_max_ctas_per_sm();
-int move_kernel_chains_per_tile(int P);
+int move_kernel_max_ctas_per_sm(int warps);
+int move_kernel_chains_per_tile(int P, int warps);
 // The smart move's standard normal deviates of n words (verification aid).
 cudaError_t launch_normal_words(const uint32_t* w, float* out, int64_t n, cudaStream_t s);
 // One mbarrier wait that nothing satisfies, bounded by `cycles` (sets kErrTimeout in *err).

@@ -7,7 +7,9 @@
 //  * persistent CTAs, warp-specialised: one producer warp streams each
 //    tile's positions (x, y, z) and logical chain ids from HBM into a ring of
 //    kStages shared-memory stages with cp.async.bulk, completion tracked by
-//    mbarriers; kConsumerWarps consumer warps compute;
+//    mbarriers; W consumer warps compute (W = 8 or 12: the single-system
+//    kernel is built for both and the autotuner picks one per workload, the
+//    batch kernel uses 8);
 //  * a consumer lane k of a chain holds beads 2k (even set) and 2k+1 (odd
 //    set); neighbours come from the adjacent lane by width-P shuffles;
 //  * both beads' proposals are formed first, so the four gathers of the lane
@@ -46,25 +48,31 @@
 
 namespace soma {
 
-constexpr int kConsumerWarps = 8;
 constexpr int kStages = 4;
-constexpr int kTileBeads = kConsumerWarps * 64;   // a warp holds at most 64 beads
-constexpr int kTileChains = kConsumerWarps * 32;  // at most 32 chains per warp (P = 1)
-// A tile's bulk copies start at chain c0 = tile * kConsumerWarps * 32/P and
-// bead c0 * N; both addresses are 16-byte aligned for every P and N only
-// when the chains per tile are a multiple of 4 (P = 32: kConsumerWarps).
-static_assert(kConsumerWarps % 4 == 0, "tile copies would start off a 16-byte boundary");
+constexpr int kBatchWarps = 8;  // consumer warps of the batch kernel
+// Resident CTAs per SM the register budget (72) is for: 3 of 8 + 1 warps,
+// 2 of 12 + 1.
+template <int W>
+constexpr int move_min_blocks() { return W <= 8 ? 3 : 2; }
+// A tile's bulk copies start at chain c0 = tile * W * 32/P and bead c0 * N;
+// both addresses are 16-byte aligned for every P and N only when the chains
+// per tile are a multiple of 4 (P = 32: W itself).
+template <int W>
+constexpr bool tile_copies_aligned() { return W % 4 == 0; }
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz: a wait that long is an error
 constexpr float kLog2e = 1.4426950408889634f;
 
 // A batch rides in the kernel's parameter space (at most 32,764 bytes).
 static_assert(sizeof(BatchArgs) <= 32000, "BatchArgs exceeds the kernel parameter limit");
 
+// A tile of W warps: at most 64 beads per warp, at most 32 chains (P = 1).
+template <int W>
 struct __align__(128) MoveStage {
-  float x[kTileBeads];
-  float y[kTileBeads];
-  float z[kTileBeads];
-  uint32_t cid[kTileChains];
+  static_assert(tile_copies_aligned<W>(), "tile copies would start off a 16-byte boundary");
+  float x[W * 64];
+  float y[W * 64];
+  float z[W * 64];
+  uint32_t cid[W * 32];
   uint32_t sys;  // batched launches: the tile's system, written by the producer
   uint32_t pad[3];
 };
@@ -200,7 +208,8 @@ __device__ __forceinline__ int cell_idx(const MoveArgs& a, float x, float y, flo
 }
 
 // Producer: issue the copies of tile `tile` (local to system a) into stage st.
-__device__ __forceinline__ void produce_tile(const MoveArgs& a, int tile, MoveStage& st, uint64_t* full) {
+template <int W>
+__device__ __forceinline__ void produce_tile(const MoveArgs& a, int tile, MoveStage<W>& st, uint64_t* full) {
   const int c0 = tile * a.chains_per_tile;
   const int nch = min(a.chains_per_tile, a.n_poly - c0);
   const int64_t b0 = (int64_t)c0 * a.N;
@@ -520,8 +529,8 @@ __device__ __forceinline__ void smart_pair(const MoveArgs& a, long long tl, cons
 // it, moves the even then the odd beads of its chains, writes back, bins.
 // Returns the number of accepted moves of this lane.
 // prev: count buffer of step t-1 (fields), cur: count buffer of step t (histogram).
-template <bool kFromCounts, bool kSmart, bool kWall, bool kConv>
-__device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, const MoveStage& st, uint64_t* empty,
+template <bool kFromCounts, bool kSmart, bool kWall, bool kConv, int W>
+__device__ __forceinline__ unsigned consume_tile(const MoveArgs& a, int tile, const MoveStage<W>& st, uint64_t* empty,
                                                  long long tl, const uint2* __restrict__ prev,
                                                  uint32_t* __restrict__ cur, int warp, int lane) {
   const int P = a.P, N = a.N;
@@ -636,11 +645,11 @@ __device__ __forceinline__ void clear_next(const MoveArgs& a, long long tl, int 
   for (int64_t i = lo + tid; i < hi; i += nthreads) next2[i] = make_uint2(0u, 0u);
 }
 
-__device__ __forceinline__ void init_barriers(uint64_t* full, uint64_t* empty) {
+__device__ __forceinline__ void init_barriers(uint64_t* full, uint64_t* empty, int consumer_warps) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kConsumerWarps);
+      mbar_init(&empty[s], consumer_warps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -653,16 +662,17 @@ __device__ __forceinline__ void drain(uint64_t* full, int issued, int* err) {
     if (!mbar_wait(&full[j % kStages], (uint32_t)(j / kStages) & 1u, err)) break;
 }
 
-// Register budget for 3 resident CTAs per SM (72 registers, no spill).
-template <bool kFromCounts, bool kSmart, bool kWall, bool kConv>
-__global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __grid_constant__ MoveArgs a, StepRef r) {
-  __shared__ MoveStage stage[kStages];
+// W consumer warps and one producer warp; register budget 72 (no spill).
+template <int W, bool kFromCounts, bool kSmart, bool kWall, bool kConv>
+__global__ void __launch_bounds__((W + 1) * 32, move_min_blocks<W>())
+    k_move(const __grid_constant__ MoveArgs a, StepRef r) {
+  __shared__ MoveStage<W> stage[kStages];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
-  init_barriers(full, empty);
+  init_barriers(full, empty, W);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  if (warp == kConsumerWarps) {  // producer warp: lane 0 streams the tiles
+  if (warp == W) {  // producer warp: lane 0 streams the tiles
     if (lane == 0) {
       int it = 0;
       for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
@@ -683,11 +693,12 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3) k_move(const __g
   for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x, ++it) {
     const int s = it % kStages;
     if (!mbar_wait(&full[s], (uint32_t)(it / kStages) & 1u, a.err)) break;
-    nacc += consume_tile<kFromCounts, kSmart, kWall, kConv>(a, tile, stage[s], &empty[s], tl, prev, cur, warp, lane);
+    nacc += consume_tile<kFromCounts, kSmart, kWall, kConv, W>(a, tile, stage[s], &empty[s], tl, prev, cur, warp,
+                                                               lane);
   }
   nacc = __reduce_add_sync(0xffffffffu, nacc);
   if (lane == 0 && nacc) atomicAdd(a.acc + blockIdx.x, (unsigned long long)nacc);
-  clear_next(a, tl, threadIdx.x, kConsumerWarps * 32);
+  clear_next(a, tl, threadIdx.x, W * 32);
 }
 
 // System of a global tile index (uniform across the CTA): binary search.
@@ -707,17 +718,17 @@ __device__ __forceinline__ int batch_system(const BatchArgs& p, int tile) {
 // Register budget for 3 resident CTAs per SM as k_move (the bond-force-biased
 // specialisations spill a few bytes and still beat 2 CTAs per SM).
 template <bool kSmart, bool kWall>
-__global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3)
+__global__ void __launch_bounds__((kBatchWarps + 1) * 32, move_min_blocks<kBatchWarps>())
     k_move_batch(const __grid_constant__ BatchArgs p, StepRef r) {
-  __shared__ MoveStage stage[kStages];
+  __shared__ MoveStage<kBatchWarps> stage[kStages];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
-  init_barriers(full, empty);
+  init_barriers(full, empty, kBatchWarps);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_tiles = p.tile_start[p.n_sys];
   int* err = p.sys[0].err;
 
-  if (warp == kConsumerWarps) {
+  if (warp == kBatchWarps) {
     if (lane == 0) {
       int it = 0;
       for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
@@ -748,16 +759,16 @@ __global__ void __launch_bounds__((kConsumerWarps + 1) * 32, 3)
     unsigned n;
     if (a.conv)
       n = a.from_counts
-              ? consume_tile<true, kSmart, kWall, true>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
-              : consume_tile<false, kSmart, kWall, true>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
+              ? consume_tile<true, kSmart, kWall, true, kBatchWarps>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
+              : consume_tile<false, kSmart, kWall, true, kBatchWarps>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
     else
       n = a.from_counts
-              ? consume_tile<true, kSmart, kWall, false>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
-              : consume_tile<false, kSmart, kWall, false>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
+              ? consume_tile<true, kSmart, kWall, false, kBatchWarps>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane)
+              : consume_tile<false, kSmart, kWall, false, kBatchWarps>(a, lt, stage[s], &empty[s], tl, prev, cur, warp, lane);
     n = __reduce_add_sync(0xffffffffu, n);
     if (lane == 0 && n) atomicAdd(a.acc + blockIdx.x, (unsigned long long)n);
   }
-  for (int sys = 0; sys < p.n_sys; ++sys) clear_next(p.sys[sys], tl, threadIdx.x, kConsumerWarps * 32);
+  for (int sys = 0; sys < p.n_sys; ++sys) clear_next(p.sys[sys], tl, threadIdx.x, kBatchWarps * 32);
 }
 
 // Self-check of the bounded-wait failure path: one thread waits on an
@@ -782,10 +793,12 @@ cudaError_t launch_wait_selfcheck(int* err, long long cycles, cudaStream_t s) {
 // from counts).  The held-field variant uses more registers; launched with
 // the same grid its extra CTAs simply wait for a slot (CTAs never wait on
 // one another).
-int move_kernel_max_ctas_per_sm() {
+int move_kernel_max_ctas_per_sm(int warps) {
   int n = 0;
   const cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<true, false, false, false>, (kConsumerWarps + 1) * 32, 0);
+      warps == 12
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<12, true, false, false, false>, 13 * 32, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<8, true, false, false, false>, 9 * 32, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -793,23 +806,32 @@ int move_kernel_max_ctas_per_sm() {
   return n > 0 ? n : 1;
 }
 
-int move_kernel_chains_per_tile(int P) { return kConsumerWarps * (32 / P); }
+int move_kernel_chains_per_tile(int P, int warps) { return warps * (32 / P); }
 
-cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s) {
-  const int threads = (kConsumerWarps + 1) * 32;
-  using Kernel = void (*)(MoveArgs, StepRef);
-  // [conv][smart][wall][from_counts]
-  static const Kernel table[2][2][2][2] = {
-      {{{k_move<false, false, false, false>, k_move<true, false, false, false>},
-        {k_move<false, false, true, false>, k_move<true, false, true, false>}},
-       {{k_move<false, true, false, false>, k_move<true, true, false, false>},
-        {k_move<false, true, true, false>, k_move<true, true, true, false>}}},
-      {{{k_move<false, false, false, true>, k_move<true, false, false, true>},
-        {k_move<false, false, true, true>, k_move<true, false, true, true>}},
-       {{k_move<false, true, false, true>, k_move<true, true, false, true>},
-        {k_move<false, true, true, true>, k_move<true, true, true, true>}}}};
-  const Kernel k = table[a.conv ? 1 : 0][a.smart ? 1 : 0][a.wall_z ? 1 : 0][from_counts ? 1 : 0];
-  k<<<grid, threads, 0, s>>>(a, r);
+using MoveKernel = void (*)(MoveArgs, StepRef);
+
+// [conv][smart][wall][from_counts] of the W-warp kernel
+template <int W>
+static MoveKernel move_kernel_of(bool conv, bool smart, bool wall, bool from_counts) {
+  static const MoveKernel table[2][2][2][2] = {
+      {{{k_move<W, false, false, false, false>, k_move<W, true, false, false, false>},
+        {k_move<W, false, false, true, false>, k_move<W, true, false, true, false>}},
+       {{k_move<W, false, true, false, false>, k_move<W, true, true, false, false>},
+        {k_move<W, false, true, true, false>, k_move<W, true, true, true, false>}}},
+      {{{k_move<W, false, false, false, true>, k_move<W, true, false, false, true>},
+        {k_move<W, false, false, true, true>, k_move<W, true, false, true, true>}},
+       {{k_move<W, false, true, false, true>, k_move<W, true, true, false, true>},
+        {k_move<W, false, true, true, true>, k_move<W, true, true, true, true>}}}};
+  return table[conv ? 1 : 0][smart ? 1 : 0][wall ? 1 : 0][from_counts ? 1 : 0];
+}
+
+cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s, int warps) {
+  const bool c = a.conv != 0, sm = a.smart != 0, w = a.wall_z != 0;
+  if (warps == 12) {
+    move_kernel_of<12>(c, sm, w, from_counts)<<<grid, 13 * 32, 0, s>>>(a, r);
+  } else {
+    move_kernel_of<8>(c, sm, w, from_counts)<<<grid, 9 * 32, 0, s>>>(a, r);
+  }
   return cudaGetLastError();
 }
 
@@ -817,7 +839,7 @@ static_assert(sizeof(BatchArgs) + sizeof(StepRef) <= 32764, "batch parameters ex
 
 cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStream_t s) {
   const bool smart = p.n_sys > 0 && p.sys[0].smart, wall = p.n_sys > 0 && p.sys[0].wall_z;
-  const int threads = (kConsumerWarps + 1) * 32;
+  const int threads = (kBatchWarps + 1) * 32;
   if (smart)
     wall ? k_move_batch<true, true><<<grid, threads, 0, s>>>(p, r) : k_move_batch<true, false><<<grid, threads, 0, s>>>(p, r);
   else
@@ -832,7 +854,7 @@ int move_batch_max_ctas_per_sm(bool smart, bool wall) {
   const Kernel k = smart ? (wall ? k_move_batch<true, true> : k_move_batch<true, false>)
                          : (wall ? k_move_batch<false, true> : k_move_batch<false, false>);
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, (kConsumerWarps + 1) * 32, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, (kBatchWarps + 1) * 32, 0) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }

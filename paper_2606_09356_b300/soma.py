@@ -76,6 +76,7 @@ class soma_options(ctypes.Structure):
         ("hist_mode", ctypes.c_int32), ("graph_steps", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
         ("autotune", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", ctypes.c_void_p),
+        ("move_warps", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -92,7 +93,7 @@ class soma_info(ctypes.Structure):
         ("n_beads", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("k_b", ctypes.c_double),
         ("A", ctypes.c_double), ("rho_bar", ctypes.c_double), ("lanes_per_chain", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32), ("sort_interval", ctypes.c_int32), ("hist_mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+        ("move_warps", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 

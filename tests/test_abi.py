@@ -49,9 +49,9 @@ def test_struct_layouts_match_c():
 #include <stddef.h>
 #include "soma.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(soma_system_desc), sizeof(soma_options), sizeof(soma_obs),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(soma_system_desc), sizeof(soma_options), sizeof(soma_obs),
          sizeof(soma_info), offsetof(soma_system_desc, box), offsetof(soma_system_desc, seed),
-         offsetof(soma_options, alloc));
+         offsetof(soma_options, alloc), offsetof(soma_options, move_warps));
   return 0;
 }
 '''
@@ -63,7 +63,7 @@ int main(void) {
         got = [int(v) for v in subprocess.check_output([exe]).split()]
     exp = [ctypes.sizeof(soma.soma_system_desc), ctypes.sizeof(soma.soma_options), ctypes.sizeof(soma.soma_obs),
            ctypes.sizeof(soma.soma_info), soma.soma_system_desc.box.offset, soma.soma_system_desc.seed.offset,
-           soma.soma_options.alloc.offset]
+           soma.soma_options.alloc.offset, soma.soma_options.move_warps.offset]
     assert got == exp
 
 

@@ -41,6 +41,31 @@ def test_launch_shape_histogram_graph_and_reorder_invariance():
         _same(ref, _run(s, 40, **{**dict(graph_steps=0, sort_interval=0), **opts}))
 
 
+@pytest.mark.parametrize("kw", [dict(), dict(move=soma.SOMA_MOVE_SMART), dict(wall_z=1), dict(N=7, n_A=3),
+                                dict(N=64, n_A=19), dict(N=1, n_A=1, A=0.3)],
+                         ids=["uniform", "smart", "walls", "odd_N", "N64", "monomers"])
+def test_block_shape_invariance(kw):
+    """The move kernel with 8 or 12 consumer warps per CTA (tiles of 8 or 12
+    warps' chains) steps the same trajectory, at every resident-CTA count."""
+    s = soma.System(**{**SMALL, **kw})
+    ref = _run(s, 30, move_warps=8, graph_steps=0, sort_interval=7)
+    for opts in (dict(move_warps=12), dict(move_warps=12, ctas_per_sm=1), dict(move_warps=12, graph_steps=5)):
+        _same(ref, _run(s, 30, **{**dict(graph_steps=0, sort_interval=7), **opts}))
+    with soma.Handle(s, move_warps=12) as h:
+        assert h.info()["move_warps"] == 12
+    with soma.Handle(s, move_warps=12, autotune=1) as h:
+        h.mc_steps(1)
+        assert h.info()["move_warps"] == 12  # fixed by the option, the autotuner keeps it
+    with pytest.raises(soma.SomaError) as e:
+        soma.Handle(s, move_warps=10)
+    assert e.value.code == soma.SOMA_EINVAL
+
+
+def test_the_131072_chain_melt_at_both_block_shapes():
+    s = soma.System(**workloads.system_kwargs("melt_131072x32"))
+    _same(_run(s, 6, move_warps=8, graph_steps=0), _run(s, 6, move_warps=12, graph_steps=0))
+
+
 def test_tuned_sort_interval_keeps_the_trajectory():
     s = soma.System(**SMALL)
     ref = _run(s, 40, graph_steps=0, sort_interval=0)
