@@ -552,7 +552,7 @@ def run_gpu(args):
             "config": {"workload": workload_desc(args.workload, c), "n_beads": n_b, "n_cells": n_c,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "sort_interval": info_after["sort_interval"],
-                       "tuned": {k: info_after[k] for k in ("ctas_per_sm", "hist_mode")},
+                       "tuned": {k: info_after[k] for k in ("ctas_per_sm", "hist_mode", "move_warps")},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "step_ms_stats": {"median": float(statistics.median(step_ms)), "min": float(min(step_ms)),
@@ -738,7 +738,7 @@ def bench_variant(soma, torch, workload, kw, device, sptr, stream, flush, steps,
     achieved = move_kernel_bytes(n_b, n_c) / (move_avg * 1e-3) / 1e9
     out = {"value": steps * n_b / (total_ms * 1e-3), "unit": UNIT, "ms_per_step": total_ms / steps,
            "move_ms": move_avg, "achieved_gbs": achieved, "frac": achieved / hbm_peak, "acceptance": acc,
-           "note": note}
+           "tuned": {k: info[k] for k in ("ctas_per_sm", "hist_mode", "move_warps")}, "note": note}
     if fd_n:
         out["field_ms"] = fd_ms / fd_n
     if conversion:

@@ -140,8 +140,8 @@ cudaError_t launch_scan_u64(const unsigned long long* in, unsigned long long* ou
 // ---------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortTile = 4096;
-constexpr int kWarpItems = kSortTile / kSortWarps;  // 512 consecutive items per warp
+constexpr int kSortTile = 1024;  // small tiles: many CTAs even for 10^5 chains
+constexpr int kWarpItems = kSortTile / kSortWarps;  // 128 consecutive items per warp
 constexpr int kDigits = 256;
 
 static int64_t sort_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }

@@ -2,7 +2,7 @@
 profilers such as ncu; prints nothing but a one-line summary).
 
     python -m paper_2606_09356_b300.profile_run --workload melt_131072x32 --steps 20 [--move smart]
-        [--walls] [--conversion]
+        [--walls] [--conversion] [--move-warps 12]
 
 --conversion switches on boundary-zone conversion (zones 2 R_e wide at the
 bottom and top, per-step rates 0.05, 0.02, 0.03, 0.04, converted molecules
@@ -26,13 +26,14 @@ def main():
     p.add_argument("--move", default="uniform", choices=["uniform", "smart"])
     p.add_argument("--walls", action="store_true")
     p.add_argument("--conversion", action="store_true")
+    p.add_argument("--move-warps", type=int, default=0, help="consumer warps per CTA: 8 or 12 (0: 8)")
     a = p.parse_args()
     _build.build()
     move = soma.SOMA_MOVE_SMART if a.move == "smart" else soma.SOMA_MOVE_UNIFORM
     kw = workloads.system_kwargs(a.workload)
     s = soma.System(**{**kw, "move": move, "wall_z": 1 if a.walls else 0})
     with soma.Handle(s, graph_steps=a.graph_steps, sort_interval=a.sort_interval, hist_mode=a.hist_mode,
-                     ctas_per_sm=a.ctas_per_sm) as h:
+                     ctas_per_sm=a.ctas_per_sm, move_warps=a.move_warps) as h:
         if a.conversion:
             h.set_conversion(kw["n_A"] // 2, 2.0, 2.0, (0.05, 0.02, 0.03, 0.04))
         t = time.perf_counter()

@@ -1,5 +1,5 @@
 """The library's stable radix sort (the sort of the chain reorder) against
-numpy's stable argsort, bit for bit: sizes around its 4,096-item tiles,
+numpy's stable argsort, bit for bit: sizes around its 1,024-item tiles,
 ragged sizes, heavily repeated keys (stability), several key widths."""
 import numpy as np
 import pytest
@@ -15,7 +15,7 @@ def _lib():
     G.lib()
 
 
-@pytest.mark.parametrize("n", [1, 2, 31, 4095, 4096, 4097, 8192 + 511, 100003, (1 << 20) + 7])
+@pytest.mark.parametrize("n", [1, 2, 31, 1023, 1024, 1025, 4095, 4097, 8192 + 511, 100003, (1 << 20) + 7])
 @pytest.mark.parametrize("end_bit,distinct", [(46, None), (64, None), (40, 50), (8, None)])
 def test_sort_matches_numpy_stable_argsort(n, end_bit, distinct):
     rng = np.random.default_rng(n * 131 + end_bit)
