@@ -513,8 +513,10 @@ int soma_selfcheck_timeout(int device, uint64_t cycles);
  * array sized for at most 4096 q vectors (about 112 KiB on every GPU that
  * loads the library, held until exit); nq > 4096 returns SOMA_EINVAL.  The
  * first call on each device (that device current) looks up the array's
- * device address and should come before any stream capture.  All calls share
- * the array and each clears it first: calls that overlap on the GPU race.
+ * device address.  Calls are not for stream capture: each copies m_xyz from
+ * the caller's host memory, which a capture refuses when it is pageable and,
+ * when it is pinned, would re-read at every replay.  All calls share the
+ * array and each clears it first: calls that overlap on the GPU race.
  * Never calls cudaMalloc, cudaFree or an allocating library routine. */
 int soma_structure_factor_noalloc(const float* pos, int64_t n_beads, int32_t N, int32_t n_A,
                                   const double* box, int nq, const int32_t* m_xyz, double* S,
