@@ -131,8 +131,10 @@ typedef struct soma_options {
   soma_free_fn free;
   void* alloc_ctx;
   int32_t move_warps;    /* consumer warps per CTA of the one-system move kernel: 0 = 8, or the
-                            autotuner's choice of 8 and 12; 8 or 12 fixes it (else SOMA_EINVAL).
-                            A handle of several systems always uses 8 (the batch kernel). */
+                            autotuner's choice of 8, 12 and 24; 8, 12 or 24 fixes it (other
+                            values: SOMA_EINVAL; a shape the device cannot launch:
+                            SOMA_ENOTSUP).  A handle of several systems always uses 8 (the
+                            batch kernel). */
   int32_t reserved;      /* 0 */
 } soma_options;
 
@@ -156,7 +158,7 @@ typedef struct soma_info {
   int32_t ctas_per_sm;     /* move-kernel CTAs per SM in use */
   int32_t sort_interval;   /* reorder interval in use */
   int32_t hist_mode;       /* histogram strategy in use */
-  int32_t move_warps;      /* consumer warps per CTA of the move kernel in use (8 or 12) */
+  int32_t move_warps;      /* consumer warps per CTA of the move kernel in use (8, 12 or 24) */
   int32_t reserved2;
 } soma_info;
 

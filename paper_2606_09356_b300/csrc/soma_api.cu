@@ -72,8 +72,8 @@ struct soma_handle {
   std::vector<void*> owned;
   // launch geometry
   int max_ctas_per_sm = 1;             // of the single-system move kernel in its current shape
-  int move_warps = 8;                  // its consumer warps per CTA (8 or 12; the autotuner picks)
-  int max_ctas_warps[2] = {1, 1};      // resident CTAs per SM of the 8- and 12-warp shapes
+  int move_warps = 8;                  // its consumer warps per CTA (8, 12 or 24; the autotuner picks)
+  int max_ctas_warps[kMoveShapes] = {};  // resident CTAs per SM of each shape (0: cannot run here)
   int max_ctas_batch = 1;              // the largest over the batch kernel's specialisations
   int max_ctas_batch_kind[2][2] = {};  // [smart][wall]
   int ctas_per_sm = 1;
@@ -550,9 +550,13 @@ int set_frozen(soma_handle* h, int sys, int frozen) {
   return SOMA_OK;
 }
 
+// Resident CTAs per SM of the shape with `warps` consumer warps (a shape
+// the options were validated against).
+int shape_ctas(const soma_handle* h, int warps) { return h->max_ctas_warps[std::max(0, move_shape(warps))]; }
+
 void apply_geometry(soma_handle* h, int ctas_per_sm, int hist_mode, int move_warps) {
   h->move_warps = move_warps;
-  h->max_ctas_per_sm = h->max_ctas_warps[move_warps == 12 ? 1 : 0];
+  h->max_ctas_per_sm = shape_ctas(h, move_warps);
   h->ctas_per_sm = std::max(1, std::min(ctas_per_sm, std::max(h->max_ctas_per_sm, h->max_ctas_batch)));
   h->hist_mode = hist_mode;
   build_args(h);
@@ -648,7 +652,7 @@ static int create_handle(const soma_system_desc* sys, int n_sys, const soma_opti
   if (o.hist_mode < SOMA_HIST_AUTO || o.hist_mode > SOMA_HIST_SEPARATE) return SOMA_EINVAL;
   if (o.graph_steps < 0 || o.graph_steps > 4096) return SOMA_EINVAL;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SOMA_EINVAL;
-  if (o.move_warps != 0 && o.move_warps != 8 && o.move_warps != 12) return SOMA_EINVAL;
+  if (o.move_warps != 0 && move_shape(o.move_warps) < 0) return SOMA_EINVAL;
 
   soma_handle* h = new (std::nothrow) soma_handle();
   if (!h) return SOMA_ENOMEM;
@@ -675,10 +679,11 @@ static int create_handle(const soma_system_desc* sys, int n_sys, const soma_opti
       cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->order_ev, cudaEventDisableTiming) != cudaSuccess)
     return bail(SOMA_ECUDA);
-  h->max_ctas_warps[0] = move_kernel_max_ctas_per_sm(8);
-  h->max_ctas_warps[1] = move_kernel_max_ctas_per_sm(12);
-  h->move_warps = (o.move_warps == 12 && n_sys == 1) ? 12 : 8;
-  h->max_ctas_per_sm = h->max_ctas_warps[h->move_warps == 12 ? 1 : 0];
+  for (int i = 0; i < kMoveShapes; ++i) h->max_ctas_warps[i] = move_kernel_max_ctas_per_sm(kMoveWarps[i]);
+  h->max_ctas_warps[0] = std::max(1, h->max_ctas_warps[0]);  // the default shape always launches
+  h->move_warps = (o.move_warps > 8 && n_sys == 1) ? o.move_warps : 8;
+  if (shape_ctas(h, h->move_warps) == 0) return bail(SOMA_ENOTSUP);
+  h->max_ctas_per_sm = shape_ctas(h, h->move_warps);
   for (int sm = 0; sm < 2; ++sm)
     for (int wz = 0; wz < 2; ++wz) {
       h->max_ctas_batch_kind[sm][wz] = move_batch_max_ctas_per_sm(sm != 0, wz != 0);
@@ -689,8 +694,8 @@ static int create_handle(const soma_system_desc* sys, int n_sys, const soma_opti
   h->sort_interval = o.sort_interval < 0 ? kDefaultSortInterval : o.sort_interval;
   h->f64 = o.precision == SOMA_PREC_FP64;
   if (h->f64) h->sort_interval = 0;  // the precision reference keeps its storage order
-  h->acc_per_sys =
-      h->sm_count * std::max(std::max(h->max_ctas_warps[0], h->max_ctas_warps[1]), h->max_ctas_batch);
+  h->acc_per_sys = h->sm_count * std::max(*std::max_element(h->max_ctas_warps, h->max_ctas_warps + kMoveShapes),
+                                          h->max_ctas_batch);
 
   // --- per-system constants and arrays ---------------------------------
   h->host_sys.resize(n_sys);
@@ -1556,13 +1561,13 @@ int soma_autotune(soma_handle* h) {
   CK(cudaEventCreate(&b));
   const int timing = h->opt.kernel_timing;
   h->opt.kernel_timing = 0;
-  // block shapes: one system tries 8 and 12 consumer warps per CTA (the
+  // block shapes: one system tries 8, 12 and 24 consumer warps per CTA (the
   // batch kernel and the FP64 form have one shape)
   const bool shapes = h->n_sys == 1 && !h->f64 && h->host_sys[0].P > 0;
-  for (int w : {8, 12}) {
-    if (w == 12 && !shapes) continue;
+  for (int w : kMoveWarps) {
+    if (w != 8 && !shapes) continue;
     if (h->opt.move_warps && w != h->opt.move_warps) continue;
-    const int max_c = h->n_sys > 1 ? h->max_ctas_batch : h->max_ctas_warps[w == 12 ? 1 : 0];
+    const int max_c = h->n_sys > 1 ? h->max_ctas_batch : shape_ctas(h, w);
     for (int c = 1; c <= max_c; ++c) {
       if (h->opt.ctas_per_sm && c != h->opt.ctas_per_sm) continue;
       for (int hm = SOMA_HIST_FUSED; hm <= SOMA_HIST_SEPARATE; ++hm) {

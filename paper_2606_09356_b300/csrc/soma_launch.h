@@ -9,10 +9,20 @@
 namespace soma {
 
 // Kernel (a) with fused (b), soma_move.cu.
-// warps: consumer warps per CTA of the single-system kernel, 8 or 12.
+// warps: consumer warps per CTA of the single-system kernel, 8, 12 or 24.
 cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s, int warps);
 cudaError_t launch_move_batch(const BatchArgs& p, int grid, StepRef r, cudaStream_t s);
 int move_batch_max_ctas_per_sm(bool smart, bool wall);
+// Block shapes of the one-system move kernel (consumer warps per CTA).
+constexpr int kMoveShapes = 3;
+constexpr int kMoveWarps[kMoveShapes] = {8, 12, 24};
+// Index of a shape in kMoveWarps, -1 for no shape.
+inline int move_shape(int warps) {
+  for (int i = 0; i < kMoveShapes; ++i)
+    if (kMoveWarps[i] == warps) return i;
+  return -1;
+}
+// Resident CTAs per SM of a shape on the current device (0: it cannot run).
 int move_kernel_max_ctas_per_sm(int warps);
 int move_kernel_chains_per_tile(int P, int warps);
 // The smart move's standard normal deviates of n words (verification aid).

@@ -7,9 +7,9 @@
 //  * persistent CTAs, warp-specialised: one producer warp streams each
 //    tile's positions (x, y, z) and logical chain ids from HBM into a ring of
 //    kStages shared-memory stages with cp.async.bulk, completion tracked by
-//    mbarriers; W consumer warps compute (W = 8 or 12: the single-system
-//    kernel is built for both and the autotuner picks one per workload, the
-//    batch kernel uses 8);
+//    mbarriers; W consumer warps compute (W = 8, 12 or 24: the single-system
+//    kernel is built for all three and the autotuner picks one per workload,
+//    the batch kernel uses 8);
 //  * a consumer lane k of a chain holds beads 2k (even set) and 2k+1 (odd
 //    set); neighbours come from the adjacent lane by width-P shuffles;
 //  * both beads' proposals are formed first, so the four gathers of the lane
@@ -51,9 +51,9 @@ namespace soma {
 constexpr int kStages = 4;
 constexpr int kBatchWarps = 8;  // consumer warps of the batch kernel
 // Resident CTAs per SM the register budget (72) is for: 3 of 8 + 1 warps,
-// 2 of 12 + 1.
+// 2 of 12 + 1, 1 of 24 + 1.
 template <int W>
-constexpr int move_min_blocks() { return W <= 8 ? 3 : 2; }
+constexpr int move_min_blocks() { return W <= 8 ? 3 : (W <= 12 ? 2 : 1); }
 // A tile's bulk copies start at chain c0 = tile * W * 32/P and bead c0 * N;
 // both addresses are 16-byte aligned for every P and N only when the chains
 // per tile are a multiple of 4 (P = 32: W itself).
@@ -129,6 +129,28 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 __device__ __forceinline__ uint32_t round16(uint32_t b) { return (b + 15u) & ~15u; }
+
+// The stage ring of a W-warp CTA: static shared memory up to the 48 KiB a
+// static allocation may take (8 and 12 warps), dynamic shared memory above
+// it (24 warps: 86,592 bytes, opted in per kernel by set_move_smem_limit).
+constexpr size_t kStaticSmemLimit = 48 * 1024;
+template <int W>
+__host__ __device__ constexpr size_t move_ring_bytes() { return kStages * sizeof(MoveStage<W>); }
+template <int W>
+__host__ __device__ constexpr size_t move_dynamic_smem() {
+  return move_ring_bytes<W>() <= kStaticSmemLimit ? 0 : move_ring_bytes<W>();
+}
+
+template <int W>
+__device__ __forceinline__ MoveStage<W>* move_ring() {
+  if constexpr (move_dynamic_smem<W>() == 0) {
+    __shared__ MoveStage<W> ring[kStages];
+    return ring;
+  } else {
+    extern __shared__ __align__(128) unsigned char move_dyn_smem[];
+    return reinterpret_cast<MoveStage<W>*>(move_dyn_smem);
+  }
+}
 
 // Stage reads as volatile shared loads: each is performed exactly once, in
 // program order before the warp releases the stage to the producer.  (A
@@ -666,7 +688,7 @@ __device__ __forceinline__ void drain(uint64_t* full, int issued, int* err) {
 template <int W, bool kFromCounts, bool kSmart, bool kWall, bool kConv>
 __global__ void __launch_bounds__((W + 1) * 32, move_min_blocks<W>())
     k_move(const __grid_constant__ MoveArgs a, StepRef r) {
-  __shared__ MoveStage<W> stage[kStages];
+  MoveStage<W>* stage = move_ring<W>();
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
   init_barriers(full, empty, W);
@@ -789,23 +811,6 @@ cudaError_t launch_wait_selfcheck(int* err, long long cycles, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Resident CTAs per SM of the variant that runs every ordinary step (fields
-// from counts).  The held-field variant uses more registers; launched with
-// the same grid its extra CTAs simply wait for a slot (CTAs never wait on
-// one another).
-int move_kernel_max_ctas_per_sm(int warps) {
-  int n = 0;
-  const cudaError_t e =
-      warps == 12
-          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<12, true, false, false, false>, 13 * 32, 0)
-          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<8, true, false, false, false>, 9 * 32, 0);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return 1;
-  }
-  return n > 0 ? n : 1;
-}
-
 int move_kernel_chains_per_tile(int P, int warps) { return warps * (32 / P); }
 
 using MoveKernel = void (*)(MoveArgs, StepRef);
@@ -825,12 +830,60 @@ static MoveKernel move_kernel_of(bool conv, bool smart, bool wall, bool from_cou
   return table[conv ? 1 : 0][smart ? 1 : 0][wall ? 1 : 0][from_counts ? 1 : 0];
 }
 
+// Every specialisation of the W-warp kernel may take the ring's dynamic
+// shared memory (a per-kernel attribute of the current device; nothing to
+// do where the ring is static).
+template <int W>
+static cudaError_t set_move_smem_limit() {
+  if constexpr (move_dynamic_smem<W>() != 0) {
+    for (int i = 0; i < 16; ++i) {
+      const MoveKernel k = move_kernel_of<W>(i & 8, i & 4, i & 2, i & 1);
+      const cudaError_t e =
+          cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)move_dynamic_smem<W>());
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+// Resident CTAs per SM of the W-warp variant that runs every ordinary step
+// (fields from counts), 0 where the shape cannot run on this device.  Sets
+// the W-warp kernels' shared-memory limit on the current device, so it is
+// called before any launch of the shape.  The held-field variant uses more
+// registers; launched with the same grid its extra CTAs simply wait for a
+// slot (CTAs never wait on one another).
+template <int W>
+static int max_ctas_of() {
+  int n = 0;
+  if (set_move_smem_limit<W>() != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_move<W, true, false, false, false>, (W + 1) * 32,
+                                                    move_dynamic_smem<W>()) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int move_kernel_max_ctas_per_sm(int warps) {
+  switch (warps) {
+    case 8: return max_ctas_of<8>();
+    case 12: return max_ctas_of<12>();
+    case 24: return max_ctas_of<24>();
+    default: return 0;
+  }
+}
+
+template <int W>
+static void launch_move_w(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s) {
+  move_kernel_of<W>(a.conv != 0, a.smart != 0, a.wall_z != 0, from_counts)<<<grid, (W + 1) * 32,
+                                                                             move_dynamic_smem<W>(), s>>>(a, r);
+}
+
 cudaError_t launch_move(const MoveArgs& a, int grid, bool from_counts, StepRef r, cudaStream_t s, int warps) {
-  const bool c = a.conv != 0, sm = a.smart != 0, w = a.wall_z != 0;
-  if (warps == 12) {
-    move_kernel_of<12>(c, sm, w, from_counts)<<<grid, 13 * 32, 0, s>>>(a, r);
-  } else {
-    move_kernel_of<8>(c, sm, w, from_counts)<<<grid, 9 * 32, 0, s>>>(a, r);
+  switch (warps) {
+    case 12: launch_move_w<12>(a, grid, from_counts, r, s); break;
+    case 24: launch_move_w<24>(a, grid, from_counts, r, s); break;
+    default: launch_move_w<8>(a, grid, from_counts, r, s); break;
   }
   return cudaGetLastError();
 }

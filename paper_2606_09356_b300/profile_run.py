@@ -26,7 +26,7 @@ def main():
     p.add_argument("--move", default="uniform", choices=["uniform", "smart"])
     p.add_argument("--walls", action="store_true")
     p.add_argument("--conversion", action="store_true")
-    p.add_argument("--move-warps", type=int, default=0, help="consumer warps per CTA: 8 or 12 (0: 8)")
+    p.add_argument("--move-warps", type=int, default=0, help="consumer warps per CTA: 8, 12 or 24 (0: 8)")
     a = p.parse_args()
     _build.build()
     move = soma.SOMA_MOVE_SMART if a.move == "smart" else soma.SOMA_MOVE_UNIFORM

@@ -45,25 +45,32 @@ def test_launch_shape_histogram_graph_and_reorder_invariance():
                                 dict(N=64, n_A=19), dict(N=1, n_A=1, A=0.3)],
                          ids=["uniform", "smart", "walls", "odd_N", "N64", "monomers"])
 def test_block_shape_invariance(kw):
-    """The move kernel with 8 or 12 consumer warps per CTA (tiles of 8 or 12
-    warps' chains) steps the same trajectory, at every resident-CTA count."""
+    """The move kernel with 8, 12 or 24 consumer warps per CTA (tiles of 8,
+    12 or 24 warps' chains; the 24-warp ring in dynamic shared memory) steps
+    the same trajectory, at every resident-CTA count."""
     s = soma.System(**{**SMALL, **kw})
     ref = _run(s, 30, move_warps=8, graph_steps=0, sort_interval=7)
-    for opts in (dict(move_warps=12), dict(move_warps=12, ctas_per_sm=1), dict(move_warps=12, graph_steps=5)):
-        _same(ref, _run(s, 30, **{**dict(graph_steps=0, sort_interval=7), **opts}))
-    with soma.Handle(s, move_warps=12) as h:
-        assert h.info()["move_warps"] == 12
-    with soma.Handle(s, move_warps=12, autotune=1) as h:
-        h.mc_steps(1)
-        assert h.info()["move_warps"] == 12  # fixed by the option, the autotuner keeps it
-    with pytest.raises(soma.SomaError) as e:
-        soma.Handle(s, move_warps=10)
-    assert e.value.code == soma.SOMA_EINVAL
+    for w in (12, 24):
+        for opts in (dict(move_warps=w), dict(move_warps=w, ctas_per_sm=1), dict(move_warps=w, graph_steps=5)):
+            _same(ref, _run(s, 30, **{**dict(graph_steps=0, sort_interval=7), **opts}))
+        with soma.Handle(s, move_warps=w) as h:
+            assert h.info()["move_warps"] == w
+        with soma.Handle(s, move_warps=w, autotune=1) as h:
+            h.mc_steps(1)
+            assert h.info()["move_warps"] == w  # fixed by the option, the autotuner keeps it
+    with soma.Handle(s, move_warps=24) as h:
+        assert h.info()["ctas_per_sm"] == 1  # 800 threads of 72 registers: one CTA per SM
+    for bad in (10, 16, 32):
+        with pytest.raises(soma.SomaError) as e:
+            soma.Handle(s, move_warps=bad)
+        assert e.value.code == soma.SOMA_EINVAL
 
 
-def test_the_131072_chain_melt_at_both_block_shapes():
+def test_the_131072_chain_melt_at_every_block_shape():
     s = soma.System(**workloads.system_kwargs("melt_131072x32"))
-    _same(_run(s, 6, move_warps=8, graph_steps=0), _run(s, 6, move_warps=12, graph_steps=0))
+    ref = _run(s, 6, move_warps=8, graph_steps=0)
+    for w in (12, 24):
+        _same(ref, _run(s, 6, move_warps=w, graph_steps=0))
 
 
 def test_tuned_sort_interval_keeps_the_trajectory():
@@ -141,7 +148,8 @@ def test_persistent_grid_invariance_full_size():
 def test_long_run_grid_invariance_full_size(variant):
     """A stage-ring race would show up only now and then: melt_131072x32 at full
     size for many steps, CUDA graphs and chain reorders on, with 3 and 1
-    resident CTAs per SM, must stay bit-identical throughout."""
+    resident CTAs per SM and with the 24-warp shape (its ring in dynamic
+    shared memory), must stay bit-identical throughout."""
     kw = dict(workloads.system_kwargs("melt_131072x32"))
     if variant == "smart":
         kw["move"] = soma.SOMA_MOVE_SMART
@@ -150,8 +158,8 @@ def test_long_run_grid_invariance_full_size(variant):
     s = soma.System(**kw)
     steps = 1000 if variant == "uniform" else 300
     ref = None
-    for c in (3, 1):
-        with soma.Handle(s, ctas_per_sm=c, graph_steps=50, sort_interval=97) as h:
+    for opts in (dict(ctas_per_sm=3), dict(ctas_per_sm=1), dict(move_warps=24)):
+        with soma.Handle(s, graph_steps=50, sort_interval=97, **opts) as h:
             h.mc_steps(steps)
             st = (h.get_state()[0], h.get_density(), h.accepted())
         if ref is None:
