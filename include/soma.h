@@ -117,7 +117,11 @@ typedef void* (*soma_alloc_fn)(size_t bytes, void* ctx);
 typedef void (*soma_free_fn)(void* ptr, void* ctx);
 
 typedef struct soma_options {
-  int32_t device;        /* CUDA device ordinal; -1 = the current device */
+  int32_t device;        /* CUDA device ordinal; -1 = the device current at creation.  Every
+                            call on the handle (creation and soma_destroy included) makes
+                            this device current for its duration and restores the caller's
+                            current device on return; streams passed to a call must belong
+                            to it. */
   int32_t sort_interval; /* steps between chain reorders; 0 = never; -1 = tuned by the
                             autotuner (reorder cost against the step-time drift
                             after a reorder), 200 until it runs */
@@ -484,7 +488,8 @@ int soma_normal_deviates(const uint32_t* words, float* out, size_t n);
 /* Failure-path self-check (no counterpart in the paper, which names no
  * fault mechanism): on `device` (-1 = current) one thread waits, with the
  * move kernels' bounded mbarrier wait, on a barrier that nothing arrives
- * on, for at most `cycles` SM clock cycles (1e3 .. 2e10, else SOMA_EINVAL).
+ * on, for at most `cycles` SM clock cycles (1e3 .. 2e10, else SOMA_EINVAL);
+ * the caller's current device is restored on return.
  * Returns SOMA_ETIMEOUT when the wait gave up, set the device error bit and
  * returned as designed (the context stays usable); SOMA_OK would mean the
  * wait completed, SOMA_ECUDA / SOMA_ENOMEM a CUDA failure.  Allocates and

@@ -34,6 +34,44 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Makes `device` (>= 0) the calling thread's current device for the scope
+// and gives the caller's current device back at its end.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int device) {
+    if (device < 0) return;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      ok_ = false;
+      return;
+    }
+    if (cur == device) return;
+    if (cudaSetDevice(device) != cudaSuccess) {
+      ok_ = false;
+      return;
+    }
+    prev_ = cur;
+  }
+  ~DeviceScope() {
+    if (prev_ >= 0) cudaSetDevice(prev_);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+  bool ok() const { return ok_; }
+
+ private:
+  int prev_ = -1;
+  bool ok_ = true;
+};
+
+// Opening of every call on a handle: the handle must be usable, and the call
+// runs with the handle's device current (the caller's is restored on return).
+#define SOMA_ENTER(h)                            \
+  int rc = check_live(h);                        \
+  if (rc) return rc;                             \
+  const DeviceScope device_scope((h)->device);   \
+  if (!device_scope.ok()) return SOMA_ECUDA
+
 constexpr int kDefaultSortInterval = 200;
 constexpr int kDefaultGraphSteps = 16;
 enum { T_MOVE = 0, T_BIN = 1, T_FIELD = 2, T_SORT = 3 };
@@ -53,7 +91,7 @@ int next_pow2(int v) {
 }  // namespace
 
 struct soma_handle {
-  int device = 0, sm_count = 0;
+  int device = -1, sm_count = 0;  // the handle's CUDA device (set at creation)
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // dedicated stream for graph capture
   cudaEvent_t order_ev = nullptr;  // recorded after every soma_mc_steps, on its stream
@@ -598,6 +636,7 @@ int soma_last_error(const soma_handle* h) { return h ? h->sticky : SOMA_EINVAL; 
 
 void soma_destroy(soma_handle* h) {
   if (!h) return;
+  const DeviceScope device_scope(h->device);
   if (h->order_ev) cudaEventSynchronize(h->order_ev);  // steps enqueued on a caller's stream
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& te : h->pending) {
@@ -654,6 +693,9 @@ static int create_handle(const soma_system_desc* sys, int n_sys, const soma_opti
   if ((o.alloc == nullptr) != (o.free == nullptr)) return SOMA_EINVAL;
   if (o.move_warps != 0 && move_shape(o.move_warps) < 0) return SOMA_EINVAL;
 
+  // creation runs on opt.device and leaves the caller's current device as it was
+  const DeviceScope device_scope(o.device);
+  if (!device_scope.ok()) return SOMA_ECUDA;
   soma_handle* h = new (std::nothrow) soma_handle();
   if (!h) return SOMA_ENOMEM;
   h->opt = o;
@@ -666,12 +708,7 @@ static int create_handle(const soma_system_desc* sys, int n_sys, const soma_opti
     return code;
   };
 
-  if (o.device >= 0) {
-    if (cudaSetDevice(o.device) != cudaSuccess) return bail(SOMA_ECUDA);
-    h->device = o.device;
-  } else if (cudaGetDevice(&h->device) != cudaSuccess) {
-    return bail(SOMA_ECUDA);
-  }
+  if (cudaGetDevice(&h->device) != cudaSuccess) return bail(SOMA_ECUDA);  // opt.device, or the current one
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess) return bail(SOMA_ECUDA);
   h->sm_count = prop.multiProcessorCount;
@@ -844,8 +881,7 @@ int soma_create_partition(const soma_system_desc* sys, const soma_options* opt, 
 }
 
 int soma_exchange_counts(soma_handle* h, uint32_t** counts, size_t* n_words) {
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (!counts || !n_words || h->f64 || h->n_sys != 1) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[0];
   *counts = count_buffer(S.counts, S.n_c, (long long)h->step - 1);
@@ -855,8 +891,7 @@ int soma_exchange_counts(soma_handle* h, uint32_t** counts, size_t* n_words) {
 
 int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
   NvtxRange nvtx_range("soma_mc_steps");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (n_steps < 0) return SOMA_EINVAL;
   if (h->step + (uint64_t)n_steps >= (uint64_t)kInitStep) return SOMA_EINVAL;
   if (n_steps == 0) return SOMA_OK;
@@ -915,8 +950,7 @@ int soma_mc_steps(soma_handle* h, int64_t n_steps, void* stream) {
 
 int soma_sync(soma_handle* h, void* stream) {
   NvtxRange nvtx_range("soma_sync");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   CK(cudaStreamSynchronize(pick(h, stream)));
   CK(cudaStreamSynchronize(h->stream));
   return check_device_error(h);
@@ -924,8 +958,7 @@ int soma_sync(soma_handle* h, void* stream) {
 
 int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where) {
   NvtxRange nvtx_range("soma_get_density");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
@@ -940,8 +973,7 @@ int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where
 
 int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t n) {
   NvtxRange nvtx_range("soma_density_profile");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !out || axis < 0 || axis > 2) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   const int dims[3] = {S.nx, S.ny, S.nz};
@@ -970,8 +1002,7 @@ int soma_density_profile(soma_handle* h, int sys, int axis, double* out, size_t 
 
 int soma_vertical_correlation(soma_handle* h, int sys, int type, double* out, size_t n) {
   NvtxRange nvtx_range("soma_vertical_correlation");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !out || type < 0 || type > 1) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if (n != (size_t)S.nz) return SOMA_EINVAL;
@@ -1003,8 +1034,7 @@ int soma_vertical_correlation(soma_handle* h, int sys, int type, double* out, si
 
 int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where) {
   NvtxRange nvtx_range("soma_get_fields");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if (n != (size_t)(2 * S.n_c)) return SOMA_EINVAL;
@@ -1021,8 +1051,7 @@ int soma_get_fields(soma_handle* h, int sys, float* out, size_t n, int where) {
 
 int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int where) {
   NvtxRange nvtx_range("soma_set_density");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys || !phi) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
@@ -1037,8 +1066,7 @@ int soma_set_density(soma_handle* h, int sys, const float* phi, size_t n, int wh
 
 int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int where) {
   NvtxRange nvtx_range("soma_freeze_fields");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
@@ -1059,8 +1087,7 @@ int soma_freeze_fields(soma_handle* h, int sys, const float* w, size_t n, int wh
 
 int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* step, int where) {
   NvtxRange nvtx_range("soma_get_state");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
@@ -1078,8 +1105,7 @@ int soma_get_state(soma_handle* h, int sys, float* pos, int16_t* img, uint64_t* 
 
 int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img, uint64_t step, int where) {
   NvtxRange nvtx_range("soma_set_state");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys || !pos || !img) return SOMA_EINVAL;
   if (step >= (uint64_t)kInitStep) return SOMA_EINVAL;
@@ -1110,8 +1136,7 @@ int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img
 
 int soma_get_state64(soma_handle* h, int sys, double* pos, int16_t* img, uint64_t* step, int where) {
   NvtxRange nvtx_range("soma_get_state64");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (!h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
@@ -1129,8 +1154,7 @@ int soma_get_state64(soma_handle* h, int sys, double* pos, int16_t* img, uint64_
 
 int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* img, uint64_t step, int where) {
   NvtxRange nvtx_range("soma_set_state64");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (!h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys || !pos || !img) return SOMA_EINVAL;
   if (step >= (uint64_t)kInitStep) return SOMA_EINVAL;
@@ -1160,8 +1184,7 @@ int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* 
 }
 
 int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted) {
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !accepted) return SOMA_EINVAL;
   // the steps may have gone to a caller's stream: read after them
   CK(cudaStreamWaitEvent(h->stream, h->order_ev, 0));
@@ -1174,8 +1197,7 @@ int soma_get_accepted(soma_handle* h, int sys, uint64_t* accepted) {
 }
 
 int soma_copy_accepted(soma_handle* h, int sys, uint64_t* dst, void* stream) {
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !dst) return SOMA_EINVAL;
   cudaStream_t s = pick(h, stream);
   CK(cudaStreamWaitEvent(s, h->order_ev, 0));  // after the latest steps, on any stream
@@ -1197,8 +1219,7 @@ int soma_copy_accepted(soma_handle* h, int sys, uint64_t* dst, void* stream) {
 
 int soma_observables(soma_handle* h, int sys, soma_obs* out) {
   NvtxRange nvtx_range("soma_observables");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if ((rc = sync_all(h))) return rc;
@@ -1228,8 +1249,7 @@ int soma_observables(soma_handle* h, int sys, soma_obs* out) {
 
 int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz, double* S_out) {
   NvtxRange nvtx_range("soma_structure_factor");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || nq < 0 || (nq > 0 && (!m_xyz || !S_out))) return SOMA_EINVAL;
   if (nq == 0) return SOMA_OK;
   if ((rc = sync_all(h))) return rc;
@@ -1255,8 +1275,7 @@ int soma_structure_factor(soma_handle* h, int sys, int nq, const int32_t* m_xyz,
 
 int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n, double lambdaN, int where) {
   NvtxRange nvtx_range("soma_set_umbrella");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
   if (!std::isfinite(lambdaN) || lambdaN < 0.0) return SOMA_EINVAL;
@@ -1290,8 +1309,7 @@ int soma_set_umbrella(soma_handle* h, int sys, const float* phi_target, size_t n
 
 int soma_set_conversion(soma_handle* h, int sys, int32_t n_A_alt, double zone_lo, double zone_hi, const double* p) {
   NvtxRange nvtx_range("soma_set_conversion");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys) return SOMA_EINVAL;
   SysDev& S = h->host_sys[sys];
   const bool on = n_A_alt >= 0;
@@ -1335,8 +1353,7 @@ int soma_set_conversion(soma_handle* h, int sys, int32_t n_A_alt, double zone_lo
 }
 
 int soma_get_conversions(soma_handle* h, int sys, uint64_t* out) {
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if ((rc = sync_all(h))) return rc;
@@ -1350,8 +1367,7 @@ int soma_get_conversions(soma_handle* h, int sys, uint64_t* out) {
 
 int soma_get_chain_types(soma_handle* h, int sys, uint8_t* out, size_t n) {
   NvtxRange nvtx_range("soma_get_chain_types");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !out) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if (n != (size_t)S.n_poly) return SOMA_EINVAL;
@@ -1365,8 +1381,7 @@ int soma_get_chain_types(soma_handle* h, int sys, uint8_t* out, size_t n) {
 
 int soma_set_chain_types(soma_handle* h, int sys, const uint8_t* types, size_t n) {
   NvtxRange nvtx_range("soma_set_chain_types");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (sys < 0 || sys >= h->n_sys || !types) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if (n != (size_t)S.n_poly || !S.conv) return SOMA_EINVAL;
@@ -1384,8 +1399,7 @@ int soma_set_chain_types(soma_handle* h, int sys, const uint8_t* types, size_t n
 
 int soma_place(soma_handle* h, int sys, const float* phi_target, size_t n, int where) {
   NvtxRange nvtx_range("soma_place");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (h->f64) return SOMA_ENOTSUP;
   if (sys < 0 || sys >= h->n_sys || !phi_target) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
@@ -1439,7 +1453,8 @@ int soma_normal_deviates(const uint32_t* words, float* out, size_t n) {
 
 int soma_selfcheck_timeout(int device, uint64_t cycles) {
   if (cycles < 1000 || cycles > 20000000000ull) return SOMA_EINVAL;
-  if (device >= 0 && cudaSetDevice(device) != cudaSuccess) return SOMA_ECUDA;
+  const DeviceScope device_scope(device);
+  if (!device_scope.ok()) return SOMA_ECUDA;
   int* err = nullptr;
   if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
@@ -1457,8 +1472,7 @@ int soma_selfcheck_timeout(int device, uint64_t cycles) {
 
 int soma_reorder(soma_handle* h, void* stream) {
   NvtxRange nvtx_range("soma_reorder");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (h->f64) return SOMA_ENOTSUP;
   return enqueue_reorder(h, pick(h, stream));
 }
@@ -1509,8 +1523,7 @@ int soma_kernel_times(soma_handle* h, double* ms, int64_t* launches, int reset) 
 // run; the acceptance counters are restored as well.
 int soma_autotune(soma_handle* h) {
   NvtxRange nvtx_range("soma_autotune");
-  int rc = check_live(h);
-  if (rc) return rc;
+  SOMA_ENTER(h);
   if (h->partition) return SOMA_ENOTSUP;  // its trial steps would run between count exchanges
   h->tuned = true;
   if ((rc = sync_all(h))) return rc;
