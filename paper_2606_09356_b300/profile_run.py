@@ -4,6 +4,9 @@ profilers such as ncu; prints nothing but a one-line summary).
     python -m paper_2606_09356_b300.profile_run --workload melt_131072x32 --steps 20 [--move smart]
         [--walls] [--conversion] [--move-warps 12]
 
+--workload batch64 steps the 64-system batch in one handle (the batch
+kernel; uniform moves, periodic z).
+
 --conversion switches on boundary-zone conversion (zones 2 R_e wide at the
 bottom and top, per-step rates 0.05, 0.02, 0.03, 0.04, converted molecules
 with half the A block); it is meant with --walls.
@@ -30,17 +33,22 @@ def main():
     a = p.parse_args()
     _build.build()
     move = soma.SOMA_MOVE_SMART if a.move == "smart" else soma.SOMA_MOVE_UNIFORM
-    kw = workloads.system_kwargs(a.workload)
-    s = soma.System(**{**kw, "move": move, "wall_z": 1 if a.walls else 0})
-    with soma.Handle(s, graph_steps=a.graph_steps, sort_interval=a.sort_interval, hist_mode=a.hist_mode,
+    if a.workload == "batch64":
+        systems = [soma.System(**{k: v for k, v in d.items() if k != "f_A"}) for d in workloads.batch64()]
+        n_beads = sum(x.n_beads for x in systems)
+    else:
+        kw = workloads.system_kwargs(a.workload)
+        systems = soma.System(**{**kw, "move": move, "wall_z": 1 if a.walls else 0})
+        n_beads = systems.n_beads
+    with soma.Handle(systems, graph_steps=a.graph_steps, sort_interval=a.sort_interval, hist_mode=a.hist_mode,
                      ctas_per_sm=a.ctas_per_sm, move_warps=a.move_warps) as h:
-        if a.conversion:
+        if a.conversion and a.workload != "batch64":
             h.set_conversion(kw["n_A"] // 2, 2.0, 2.0, (0.05, 0.02, 0.03, 0.04))
         t = time.perf_counter()
         h.mc_steps(a.steps)
         h.sync()
         dt = time.perf_counter() - t
-        print(f"{a.workload}: {a.steps} steps, {a.steps * s.n_beads / dt:.3e} moves/s (wall, incl. launch)")
+        print(f"{a.workload}: {a.steps} steps, {a.steps * n_beads / dt:.3e} moves/s (wall, incl. launch)")
 
 
 if __name__ == "__main__":

@@ -73,6 +73,14 @@ def test_the_131072_chain_melt_at_every_block_shape():
         _same(ref, _run(s, 6, move_warps=w, graph_steps=0))
 
 
+def test_the_1048576_chain_melt_at_24_and_8_warps():
+    """melt_1048576x64 at full size (67 M beads, 24 chains per 24-warp tile,
+    43,691 tiles over one CTA per SM) steps the same trajectory at 24 and
+    at 8 consumer warps per CTA."""
+    s = soma.System(**workloads.system_kwargs("melt_1048576x64"))
+    _same(_run(s, 2, move_warps=8, graph_steps=0), _run(s, 2, move_warps=24, graph_steps=0))
+
+
 def test_tuned_sort_interval_keeps_the_trajectory():
     s = soma.System(**SMALL)
     ref = _run(s, 40, graph_steps=0, sort_interval=0)

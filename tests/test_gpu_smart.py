@@ -134,6 +134,24 @@ def test_mixed_move_kinds_batched_equal_plain():
             _same(batched[i], (h.get_state()[0], h.get_density(), h.accepted()))
 
 
+def test_batch64_smart_full_size_equals_solo_runs():
+    """The 64-system batch with force-biased moves (the batch kernel whose
+    system index is warp-uniform): after 3 steps the largest, the densest
+    and the smallest systems equal the same systems stepped alone."""
+    specs = workloads.batch64()
+    systems = [soma.System(**{**{k: v for k, v in d.items() if k != "f_A"}, "move": SMART}) for d in specs]
+    beads = [x.n_beads for x in systems]
+    dens = [x.n_beads / x.n_cells for x in systems]
+    picks = sorted({int(np.argmax(beads)), int(np.argmax(dens)), int(np.argmin(beads))})
+    with soma.Handle(systems, graph_steps=0) as hb:
+        hb.mc_steps(3)
+        batched = {i: (hb.get_state(i)[0], hb.get_density(i), hb.accepted(i)) for i in picks}
+    for i in picks:
+        with soma.Handle(systems[i], graph_steps=0) as h:
+            h.mc_steps(3)
+            _same(batched[i], (h.get_state()[0], h.get_density(), h.accepted()))
+
+
 def test_smart_ideal_chains_keep_gaussian_statistics():
     """chiN = kappaN = 0: the harmonic chain's Boltzmann law is stationary
     under the force-biased moves, so <b^2>(N-1) and <R_e^2> stay 1."""
