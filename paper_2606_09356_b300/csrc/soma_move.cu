@@ -737,8 +737,9 @@ __device__ __forceinline__ int batch_system(const BatchArgs& p, int tile) {
 }
 
 // One move kind and one z boundary per launch (the host groups systems so).
-// Register budget for 3 resident CTAs per SM as k_move (the bond-force-biased
-// specialisations spill a few bytes and still beat 2 CTAs per SM).
+// Register budget for 3 resident CTAs per SM as the 8-warp k_move (with the
+// warp-uniform system index below, only the walled bond-force-biased
+// specialisation still spills, 12 bytes; it beats 2 CTAs per SM).
 template <bool kSmart, bool kWall>
 __global__ void __launch_bounds__((kBatchWarps + 1) * 32, move_min_blocks<kBatchWarps>())
     k_move_batch(const __grid_constant__ BatchArgs p, StepRef r) {
