@@ -1,7 +1,9 @@
 """The checked build (libsoma_debug.so, -DSOMA_DEBUG: device bounds checks on
 every final cell, position and image counter of the move kernel) runs the
-same shapes as the product library with no check firing and bit-identical
-results (needs a GPU).  Each library runs in its own process."""
+same shapes as the product library, at each block shape of the move kernel
+(8, 12 and 24 consumer warps per CTA), with no check firing and
+bit-identical results (needs a GPU).  Each library runs in its own
+process."""
 import json
 import os
 import subprocess
@@ -29,9 +31,9 @@ shapes = [
     dict(workloads.system_kwargs("melt_512x32"), move=soma.SOMA_MOVE_SMART, wall_z=1),
 ]
 out = []
-for kw in shapes:
+for kw, warps in [(kw, w) for kw in shapes for w in (8, 12, 24)]:
     s = soma.System(**kw)
-    with soma.Handle(s, graph_steps=4) as h:
+    with soma.Handle(s, graph_steps=4, move_warps=warps) as h:
         h.mc_steps(30)
         nx = s.grid[0]
         pA = np.repeat(0.5 + 0.4 * np.sin(2 * np.pi * (np.arange(nx) + 0.5) / nx), s.grid[1] * s.grid[2])
@@ -59,3 +61,6 @@ def test_checked_build_runs_clean_and_matches_release():
     release = _run(_build.LIB)
     checked = _run(_build.LIB_DEBUG)
     assert checked == release
+    # every block shape steps the same trajectory
+    for i in range(0, len(release), 3):
+        assert release[i] == release[i + 1] == release[i + 2]
