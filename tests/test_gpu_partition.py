@@ -66,6 +66,28 @@ def test_partitions_reproduce_the_whole_system(move, wall):
     _check_same(s, whole, parts)
 
 
+@pytest.mark.parametrize("warps", [12, 24])
+def test_partitions_at_every_block_shape(warps):
+    """Partitions whose move kernel runs 12 or 24 consumer warps per CTA (so
+    a partition's tiles hold 24 or 48 chains and its last tile is ragged)
+    reproduce the whole system stepped at 8."""
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
+    st = torch.cuda.Stream()
+    whole = soma.Handle(s, graph_steps=0, sort_interval=5, move_warps=8)
+    parts = [soma.Handle(s, partition=r, graph_steps=0, sort_interval=5, move_warps=warps)
+             for r in [(0, 101), (101, 389), (389, 512)]]
+    assert all(h.info()["move_warps"] == warps for h in parts)
+    torch.cuda.synchronize()
+    partition.sum_on_one_device(parts, st)
+    for _ in range(12):
+        whole.mc_steps(1, stream=st.cuda_stream)
+        for h in parts:
+            h.mc_steps(1, stream=st.cuda_stream)
+        partition.sum_on_one_device(parts, st)
+    torch.cuda.synchronize()
+    _check_same(s, whole, parts)
+
+
 def test_partitions_with_conversion_and_odd_chains():
     s = soma.System(n_poly=301, N=7, n_A=3, box=(4.0, 4.0, 4.5), grid=(16, 16, 18), chiN=18.0, kappaN=40.0,
                     seed=5, wall_z=1)
