@@ -966,8 +966,8 @@ int soma_get_density(soma_handle* h, int sys, uint32_t* out, size_t n, int where
   const uint32_t* src = count_buffer(S.counts, S.n_c, (long long)h->step - 1);
   uint32_t* dst = where == SOMA_DEVICE ? out : reinterpret_cast<uint32_t*>(h->d_stage_phi);
   CK(launch_deinterleave(src, S.n_c, dst, h->sm_count, h->stream));
+  if (where != SOMA_DEVICE) CK(cudaMemcpyAsync(out, dst, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  if (where != SOMA_DEVICE) CK(cudaMemcpy(out, dst, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
   return SOMA_OK;
 }
 
@@ -1111,14 +1111,17 @@ int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img
   if (step >= (uint64_t)kInitStep) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if ((rc = sync_all(h))) return rc;
+  // both copies, the validation and the read of its verdict are queued on
+  // the handle's stream and waited for once (from pinned host memory the
+  // copies run as DMA while the host queues the rest)
   const cudaMemcpyKind k = where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CK(cudaMemcpy(h->d_stage_pos, pos, (size_t)S.n_b * 12, k));
-  CK(cudaMemcpy(h->d_stage_img, img, (size_t)S.n_b * 6, k));
   CK(cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+  CK(cudaMemcpyAsync(h->d_stage_pos, pos, (size_t)S.n_b * 12, k, h->stream));
   CK(launch_validate_pos(h->d_stage_pos, S.n_b, S.L, h->d_err, h->sm_count, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpyAsync(h->d_stage_img, img, (size_t)S.n_b * 6, k, h->stream));
   int err = 0;
-  CK(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&err, h->d_err, 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   if (err) {
     CK(cudaMemset(h->d_err, 0, 4));
     return SOMA_EINVAL;  // a position outside [0, L): rejected, the state is untouched
@@ -1161,13 +1164,13 @@ int soma_set_state64(soma_handle* h, int sys, const double* pos, const int16_t* 
   const SysDev& S = h->host_sys[sys];
   if ((rc = sync_all(h))) return rc;
   const cudaMemcpyKind k = where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CK(cudaMemcpy(h->d_stage_pos64, pos, (size_t)S.n_b * 24, k));
-  CK(cudaMemcpy(h->d_stage_img, img, (size_t)S.n_b * 6, k));
   CK(cudaMemsetAsync(h->d_err, 0, 4, h->stream));
+  CK(cudaMemcpyAsync(h->d_stage_pos64, pos, (size_t)S.n_b * 24, k, h->stream));
   CK(launch_validate_pos64(h->d_stage_pos64, S.n_b, S.L64, h->d_err, h->sm_count, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpyAsync(h->d_stage_img, img, (size_t)S.n_b * 6, k, h->stream));
   int err = 0;
-  CK(cudaMemcpy(&err, h->d_err, 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&err, h->d_err, 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   if (err) {
     CK(cudaMemset(h->d_err, 0, 4));
     return SOMA_EINVAL;
