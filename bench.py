@@ -379,8 +379,9 @@ def run_gpu(args):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     # the autotuner times trial steps with CUDA events; under a profiler those
     # timings are distorted (serialised, cache-flushed launches), so profiling
-    # runs pass --no-autotune and get the default launch shape, which is what
-    # the autotuner picks on this workload outside a profiler
+    # runs pass --no-autotune and get the default launch shape (8 consumer
+    # warps, 3 CTAs per SM), which ties with the autotuner's pick on this
+    # workload outside a profiler
     # kernel_timing = 0: no timing events of the library's own inside the step
     # windows; a step is one launch of the move kernel (the launch counts
     # below confirm it), so the window is that launch's duration
