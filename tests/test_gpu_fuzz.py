@@ -56,7 +56,9 @@ def test_random_shape_steps_match_oracle(seed):
     s = random_system(rng, 0)
     orc = G.oracle_for(s)
     band = 1e-4 if s.move else None
-    with soma.Handle(s, graph_steps=0, ctas_per_sm=int(rng.integers(0, 4))) as h:
+    # the block shape cycles with the seed (no draw from rng: the shapes stay
+    # those of the seed); resident CTAs above a shape's limit are clamped
+    with soma.Handle(s, graph_steps=0, ctas_per_sm=int(rng.integers(0, 4)), move_warps=(8, 12, 24)[seed % 3]) as h:
         mode = int(rng.integers(0, 3))
         tg, lam = None, float(rng.uniform(1, 60))
         if mode == 1:  # umbrella toward a random target
