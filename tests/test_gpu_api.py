@@ -28,6 +28,39 @@ def test_set_state_rejects_positions_outside_the_box_and_keeps_state():
         assert h.get_state()[2] == 2
 
 
+def test_set_state_from_pinned_host_and_device_memory():
+    """The state goes up from pageable, pinned and device buffers alike
+    (queued copies, one wait), and a position outside the box in device
+    memory is refused like one in host memory."""
+    import torch
+    s = soma.System(**workloads.system_kwargs("melt_512x32"))
+    with soma.Handle(s) as h:
+        h.mc_steps(3)
+        pos, img, step = h.get_state()
+        ref = None
+        for form in ("pageable", "pinned", "device"):
+            if form == "pageable":
+                p, i = pos.copy(), img.copy()
+            elif form == "pinned":
+                p = torch.from_numpy(pos.copy()).pin_memory().numpy()
+                i = torch.from_numpy(img.copy()).pin_memory().numpy()
+            else:
+                p = torch.from_numpy(pos.copy()).cuda().contiguous()
+                i = torch.from_numpy(img.copy()).cuda().contiguous()
+            h.set_state(p, i, step)
+            h.mc_steps(2)
+            got = (h.get_state()[0], h.get_density(), h.accepted())
+            ref = ref or got
+            assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+        bad = torch.from_numpy(pos.copy()).cuda()
+        bad[7, 2] = -0.5
+        keep = h.get_state()[0]
+        with pytest.raises(soma.SomaError) as e:
+            h.set_state(bad, torch.from_numpy(img).cuda(), step)
+        assert e.value.code == soma.SOMA_EINVAL
+        assert np.array_equal(h.get_state()[0], keep)
+
+
 def test_argument_errors():
     s = soma.System(**workloads.system_kwargs("melt_512x32"))
     with soma.Handle(s) as h:
