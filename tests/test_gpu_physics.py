@@ -117,8 +117,10 @@ def _record_stats(name, values):
 
 # (move, burn-in steps, sampled steps, sampling interval): the uniform move at
 # the full length (5,000 burn-in, 20,000 sampled, 8 seeds); the force-biased
-# move, whose oracle is about eight times slower, at a tenth of it
-LONG_RUNS = [(soma.SOMA_MOVE_UNIFORM, 5000, 20000, 500), (soma.SOMA_MOVE_SMART, 500, 2000, 250)]
+# move, whose oracle is about eight times slower, at a tenth of it by default
+# (SOMA_SMART_LONG="burn,steps,every" runs it longer)
+_SMART = tuple(int(v) for v in os.environ.get("SOMA_SMART_LONG", "500,2000,250").split(","))
+LONG_RUNS = [(soma.SOMA_MOVE_UNIFORM, 5000, 20000, 500), (soma.SOMA_MOVE_SMART,) + _SMART]
 
 
 @pytest.mark.parametrize("move,burn,steps,every", LONG_RUNS, ids=["uniform", "smart"])
