@@ -179,13 +179,39 @@ def test_long_run_statistics_agree_with_oracle(move, burn, steps, every):
         assert abs(d["gpu"] - d["oracle"]) <= 3 * d["se"] + 1e-12, (name, d)
 
 
+def _length(var, default="300,1200,100"):
+    """(burn-in, sampled steps, sampling interval) of a walled long run: the
+    default, or the environment variable `var` ("burn,steps,every")."""
+    return tuple(int(v) for v in os.environ.get(var, default).split(","))
+
+
+def _seeds():
+    """The 8 seeds of a walled long run: 1..8, or 8 from SOMA_LONG_SEED0 on."""
+    s0 = int(os.environ.get("SOMA_LONG_SEED0", "1"))
+    return range(s0, s0 + 8)
+
+
+def _check_seed_means(name, burn, steps, g, r, names):
+    """GPU and oracle seed means of each quantity (columns of g and r) agree
+    within 3 combined standard errors; the differences are recorded."""
+    n = len(g)
+    report = {"burn": burn, "steps": steps, "seeds": n}
+    for k, q in enumerate(names):
+        se = np.sqrt(g[:, k].var(ddof=1) / n + r[:, k].var(ddof=1) / n)
+        d = g[:, k].mean() - r[:, k].mean()
+        report[q] = {"gpu": float(g[:, k].mean()), "oracle": float(r[:, k].mean()), "se": float(se),
+                     "diff_over_se": float(d / se) if se > 0 else 0.0}
+        assert abs(d) <= 3 * se + 1e-12, (q, g[:, k].mean(), r[:, k].mean(), se)
+    _record_stats(name, report)
+
+
 def test_long_run_slab_statistics_agree_with_oracle():
     """Between hard walls in z (512 chains of 32 beads): <R_e^2>, acceptance and the
     total-density profile of the two wall layers from the GPU and the oracle
     agree within 3 sigma over 8 seeds (the depletion at the walls is a
     property of the confined melt that neither side is told)."""
     kw = {**workloads.system_kwargs("melt_512x32"), "wall_z": 1}
-    burn, steps, every = 300, 1200, 100
+    burn, steps, every = _length("SOMA_SLAB_LONG")
 
     def stats(seed, gpu):
         s = soma.System(**{**kw, "seed": seed})
@@ -214,11 +240,10 @@ def test_long_run_slab_statistics_agree_with_oracle():
         prof = np.mean(prof, axis=0)
         return np.mean(re2), acc, 0.5 * (prof[0] + prof[-1])
 
-    g = np.array([stats(sd, True) for sd in range(1, 9)])
-    r = np.array([stats(sd, False) for sd in range(1, 9)])
-    for k, name in ((0, "Re2"), (1, "acc"), (2, "wall-layer density")):
-        se = np.sqrt(g[:, k].var(ddof=1) / 8 + r[:, k].var(ddof=1) / 8)
-        assert abs(g[:, k].mean() - r[:, k].mean()) <= 3 * se + 1e-12, (name, g[:, k].mean(), r[:, k].mean(), se)
+    seeds = _seeds()
+    g = np.array([stats(sd, True) for sd in seeds])
+    r = np.array([stats(sd, False) for sd in seeds])
+    _check_seed_means("melt_512x32 walls", burn, steps, g, r, ("Re2", "acc", "wall-layer density"))
     # the walls deplete the layers next to them
     assert g[:, 2].mean() < 0.95
 
@@ -232,7 +257,7 @@ def test_long_run_conversion_statistics_agree_with_oracle():
     form)."""
     kw = {**workloads.system_kwargs("melt_512x32"), "wall_z": 1}
     conv = (4, 1.0, 1.0, (0.05, 0.02, 0.03, 0.04))
-    burn, steps, every = 300, 1200, 100
+    burn, steps, every = _length("SOMA_CONV_LONG")
 
     def stats(seed, gpu):
         s = soma.System(**{**kw, "seed": seed})
@@ -262,9 +287,9 @@ def test_long_run_conversion_statistics_agree_with_oracle():
         prof = np.mean(prof, axis=0)
         return np.mean(frac), 0.5 * (prof[0] + prof[-1]), acc
 
-    g = np.array([stats(sd, True) for sd in range(1, 9)])
-    r = np.array([stats(sd, False) for sd in range(1, 9)])
-    for k, name in ((0, "converted fraction"), (1, "wall-layer A fraction"), (2, "acc")):
-        se = np.sqrt(g[:, k].var(ddof=1) / 8 + r[:, k].var(ddof=1) / 8)
-        assert abs(g[:, k].mean() - r[:, k].mean()) <= 3 * se + 1e-12, (name, g[:, k].mean(), r[:, k].mean(), se)
+    seeds = _seeds()
+    g = np.array([stats(sd, True) for sd in seeds])
+    r = np.array([stats(sd, False) for sd in seeds])
+    _check_seed_means("melt_512x32 walls + conversion", burn, steps, g, r,
+                      ("converted fraction", "wall-layer A fraction", "acc"))
     assert 0.05 < g[:, 0].mean() < 0.6  # conversions happen and are undone
