@@ -115,6 +115,12 @@ def _record_stats(name, values):
         json.dump(data, f, indent=1)
 
 
+def _seeds():
+    """The 8 seeds of a long run: 1..8, or 8 from SOMA_LONG_SEED0 on."""
+    s0 = int(os.environ.get("SOMA_LONG_SEED0", "1"))
+    return range(s0, s0 + 8)
+
+
 # (move, burn-in steps, sampled steps, sampling interval): the uniform move at
 # the full length (5,000 burn-in, 20,000 sampled, 8 seeds); the force-biased
 # move, whose oracle is about eight times slower, at a tenth of it by default
@@ -157,7 +163,7 @@ def test_long_run_statistics_agree_with_oracle(move, burn, steps, every):
             sq.append(o.structure_factor(X, m))
         return np.mean(re2), acc / (steps * o.n_b), np.mean(sq, axis=0)
 
-    seeds = range(1, 9)
+    seeds = _seeds()
     g = [stats_gpu(s) for s in seeds]
     r = [stats_orc(s) for s in seeds]
 
@@ -183,12 +189,6 @@ def _length(var, default="300,1200,100"):
     """(burn-in, sampled steps, sampling interval) of a walled long run: the
     default, or the environment variable `var` ("burn,steps,every")."""
     return tuple(int(v) for v in os.environ.get(var, default).split(","))
-
-
-def _seeds():
-    """The 8 seeds of a walled long run: 1..8, or 8 from SOMA_LONG_SEED0 on."""
-    s0 = int(os.environ.get("SOMA_LONG_SEED0", "1"))
-    return range(s0, s0 + 8)
 
 
 def _check_seed_means(name, burn, steps, g, r, names):
