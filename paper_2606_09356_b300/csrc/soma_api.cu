@@ -1111,7 +1111,7 @@ int soma_set_state(soma_handle* h, int sys, const float* pos, const int16_t* img
   if (step >= (uint64_t)kInitStep) return SOMA_EINVAL;
   const SysDev& S = h->host_sys[sys];
   if ((rc = sync_all(h))) return rc;
-  // both copies, the validation and the read of its verdict are queued on
+  // both copies, the validation and the read of its outcome are queued on
   // the handle's stream and waited for once (from pinned host memory the
   // copies run as DMA while the host queues the rest)
   const cudaMemcpyKind k = where == SOMA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
